@@ -1,0 +1,349 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Each test fixes one part of the oracle by a worked example printed in the paper, a
+closed form, an independent textbook construction (Kronecker products / Jordan-Wigner
+matrices in tests/_indep.py), brute force, or a published known-answer vector.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests import _indep
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, *vals = line.split()
+                out[k] = vals
+    return out
+
+
+# ----------------------------------------------------------------------------- basis
+def test_paper_sz0_basis_and_ranks():
+    g = _golden("paper_examples.txt")
+    want = [int(x) for x in g["sz0_basis_4site"]]
+    got = oracle.sector_list(4, 2).tolist()
+    assert got == want
+    assert [oracle.rank(s, 4) for s in want] == list(range(6))
+    assert [oracle.unrank(r, 4, 2) for r in range(6)] == want
+
+
+@pytest.mark.parametrize("key", ["dim_hubbard_18", "dim_13_6", "dim_13_9"])
+def test_paper_dimension_statements(key):
+    n, k, d = (int(x) for x in _golden("paper_examples.txt")[key])
+    assert oracle.binom(n, k) ** 2 == d
+    spec = wl.hubbard_ring(n).with_basis(wl.BASIS_NUMBER, k, k)
+    assert oracle.dim(spec) == d
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 14])
+def test_rank_unrank_exhaustive(n):
+    for k in range(n + 1):
+        lst = oracle.sector_list(n, k)
+        assert len(lst) == math.comb(n, k)
+        assert np.all(np.diff(lst.astype(np.int64)) > 0)
+        for r, s in enumerate(lst.tolist()):
+            assert _indep.popcount(s) == k
+            assert oracle.rank(s, n) == r
+            assert oracle.unrank(r, n, k) == s
+
+
+def test_rank_unrank_36_bits_random():
+    rng = np.random.default_rng(1)
+    n, k = 36, 18
+    D = math.comb(n, k)
+    for r in rng.integers(0, D, size=2000).tolist() + [0, D - 1]:
+        s = oracle.unrank(r, n, k)
+        assert _indep.popcount(s) == k and s < (1 << n)
+        assert oracle.rank(s, n) == r
+    assert oracle.unrank(0, n, k) == (1 << k) - 1
+    assert oracle.unrank(D - 1, n, k) == ((1 << k) - 1) << (n - k)
+
+
+def test_paper_fermion_4ary_example():
+    """Section 3.1: |0, up, dn, updn> = [0123]_4 = 27 in the paper's interleaved layout.
+
+    The oracle keeps separate up / down strings; interleaving them (up -> bit 2i, down ->
+    bit 2i+1) must reproduce the paper's label."""
+    g = [int(x) for x in _golden("paper_examples.txt")["fermion_4ary"]]
+    digits, want = g[:4], g[4]  # sites 3, 2, 1, 0
+    up = dn = 0
+    for pos, d in zip((3, 2, 1, 0), digits):
+        up |= (d & 1) << pos
+        dn |= ((d >> 1) & 1) << pos
+    inter = 0
+    for i in range(4):
+        inter |= ((up >> i) & 1) << (2 * i) | ((dn >> i) & 1) << (2 * i + 1)
+    assert inter == want
+
+
+# ----------------------------------------------------------------------------- spin H
+def test_paper_xor_flip_example():
+    """Section 3.3: (S+_0 S-_1 + S-_0 S+_1) = 2 (S^x S^x + S^y S^y) on bond (0, 1)."""
+    g = _golden("paper_examples.txt")
+    s_in, mask, s_out = (int(x) for x in g["xor_flip"])
+    assert s_in ^ mask == s_out
+    spec = wl.ModelSpec(kind=wl.SPIN, n_sites=4, couplings=[(0, 1, np.diag([2.0, 2.0, 0.0]))])
+    H = oracle.dense_H(spec)
+    col = H[:, s_in]
+    assert abs(col[s_out] - 1.0) < 1e-15
+    assert np.count_nonzero(np.abs(col) > 1e-15) == 1
+    zero = int(g["xor_zero"][0])
+    assert np.all(np.abs(H[:, zero]) < 1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_spin_elements_vs_kronecker(seed):
+    spec = wl.random_spin_model(5, 7, seed, complex_=True, fields=True)
+    H = oracle.dense_H(spec)
+    Href = _indep.dense_spin(spec)
+    assert np.max(np.abs(H - Href)) < 1e-13
+
+
+def test_spin_field_y_sign():
+    """-h S^y on one site: <up|H|dn> = -h <up|S^y|dn> = -h (-i/2) = i h / 2."""
+    h = 0.3
+    spec = wl.ModelSpec(kind=wl.SPIN, n_sites=1, fields=[(0, (0.0, h, 0.0))])
+    H = oracle.dense_H(spec)
+    assert abs(H[1, 0] - 1j * h / 2) < 1e-15 and abs(H[0, 1] + 1j * h / 2) < 1e-15
+
+
+@pytest.mark.parametrize("n,k", [(6, 3), (7, 2), (6, 0)])
+def test_spin_sector_vs_kronecker(n, k):
+    spec = wl.random_xxz_model(n, 9, seed=10 + n + k).with_basis(wl.BASIS_SZ, k)
+    H = oracle.dense_H(spec)
+    idx = _indep.spin_sector_indices(n, k)
+    Href = _indep.dense_spin(spec.with_basis(wl.BASIS_FULL))[np.ix_(idx, idx)]
+    assert H.shape == Href.shape
+    assert np.max(np.abs(H - Href)) < 1e-13
+
+
+def test_sector_mismatch_is_reported():
+    spec = wl.random_spin_model(4, 3, seed=3).with_basis(wl.BASIS_SZ, 2)
+    with pytest.raises(oracle.OracleError):
+        oracle.apply_H(spec, np.ones(6))
+
+
+# ----------------------------------------------------------------------------- Hubbard H
+@pytest.mark.parametrize("seed", [0, 1])
+def test_hubbard_elements_vs_jordan_wigner(seed):
+    spec = wl.random_hubbard_model(3, 6, seed, complex_=True)
+    H = oracle.dense_H(spec)
+    Href = _indep.dense_hubbard(spec)
+    assert np.max(np.abs(H - Href)) < 1e-13
+
+
+@pytest.mark.parametrize("na,nb", [(2, 1), (1, 1), (3, 0)])
+def test_hubbard_sector_vs_jordan_wigner(na, nb):
+    spec = wl.random_hubbard_model(3, 7, seed=5, complex_=True).with_basis(wl.BASIS_NUMBER, na, nb)
+    H = oracle.dense_H(spec)
+    idx = _indep.hubbard_sector_indices(3, na, nb)
+    Href = _indep.dense_hubbard(spec.with_basis(wl.BASIS_FULL))[np.ix_(idx, idx)]
+    assert np.max(np.abs(H - Href)) < 1e-13
+
+
+def test_hubbard_interleaved_order_is_a_gauge():
+    """The paper's per-site interleaving of up/down modes (section 3.1) orders the modes
+    differently; the spectrum must not change."""
+    spec = wl.random_hubbard_model(3, 6, seed=7, complex_=False)
+    ev_ours = np.linalg.eigvalsh(oracle.dense_H(spec))
+    ev_inter = np.linalg.eigvalsh(_indep.dense_hubbard(spec, mode_of=lambda i, s: 2 * i + s))
+    assert np.max(np.abs(ev_ours - ev_inter)) < 1e-12
+
+
+def test_hop_sign_literal():
+    # modes: up 0..3 = 0..3, dn 0..3 = 4..7; <bra| c+_p c_q |ket>
+    # bra has up sites {0, 2}; c+_2 c_0 (p=2, q=0): ket has up {0, 1}... choose explicitly
+    # ket = up {0, 1}, bra = up {1, 2}: c_0 on ket: 0 occupied before -> +; c+_2 on up{1}: 1 before -> -
+    assert oracle.hop_sign(0b0110, 0, 4, 2, 0) == -1
+    assert oracle.hop_sign(0b0110, 0, 4, 0, 2) == 0  # bra must have mode p occupied
+
+
+# ----------------------------------------------------------------------------- closed forms
+def _e0(spec):
+    return np.linalg.eigvalsh(oracle.dense_H(spec))[0]
+
+
+def test_heisenberg_4ring_e0():
+    assert abs(_e0(wl.heisenberg_ring(4)) - (-2.0)) < 1e-12
+
+
+def test_two_site_hubbard_e0():
+    t, U = 1.0, 8.0
+    spec = wl.hubbard(2, [(0, 1)], t, U).with_basis(wl.BASIS_NUMBER, 1, 1)
+    want = (U - math.sqrt(U * U + 16 * t * t)) / 2
+    assert abs(_e0(spec) - want) < 1e-12
+
+
+@pytest.mark.parametrize("na,nb,want", [(3, 3, -8.0), (2, 3, -7.0), (2, 2, -6.0), (1, 0, -2.0)])
+def test_free_fermion_ring_band_sum(na, nb, want):
+    # 6-site ring, U = 0: single-particle levels -2 cos(2 pi k / 6) = -2, -1, -1, 1, 1, 2
+    spec = wl.hubbard_ring(6, 1.0, 0.0).with_basis(wl.BASIS_NUMBER, na, nb)
+    assert abs(_e0(spec) - want) < 1e-12
+
+
+def test_free_fermion_4x4_one_species_lanczos():
+    """4x4 torus, 8 fermions of one species, U = 0: the sum of the 8 lowest levels of
+    -2(cos kx + cos ky) is -4 - 2*(-... ) = -12."""
+    lv = sorted(-2 * (math.cos(2 * math.pi * a / 4) + math.cos(2 * math.pi * b / 4)) for a in range(4) for b in range(4))
+    want = sum(lv[:8])
+    assert abs(want + 12.0) < 1e-12
+    spec = wl.hubbard_square(4, 4, 1.0, 0.0).with_basis(wl.BASIS_NUMBER, 8, 0)
+    v0 = wl.gaussian_vector(1, oracle.dim(spec))[:, 0]
+    a, b = oracle.lanczos(spec, v0, 120)
+    assert abs(oracle.ritz_values(a, b)[0] - want) < 1e-9
+
+
+def test_majumdar_ghosh_point():
+    n = 12
+    spec = wl.j1j2_ring(n, 1.0, 0.5)
+    e_sz0 = _e0(spec.with_basis(wl.BASIS_SZ, n // 2))
+    assert abs(e_sz0 - (-3 * n / 8)) < 1e-10
+    assert abs(_e0(spec.with_basis(wl.BASIS_SZ, n)) - n * 1.5 / 4) < 1e-12
+    # one magnon: E(k) = N (J1 + J2)/4 + J1 (cos k - 1) + J2 (cos 2k - 1)
+    ev = np.linalg.eigvalsh(oracle.dense_H(spec.with_basis(wl.BASIS_SZ, n - 1)))
+    k = 2 * np.pi * np.arange(n) / n
+    want = np.sort(n * 1.5 / 4 + (np.cos(k) - 1) + 0.5 * (np.cos(2 * k) - 1))
+    assert np.max(np.abs(ev - want)) < 1e-12
+
+
+def test_heisenberg_ring12_sector_minima():
+    spec = wl.heisenberg_ring(12)
+    mins = [_e0(spec.with_basis(wl.BASIS_SZ, k)) for k in range(13)]
+    assert abs(mins[6] - (-5.387390917445)) < 1e-9
+    assert abs(mins[0] - 3.0) < 1e-12 and abs(mins[12] - 3.0) < 1e-12
+    for k in range(13):
+        assert abs(mins[k] - mins[12 - k]) < 1e-10
+    # ferromagnetic bound and monotonic in |Sz|
+    for k in range(6):
+        assert mins[k] >= mins[k + 1] - 1e-10
+
+
+# ----------------------------------------------------------------------------- Lanczos
+def test_lanczos_ground_state_vs_dense():
+    spec = wl.heisenberg_ring(10).with_basis(wl.BASIS_SZ, 5)
+    v0 = wl.gaussian_vector(3, oracle.dim(spec))[:, 0]
+    a, b = oracle.lanczos(spec, v0, 80)
+    H = oracle.dense_H(spec)
+    ev = np.linalg.eigvalsh(H)
+    assert abs(oracle.ritz_values(a, b)[0] - ev[0]) < 1e-10
+    # first coefficients straight from the dense matrix
+    v = v0 / np.linalg.norm(v0)
+    hv = H @ v
+    a0 = np.vdot(v, hv).real
+    assert abs(a[0] - a0) < 1e-12
+    assert abs(b[0] - np.linalg.norm(hv - a0 * v)) < 1e-12
+
+
+def test_lanczos_shift_invariance():
+    """Section 3.4: the Krylov space of H + a I equals that of H, so alpha shifts by a and
+    beta is unchanged.  A uniform chemical potential at fixed particle number is such a
+    shift (a = -mu (N_up + N_dn))."""
+    base = wl.hubbard_ring(6, 1.0, 4.0).with_basis(wl.BASIS_NUMBER, 3, 2)
+    mu = 0.7
+    shifted = wl.ModelSpec(**{**base.__dict__, "chem_pot": [(i, mu) for i in range(6)]})
+    v0 = wl.gaussian_vector(4, oracle.dim(base))[:, 0]
+    a1, b1 = oracle.lanczos(base, v0, 30)
+    a2, b2 = oracle.lanczos(shifted, v0, 30)
+    assert np.max(np.abs((a2 - a1) - (-mu * 5))) < 1e-12
+    assert np.max(np.abs(b2 - b1)) < 1e-12
+
+
+def test_lanczos_breakdown_on_one_state_sector():
+    spec = wl.j1j2_ring(8, 1.0, 0.5).with_basis(wl.BASIS_SZ, 8)
+    a, b = oracle.lanczos(spec, np.ones(1), 10)
+    assert len(a) == 1 and abs(a[0] - 8 * 1.5 / 4) < 1e-14 and b[0] < 1e-14
+
+
+def test_lanczos_eigenvector_second_pass():
+    spec = wl.heisenberg_ring(10).with_basis(wl.BASIS_SZ, 5)
+    v0 = wl.gaussian_vector(5, oracle.dim(spec))[:, 0]
+    a, b = oracle.lanczos(spec, v0, 60)
+    e0 = oracle.ritz_values(a, b)[0]
+    x = oracle.lanczos_vector(spec, v0, a, b, oracle.ritz_vector(a, b, 0))
+    hx = oracle.apply_H(spec, x)
+    xx = np.vdot(x, x).real
+    erq = np.vdot(x, hx).real / xx
+    assert abs(erq - e0) < 1e-9
+    assert np.linalg.norm(hx - erq * x) / math.sqrt(xx) < 1e-5
+
+
+# ----------------------------------------------------------------------------- TPQ
+def test_tpq_matches_matrix_power():
+    spec = wl.kitaev_honeycomb(2, 2, -1.0, 0.05)
+    D = oracle.dim(spec)
+    psi0 = wl.gaussian_vector(7, D, complex_=True)[:, 0]
+    K, l = 12, 1.0
+    u, h2, nrm, psiK = oracle.tpq(spec, psi0, K, l, want_state=True)
+    H = _indep.dense_spin(spec)
+    A = l * np.eye(D) - H / spec.n_sites
+    ref = np.linalg.matrix_power(A, K) @ psi0
+    ref /= np.linalg.norm(ref)
+    assert np.max(np.abs(psiK - ref)) < 1e-12
+    p = psi0 / np.linalg.norm(psi0)
+    assert abs(u[0] - np.vdot(p, H @ p).real / spec.n_sites) < 1e-13
+    assert abs(h2[0] - np.linalg.norm(H @ p) ** 2 / spec.n_sites ** 2) < 1e-13
+    assert abs(nrm[0] - np.linalg.norm(A @ p)) < 1e-13
+
+
+def test_kitaev_trace_h2_closed_form():
+    """Tr H^2 / D = sum_bonds K^2/16 + sum_sites sum_a h_a^2 / 4 (distinct Pauli strings are
+    trace-orthogonal), and Tr H = 0.  Pins the honeycomb geometry (12 bonds on 2x2 cells)."""
+    K, h = -1.0, 0.05
+    spec = wl.kitaev_honeycomb(2, 2, K, h)
+    assert len(spec.couplings) == 12
+    H = oracle.dense_H(spec)
+    D = H.shape[0]
+    assert abs(np.trace(H).real / D) < 1e-14
+    want = 12 * K * K / 16 + 8 * 3 * h * h / 4
+    assert abs(np.trace(H @ H).real / D - want) < 1e-12
+    assert len(wl.kitaev_honeycomb(4, 3, K, h).couplings) == 36
+
+
+def test_tpq_vs_canonical_ensemble():
+    """The paper's own validation (section 5.1): TPQ energies at beta_k agree with the
+    canonical ensemble from full diagonalization within the sample-to-sample spread."""
+    spec = wl.kitaev_honeycomb(2, 2, -1.0, 0.05)
+    Ns = spec.n_sites
+    ev = np.linalg.eigvalsh(oracle.dense_H(spec))
+    D = len(ev)
+    K, l, R = 60, 1.0, 8
+    us = []
+    for r in range(R):
+        psi0 = wl.gaussian_vector(100 + r, D, complex_=True)[:, 0]
+        u, _, _ = oracle.tpq(spec, psi0, K, l)
+        us.append(u)
+    us = np.array(us)
+    for k in (10, 30, 59):
+        uk = us[:, k]
+        beta = np.mean(2 * k / Ns / (l - uk))
+        w = np.exp(-beta * (ev - ev[0]))
+        e_can = np.sum(w * ev) / np.sum(w) / Ns
+        assert abs(np.mean(uk) - e_can) < 4 * np.std(uk) + 2e-3
+
+
+# ----------------------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    kat = _golden("philox4x32_10_kat.txt")
+    for name, vals in kat.items():
+        v = [int(x, 16) for x in vals]
+        ctr, key, want = v[0:4], v[4:6], v[6:10]
+        assert oracle.philox4x32_10(ctr, key).tolist() == want, name
+
+
+def test_gaussian_moments():
+    idx = np.arange(200000, dtype=np.uint64)
+    g = oracle.gauss_at(123432, idx, complex_=True)
+    for part in (g.real, g.imag):
+        assert abs(part.mean()) < 0.01 and abs(part.var() - 1.0) < 0.01
+        assert abs(np.mean(part ** 4) - 3.0) < 0.05
