@@ -1,0 +1,282 @@
+"""Benchmark of the Lanczos hot path on one GB300 (or N independent replicas).
+
+Workload (default): the half-filled 4x4 periodic Hubbard model, t = 1, U = 8, N_up = N_dn = 8,
+sector dimension C(16,8)^2 = 165,636,900, real fp64 vectors, 200 Lanczos steps from a seeded
+Gaussian start (section 3.4).  One benchmark step is one complete hphi_lanczos_run: start
+vector -> 200 fused H v / vector-update steps -> fp64 tridiagonal eigensolve -> energies on
+the host.  Metric: H v throughput of the Lanczos loop in Gelem/s (basis rows x Lanczos steps
+per second); steps/s and the fraction of HBM / fp64 roofline are reported beside it.
+
+Timing: W untimed warm-up runs, then K runs between CUDA events on the launching stream,
+barrier + synchronize on both sides, max over ranks.  Vectors (1.33 GB each) exceed the
+129 MB L2, so no flush is needed.  `--impl reference` times the CPU oracle instead (the
+only other place this file runs oracle code), on a bounded slice of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "H·v Gelem/s & %HBM peak; Lanczos/mTPQ steps/s, FP64 vs mixed+batched at ΔE"
+FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TINST = 0.625   # nominal GB300 fp64 rate, 1.25 TFLOP/s = 0.625 T FMA/s
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if os.environ.get("HPHI_BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def oracle_rows_per_s(spec, target_s: float = 12.0, max_rows: int = 4_000_000):
+    """Oracle H v over a slice of rows of the workload, all host cores; rows per second."""
+    import oracle
+    D = oracle.dim(spec)
+    rng = np.random.default_rng(0)
+    v = np.empty(D, dtype=np.complex128)
+    v.real = rng.standard_normal(D)
+    v.imag = 0.0
+    n = 20000
+    t0 = time.perf_counter()
+    oracle.apply_H_slice(spec, v, 0, n)
+    dt = time.perf_counter() - t0
+    n2 = int(min(max_rows, max(n, n * target_s / max(dt, 1e-6))))
+    r0 = (D - n2) // 2
+    t0 = time.perf_counter()
+    oracle.apply_H_slice(spec, v, r0, n2)
+    dt2 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    return n2 / dt2, n2, dt2, cores
+
+
+# ----------------------------------------------------------------------------- main
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1703_03637_gb300 as hp
+
+    torch.cuda.set_device(local)
+    W = wl.workload(args.workload)
+    spec, steps = W["model"], (args.lanczos_steps or W["steps"])
+    prec = hp.FP64 if args.prec == "fp64" else hp.FP32
+    m = hp.Model.from_spec(spec)
+    D = m.dim
+    seed = wl.START_SEED + rank
+    for _ in range(args.warmup):
+        m.lanczos(steps, prec=prec, seed=seed, profile=True)
+    stream = torch.cuda.current_stream()
+    clk = Clocks(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hv_ms, hv_n, launches, res = 0.0, 0, 0, None
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = m.lanczos(steps, prec=prec, seed=seed, profile=True)
+        hv_ms += res["hv_ms"]
+        hv_n += res["hv_launches"]
+        launches += res["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop() if clk else None
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    ms_step = ms / args.steps
+    rows_per_step = D * steps
+    value = world * rows_per_step * args.steps / (ms / 1e3) / 1e9
+
+    # end to end: host (pinned) start vector -> device each step, energies back to the host
+    v0_host = torch.from_numpy(wl.gaussian_vector(seed, D)[:, 0]).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        v0_dev = v0_host.to("cuda", non_blocking=True)
+        r2 = m.lanczos(steps, prec=prec, v0=v0_dev)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * rows_per_step * e2e_steps / e2e_s / 1e9, "unit": "Gelem/s",
+           "h2d_bytes_per_step": int(v0_host.numel() * v0_host.element_size()),
+           "d2h_bytes_per_step": int(8 * (2 * steps + 8 + 4))}
+
+    if rank != 0:
+        return None
+    hbm, src = peaks()
+    esz = 8 if prec == hp.FP64 else 4
+    bytes_row = 3 * esz   # fused H v + Lanczos pass 1: gather-read C once, read P, write P
+    hv_avg_ms = hv_ms / max(hv_n, 1)
+    achieved = D * bytes_row / (hv_avg_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
+            "kernel": "k_hv_hub<fused Lanczos pass 1>", "kernel_avg_ms": round(hv_avg_ms, 4),
+            "algorithmic_bytes_per_launch": D * bytes_row}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == hp.FP64 else "f32+f64acc", "data": "synthetic",
+        "config": {"workload": args.workload, "dim": D, "lanczos_steps": steps, "model": "hubbard_4x4_U8_t1",
+                   "sector": "N_up=N_dn=8", "start": "philox gaussian, seed 123432+rank",
+                   "l2": "vectors (1.33 GB) exceed L2; no flush", "parallelism": f"replicas{world}"},
+        "lanczos_steps_per_s": round(steps / (ms_step / 1e3), 2),
+        "e0": res["eig"][0], "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    if args.cpu_baseline:
+        rps, n, dt, cores = oracle_rows_per_s(spec)
+        out["cpu_baseline"] = {"value": round(rps / 1e9, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+                               "sample": f"oracle H v on {n} contiguous rows of the same sector ({dt:.1f} s, "
+                                         f"OpenMP over {cores} host threads); a Lanczos step is one such H v per row"}
+    return out
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle, as it stands, on a bounded slice of the same workload per step."""
+    if rank != 0:
+        return None
+    import oracle
+    W = wl.workload(args.workload)
+    spec = W["model"]
+    D = oracle.dim(spec)
+    rng = np.random.default_rng(0)
+    v = np.empty(D, dtype=np.complex128)
+    v.real = rng.standard_normal(D)
+    v.imag = 0.0
+    n = 300_000
+    for _ in range(args.warmup):
+        oracle.apply_H_slice(spec, v, 0, n // 10)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.apply_H_slice(spec, v, (k * n) % (D - n), n)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    val = n * args.steps / dt / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "Gelem/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "dim": D, "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(val, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+                             "sample": f"oracle H v on {n} rows per step of the {args.workload} sector"},
+            "e2e": {"value": round(val, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hubbard_4x4_8u8d")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--lanczos-steps", type=int, default=0, help="override the workload's Lanczos step count")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; other ranks exit without work
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        out = run_reference(args, world, rank)
+        if rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    world, rank, local = dist_setup(args.gpus)
+    out = run_ours(args, world, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

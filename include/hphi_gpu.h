@@ -1,0 +1,209 @@
+/*
+ * hphi_gpu.h -- C ABI of the GB300 (sm_103a) Lanczos / microcanonical-TPQ library for
+ * two-body quantum lattice models, after Kawamura et al., "Quantum lattice model solver
+ * HPhi", Comput. Phys. Commun. 217 (2017) 180.
+ *
+ * General rules for every entry point below
+ *  - Status: every function returning int returns HPHI_OK (0) or a negative HPHI_ERR_*
+ *    code; nothing is thrown across the ABI.  hphi_last_error() gives a message for the
+ *    last failure on that model.
+ *  - Ownership: the model handle, its term list, its basis tables and its solver
+ *    workspace are allocated and freed by the library (cudaMalloc on the current device).
+ *    Vectors passed to hphi_apply_H / hphi_random_vector are caller-owned DEVICE buffers;
+ *    result arrays in the *_result structs are caller-owned HOST buffers.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work of a call is issued on it.  hphi_build_sector, hphi_lanczos_run and
+ *    hphi_tpq_run synchronise the stream before returning (their results are host
+ *    values); hphi_apply_H and hphi_random_vector are asynchronous.
+ *  - Vector layout: row-major [dim][nvec]; row r is basis state r (section 3.1 order, see
+ *    hphi_set_basis), nvec vectors interleaved per row.  Real models use double (or float
+ *    for HPHI_FP32); complex models use interleaved (re, im) pairs.
+ *  - Threading: a model may be used from one host thread at a time.
+ */
+#ifndef HPHI_GPU_H
+#define HPHI_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hphi_model hphi_model;
+
+/* Model kinds (section 2.3: "Spin" and "Fermion Hubbard" models). */
+enum { HPHI_SPIN_HALF = 0, HPHI_HUBBARD = 1 };
+
+/* Basis modes (section 3.1: full space, or the restricted space of fixed particle number /
+ * fixed total S^z, enumerated in ascending bit-string order). */
+enum { HPHI_BASIS_FULL = 0, HPHI_BASIS_SZ = 1, HPHI_BASIS_NUMBER = 2 };
+
+/* Vector storage precision.  HPHI_FP64: fp64 storage and arithmetic.  HPHI_FP32: fp32
+ * storage and fp32 H v, with every inner product accumulated to fp64. */
+enum { HPHI_FP64 = 0, HPHI_FP32 = 1 };
+
+enum {
+  HPHI_OK = 0,
+  HPHI_ERR_INVALID_ARG = -1,    /* bad argument, index out of range, wrong model kind      */
+  HPHI_ERR_BASIS_MISMATCH = -2, /* a term does not conserve the chosen sector             */
+  HPHI_ERR_OUT_OF_MEMORY = -3,  /* device allocation failed                               */
+  HPHI_ERR_NOT_BUILT = -4,      /* hphi_build_sector has not run since the last change    */
+  HPHI_ERR_CUDA = -5,           /* a CUDA runtime call failed (message has the details)   */
+  HPHI_ERR_UNSUPPORTED = -7     /* valid request outside what this build implements       */
+};
+
+/* ---------------------------------------------------------------- model definition */
+
+/* Creates an empty model.  kind: HPHI_SPIN_HALF (1 <= n_sites <= 63) or HPHI_HUBBARD
+ * (1 <= n_sites <= 24 per spin species).  *out receives the handle. */
+int hphi_create(hphi_model** out, int kind, int n_sites);
+
+/* Frees the model and all device memory the library allocated for it.  NULL is ignored. */
+void hphi_destroy(hphi_model* m);
+
+/* Message of the last failure on m (or of the last failed hphi_create if m is NULL). */
+const char* hphi_last_error(const hphi_model* m);
+
+/* Spin model, section 2.3 ("Spin"): adds sum_{a,b} J[3a+b] S_i^a S_j^b with a, b in
+ * {x, y, z}, i != j.  J is a row-major 3x3 host array.  Heisenberg: J = J0 * identity;
+ * Kitaev gamma-bond: a single diagonal entry. */
+int hphi_add_spin_coupling(hphi_model* m, int i, int j, const double J[9]);
+
+/* Spin model, section 2.3: adds - (h[0] S_i^x + h[1] S_i^y + h[2] S_i^z)  (the paper's
+ * -h S^z - Gamma S^x generalised to any direction). */
+int hphi_add_spin_field(hphi_model* m, int i, const double h[3]);
+
+/* Hubbard model, section 2.3 ("Fermion Hubbard"): adds - t c+_{i s} c_{j s} - conj(t)
+ * c+_{j s} c_{i s}, i != j, spin s = 0 (up) or 1 (down).  Fermion sign convention: modes
+ * are ordered (up 0 .. N-1, down 0 .. N-1) (Jordan-Wigner order). */
+int hphi_add_hopping(hphi_model* m, int i, int j, int spin, double t_re, double t_im);
+
+/* Hubbard: adds U n_{i up} n_{i dn}. */
+int hphi_add_onsite_U(hphi_model* m, int i, double U);
+
+/* Hubbard: adds V n_i n_j (i != j), n_i = n_{i up} + n_{i dn}. */
+int hphi_add_density(hphi_model* m, int i, int j, double V);
+
+/* Hubbard: adds - mu n_i. */
+int hphi_add_chemical_potential(hphi_model* m, int i, double mu);
+
+/* Selects the basis (section 3.1).  Spin: HPHI_BASIS_FULL (all 2^N configurations, row r
+ * is configuration r, bit i = site i, bit 1 = up) or HPHI_BASIS_SZ with a = number of up
+ * spins (rows = configurations with popcount a, ascending).  Hubbard: HPHI_BASIS_FULL
+ * (row = dn * 2^N + up) or HPHI_BASIS_NUMBER with a = N_up, b = N_dn (row = rank(dn) *
+ * C(N, a) + rank(up)).  Invalidates previously built tables. */
+int hphi_set_basis(hphi_model* m, int basis, int a, int b);
+
+/* Compiles the term list (section 3.3: diagonal folded into integer bit counts per
+ * coefficient class; off-diagonal terms as XOR masks with phase tables), checks that
+ * every term conserves the sector (HPHI_ERR_BASIS_MISMATCH otherwise), and builds the
+ * two-dimensional rank tables of the restricted space on the device (section 3.1, the
+ * split-half "two-dimensional search").  *dim_out (may be NULL) receives the dimension. */
+int hphi_build_sector(hphi_model* m, int64_t* dim_out, void* stream);
+
+/* Dimension of the built basis, or a negative status. */
+int64_t hphi_dim(const hphi_model* m);
+
+/* 1 if H has complex elements (J^{xy}-type couplings, h_y fields or complex hopping). */
+int hphi_is_complex(const hphi_model* m);
+
+/* Basis decode on the device: states[k] = configuration of row r0 + k, k < n (spin: the
+ * bit string; Hubbard: up | (dn << 32)).  states: device uint64_t[n]. */
+int hphi_basis_states(hphi_model* m, int64_t r0, int64_t n, uint64_t* states, void* stream);
+
+/* Basis rank on the device: ranks[k] = row of configuration states[k] (same encoding as
+ * hphi_basis_states), or -1 if it is outside the basis.  Device arrays of length n. */
+int hphi_basis_ranks(hphi_model* m, const uint64_t* states, int64_t n, int64_t* ranks, void* stream);
+
+/* ---------------------------------------------------------------- H v (section 3.3) */
+
+/* w = H v for nvec interleaved vectors.  v, w: device buffers [dim][nvec] of the model's
+ * scalar type in precision prec (HPHI_FP64 or HPHI_FP32); v and w must not overlap.
+ * Matrix-free: every element is generated on the fly from the bit strings. */
+int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void* stream);
+
+/* ---------------------------------------------------------------- start vectors */
+
+/* Fills v (device, [dim][nvec], precision prec) with standard-normal numbers from the
+ * counter-based generator Philox4x32-10 (Salmon et al., SC'11) and the Box-Muller
+ * transform: element e = r * nvec + c uses counter (e mod 2^32, e >> 32, 0, 0) and key
+ * (seed mod 2^32, seed >> 32); the four output words give two 53-bit uniforms
+ * u_a = ((w0 << 21) | (w1 >> 11)) + 0.5) / 2^53 and u_b likewise from w2, w3; the real part
+ * is sqrt(-2 ln u_a) cos(2 pi u_b) and the imaginary part (complex models) the sine.
+ * This replaces the paper's dSFMT draws (appendix A.2 / A.4), whose stream depends on the
+ * process count. */
+int hphi_random_vector(hphi_model* m, void* v, int nvec, int prec, uint64_t seed, void* stream);
+
+/* Raw Philox4x32-10 on the device: for k < n, out[4k..4k+3] = Philox(ctr[4k..4k+3],
+ * key[2k..2k+1]).  All pointers are device arrays. */
+int hphi_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream);
+
+/* ---------------------------------------------------------------- Lanczos (section 3.4) */
+
+typedef struct {
+  int steps;           /* m: number of H v products (size of T_m); 1..4096               */
+  int prec;            /* HPHI_FP64 or HPHI_FP32                                         */
+  uint64_t seed;       /* start vector seed if v0 == NULL (hphi_random_vector, nvec = 1) */
+  const void* v0;      /* optional device start vector [dim], always fp64 (complex128 for
+                          complex models); it is normalised internally                   */
+  int n_eig;           /* lowest eigenvalues of T_m to return, 1..8                      */
+  int refine;          /* 1: rebuild the Ritz vector x of the lowest eigenvalue by a second
+                          Lanczos pass (section 3.4) in fp64 and return the fp64 Rayleigh
+                          quotient, residual |Hx - Ex| / |x| and variance (appendix A.3)   */
+  double breakdown;    /* stop when beta_{k+1} <= breakdown * max(1, |alpha_k|); 0 -> 1e-13 */
+  int profile;         /* 1: time every fused H v launch with CUDA events (hv_ms below)   */
+} hphi_lanczos_params;
+
+typedef struct {
+  int steps_done;      /* steps actually taken (< steps only at breakdown)               */
+  double* alpha;       /* caller host array [steps] or NULL: alpha_0 .. alpha_{m-1}      */
+  double* beta;        /* caller host array [steps] or NULL: beta_1 .. beta_m            */
+  double eig[8];       /* lowest n_eig eigenvalues of T_m, ascending                     */
+  double e_refined;    /* refine = 1: <x|H|x> / <x|x> in fp64                            */
+  double residual;     /* refine = 1: |H x - E x| / |x|                                   */
+  double variance;     /* refine = 1: <H^2> - <H>^2 for x / |x|                            */
+  float device_ms;     /* device time of the Lanczos loop (CUDA events on the stream)     */
+  float hv_ms;         /* profile = 1: summed device time of the fused H v launches       */
+  int hv_launches;     /* number of fused H v launches timed in hv_ms                      */
+  int kernel_launches; /* CUDA kernels this call launched                                   */
+} hphi_lanczos_result;
+
+/* Lanczos recurrence of section 3.4 (alpha_k = (H v_k, v_k), w = H v_k - beta_k v_{k-1} -
+ * alpha_k v_k, beta_{k+1} = |w|, v_{k+1} = w / |w|) on the device, with the H v product
+ * fused with the vector update and every reduction accumulated in fp64; then the lowest
+ * eigenvalues of the tridiagonal T_m by Sturm bisection in fp64 on the device. */
+int hphi_lanczos_run(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_result* r, void* stream);
+
+/* ---------------------------------------------------------------- mTPQ (section 3.5) */
+
+typedef struct {
+  int n_starts;        /* independent random initial vectors, run interleaved: 1..256   */
+  int steps;           /* K: number of multiplications by (l - H / N_s)                  */
+  double l;            /* the constant l                                                  */
+  double n_s;          /* N_s (0 -> number of sites)                                       */
+  uint64_t seed;       /* start vectors: hphi_random_vector(seed, nvec = n_starts)        */
+  const void* psi0;    /* optional device [dim][n_starts] fp64 start block (complex128 for
+                          complex models); normalised internally per start               */
+  int prec;            /* HPHI_FP64 or HPHI_FP32 (fp32 storage, fp64 norms and energies)   */
+} hphi_tpq_params;
+
+typedef struct {
+  double* u;           /* host [steps][n_starts]: u_k = <psi_k|H|psi_k> / N_s             */
+  double* h2;          /* host [steps][n_starts]: <psi_k|H^2|psi_k> / N_s^2              */
+  double* norm;        /* host [steps][n_starts]: |(l - H/N_s) psi_k|                     */
+  float device_ms;     /* device time of the TPQ loop                                      */
+  int kernel_launches; /* CUDA kernels this call launched                                   */
+} hphi_tpq_result;
+
+/* Microcanonical TPQ (section 3.5): psi_{k+1} = (l - H/N_s) psi_k / |(l - H/N_s) psi_k| for
+ * all starts at once, one fused pass per step (H psi, the update, and the fp64 per-start
+ * reductions <psi|H psi>, |H psi|^2 and |psi_{k+1}|^2).  Record k describes psi_k, the state
+ * the (k+1)-th multiplication acts on, for k = 0 .. steps-1; the inverse temperature is
+ * beta_k = (2k / N_s) / (l - u_k). */
+int hphi_tpq_run(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* r, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPHI_GPU_H */

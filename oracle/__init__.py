@@ -67,7 +67,7 @@ def lib():
             L.or_philox4x32_10.argtypes = [P, P, P]
             L.or_gauss_pair.argtypes = [u64, u64, P]
             L.or_gauss_at.argtypes = [u64, P, i64, i32, P]
-            L.or_apply_H_rows_philox.argtypes = [P, P, i64, u64, i32, P]
+            L.or_apply_H_rows_philox.argtypes = [P, P, i64, u64, i32, i32, i32, P]
             L.or_lanczos.argtypes = [P, P, i32, f64, P, P]
             L.or_lanczos_vector.argtypes = [P, P, i32, P, P, P, P]
             L.or_tpq.argtypes = [P, P, i32, f64, f64, P, P, P, P]
@@ -179,11 +179,12 @@ def apply_H_slice(spec, v, r0: int, nrows: int) -> np.ndarray:
     return w
 
 
-def apply_H_rows_philox(spec, rows, seed: int, complex_: bool) -> np.ndarray:
+def apply_H_rows_philox(spec, rows, seed: int, complex_: bool, nvec: int = 1, col: int = 0) -> np.ndarray:
+    """Rows of H v where v [dim][nvec] is the Philox-Gaussian vector of `seed` (column `col`)."""
     om = OracleModel(spec)
     rows = np.ascontiguousarray(rows, dtype=np.uint64)
     out = np.zeros(len(rows), dtype=np.complex128)
-    _check(lib().or_apply_H_rows_philox(om.ref, _ptr(rows), len(rows), seed, int(complex_), _ptr(out)),
+    _check(lib().or_apply_H_rows_philox(om.ref, _ptr(rows), len(rows), seed, int(complex_), nvec, col, _ptr(out)),
            "apply_H_rows_philox")
     return out
 

@@ -443,8 +443,10 @@ void or_gauss_at(uint64_t seed, const uint64_t* idx, int64_t n, int is_complex, 
 // Sampled rows of H v where v is the (unnormalised) Philox-Gaussian vector of `seed`:
 // every element a row needs is regenerated from its index, so the full vector never has
 // to exist on the host.  rows: [nrows]; out: complex128 [nrows].
+// Vector layout [dim][nvec]: element (row, c) is Philox element row * nvec + c; column c of
+// H v is evaluated.
 int or_apply_H_rows_philox(const or_model* m, const uint64_t* rows, int64_t nrows, uint64_t seed,
-                           int is_complex, double* out_ri) {
+                           int is_complex, int nvec, int c, double* out_ri) {
   Basis B;
   if (!B.init(m)) return -1;
   int bad = 0;
@@ -453,7 +455,7 @@ int or_apply_H_rows_philox(const or_model* m, const uint64_t* rows, int64_t nrow
     cplx acc = 0.0;
     auto f = [&](uint64_t col, cplx el) {
       double g0, g1;
-      gauss_pair(seed, col, &g0, &g1);
+      gauss_pair(seed, col * (uint64_t)nvec + (uint64_t)c, &g0, &g1);
       acc += el * cplx(g0, is_complex ? g1 : 0.0);
     };
     const bool ok = B.kind == 0 ? spin_row_elems(m, B, rows[k], f) : hub_row_elems(m, B, rows[k], f);

@@ -1,0 +1,1021 @@
+// C ABI of the library: model definition, term compilation (section 3.3), sector build
+// (section 3.1) and the Lanczos (section 3.4) / mTPQ (section 3.5) drivers.  Host code
+// only arranges work; every step of the method runs in the kernels of k_*.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <complex>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using cplx = std::complex<double>;
+
+namespace {
+
+struct Coupling { int i, j; double J[9]; };
+struct Field { int i; double h[3]; };
+struct Hop { int i, j, spin; double tr, ti; };
+struct Onsite { int i; double U; };
+struct Density { int i, j; double V; };
+struct Chem { int i; double mu; };
+
+// device buffer owned by the model
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  hphi::Status ensure(size_t b) {
+    if (b <= bytes && p) return {};
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return {e == cudaErrorMemoryAllocation ? HPHI_ERR_OUT_OF_MEMORY : HPHI_ERR_CUDA,
+              std::string("cudaMalloc(") + std::to_string(b) + " bytes): " + cudaGetErrorString(e)};
+    }
+    bytes = b;
+    return {};
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+template <class T>
+hphi::Status upload(DBuf& b, const std::vector<T>& v, cudaStream_t st) {
+  hphi::Status s = b.ensure(sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (s.code) return s;
+  if (!v.empty()) HPHI_CUDA_TRY(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return {};
+}
+
+uint64_t binom_host(int n, int k) {
+  if (k < 0 || k > n || n < 0) return 0;
+  if (k > n - k) k = n - k;
+  unsigned __int128 r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (unsigned)(n - k + i) / (unsigned)i;
+  return (uint64_t)r;
+}
+
+// canonical class coefficient: rotate by a power of i into {re > 0, im >= 0}; returns the
+// phase code p with el = coef * i^(p-1)  (1: +1, 2: +i, 3: -1, 4: -i)
+int canon(cplx el, cplx* coef) {
+  cplx c = el;
+  for (int k = 0; k < 4; ++k) {
+    if (c.real() > 0 && c.imag() >= 0) {
+      *coef = c;
+      return k + 1;
+    }
+    c = c * cplx(0, -1);  // el = c * i^k
+  }
+  *coef = el;
+  return 1;
+}
+
+// spin single-site element <b|S^a|b'>, b' the only ket bit with a non-zero value
+cplx site_el(int a, int b, int* kb) {
+  if (a == 2) { *kb = b; return cplx(b ? 0.5 : -0.5, 0); }
+  *kb = 1 - b;
+  if (a == 0) return cplx(0.5, 0);
+  return b ? cplx(0, -0.5) : cplx(0, 0.5);
+}
+
+struct Workspace {
+  DBuf vecA, vecB, x, partials, scal, work;
+};
+
+}  // namespace
+
+struct hphi_model {
+  int kind = 0, n_sites = 0;
+  int basis = HPHI_BASIS_FULL, a = 0, b = 0;
+  std::vector<Coupling> coup;
+  std::vector<Field> field;
+  std::vector<Hop> hop;
+  std::vector<Onsite> onsite;
+  std::vector<Density> dens;
+  std::vector<Chem> chem;
+  bool built = false;
+  bool cplx_model = false;
+  int64_t dim = 0;
+  std::string err;
+  int device = 0;
+  // device data
+  DBuf d_entries, d_cls, d_lin, d_pairs, d_pcoef, d_hi_off, d_lo_rank, d_lo_list, d_lo_off;
+  hphi::SpinDev sdev{};
+  hphi::HubDev hdev{};
+  Workspace ws;
+};
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_err;
+
+int fail(hphi_model* m, int code, const std::string& msg) {
+  if (m) m->err = msg;
+  else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_err = msg;
+  }
+  return code;
+}
+
+int fail(hphi_model* m, const hphi::Status& s) { return fail(m, s.code, s.msg); }
+
+// ------------------------------------------------------------------ spin term compiler
+struct ClassTable {
+  std::vector<cplx> coefs;
+  int get(cplx c) {
+    for (size_t k = 0; k < coefs.size(); ++k)
+      if (coefs[k] == c) return (int)k;
+    coefs.push_back(c);
+    return (int)coefs.size() - 1;
+  }
+};
+
+hphi::Status compile_spin(hphi_model* m, cudaStream_t st) {
+  const int N = m->n_sites;
+  const bool sector = (m->basis == HPHI_BASIS_SZ);
+  // diagonal decomposition: c0 + sum_i lin_i b_i + sum_pairs quad b_i b_j
+  double c0 = 0.0;
+  std::vector<double> lin(N, 0.0);
+  std::map<std::pair<int, int>, double> quad;
+  struct Pat { uint64_t mask; int i, j; cplx el[4]; };  // el indexed by b_i + 2 b_j
+  std::vector<Pat> pats;
+  bool cplx_model = false;
+
+  // merge couplings on the same (unordered) pair
+  std::map<std::pair<int, int>, std::array<std::array<cplx, 4>, 4>> bond_el;  // [pattern fi+2fj][b_i+2b_j]
+  for (const Coupling& c : m->coup) {
+    const int i = c.i, j = c.j;
+    auto key = std::make_pair(i, j);
+    auto& E = bond_el[key];
+    for (int bi = 0; bi < 2; ++bi)
+      for (int bj = 0; bj < 2; ++bj)
+        for (int x = 0; x < 3; ++x)
+          for (int y = 0; y < 3; ++y) {
+            const double J = c.J[3 * x + y];
+            if (J == 0.0) continue;
+            int ki, kj;
+            const cplx ei = site_el(x, bi, &ki), ej = site_el(y, bj, &kj);
+            const int pat = (ki ^ bi) + 2 * (kj ^ bj);
+            E[pat][bi + 2 * bj] += J * ei * ej;
+          }
+  }
+  for (auto& kv : bond_el) {
+    const int i = kv.first.first, j = kv.first.second;
+    auto& E = kv.second;
+    // diagonal pattern
+    const double d00 = E[0][0].real(), d10 = E[0][1].real(), d01 = E[0][2].real(), d11 = E[0][3].real();
+    c0 += d00;
+    lin[i] += d10 - d00;
+    lin[j] += d01 - d00;
+    const double q = d11 - d10 - d01 + d00;
+    if (q != 0.0) quad[std::make_pair(std::min(i, j), std::max(i, j))] += q;
+    for (int pat = 1; pat < 4; ++pat) {
+      Pat p{};
+      p.mask = ((pat & 1) ? (1ull << i) : 0ull) | ((pat & 2) ? (1ull << j) : 0ull);
+      p.i = i;
+      p.j = j;
+      bool any = false;
+      for (int s = 0; s < 4; ++s) {
+        p.el[s] = E[pat][s];
+        if (p.el[s] != cplx(0, 0)) {
+          any = true;
+          if (p.el[s].imag() != 0.0) cplx_model = true;
+          if (sector) {
+            const int bi = s & 1, bj = s >> 1;
+            const int dpop = ((pat & 1) ? (bi ? -1 : 1) : 0) + ((pat & 2) ? (bj ? -1 : 1) : 0);
+            if (dpop != 0)
+              return {HPHI_ERR_BASIS_MISMATCH, "coupling (" + std::to_string(i) + "," + std::to_string(j) +
+                                                   ") does not conserve S^z, which the Sz basis requires"};
+          }
+        }
+      }
+      if (any) pats.push_back(p);
+    }
+  }
+  // fields: merge per site
+  std::map<int, std::array<std::array<cplx, 2>, 2>> site_el_m;  // [flip][b_i]
+  for (const Field& f : m->field) {
+    auto& E = site_el_m[f.i];
+    for (int bi = 0; bi < 2; ++bi)
+      for (int x = 0; x < 3; ++x) {
+        if (f.h[x] == 0.0) continue;
+        int ki;
+        const cplx e = site_el(x, bi, &ki);
+        E[ki ^ bi][bi] += -f.h[x] * e;
+      }
+  }
+  for (auto& kv : site_el_m) {
+    const int i = kv.first;
+    auto& E = kv.second;
+    c0 += E[0][0].real();
+    lin[i] += E[0][1].real() - E[0][0].real();
+    Pat p{};
+    p.mask = 1ull << i;
+    p.i = i;
+    p.j = i;
+    bool any = false;
+    for (int s = 0; s < 4; ++s) {
+      const int bi = s & 1;
+      // a one-site pattern reads only b_i; index b_i + 2 b_i takes values 0 and 3
+      p.el[s] = (s == 0 || s == 3) ? E[1][bi] : cplx(0, 0);
+      if (p.el[s] != cplx(0, 0)) {
+        any = true;
+        if (p.el[s].imag() != 0.0) cplx_model = true;
+        if (sector)
+          return {HPHI_ERR_BASIS_MISMATCH,
+                  "a transverse field on site " + std::to_string(i) + " does not conserve S^z, which the Sz basis requires"};
+      }
+    }
+    if (any) pats.push_back(p);
+  }
+  // classes
+  ClassTable ct;
+  std::vector<hphi::SpinEntry> ents;
+  for (const Pat& p : pats) {
+    // split the four elements by class
+    std::map<int, uint16_t> by_cls;
+    for (int s = 0; s < 4; ++s) {
+      if (p.el[s] == cplx(0, 0)) continue;
+      cplx coef;
+      const int code = canon(p.el[s], &coef);
+      const int cls = ct.get(coef);
+      by_cls[cls] |= (uint16_t)(code << (3 * s));
+    }
+    for (auto& kv : by_cls) {
+      hphi::SpinEntry e{};
+      e.mask = p.mask;
+      e.i = (uint8_t)p.i;
+      e.j = (uint8_t)p.j;
+      e.phases = kv.second;
+      e.cls = (uint16_t)kv.first;
+      ents.push_back(e);
+    }
+  }
+  if ((int)ct.coefs.size() > hphi::kMaxClasses) return {HPHI_ERR_UNSUPPORTED, "too many distinct coupling values"};
+  if ((int)ents.size() > hphi::kMaxSpinEntries) return {HPHI_ERR_UNSUPPORTED, "too many off-diagonal terms"};
+  std::stable_sort(ents.begin(), ents.end(), [](const hphi::SpinEntry& x, const hphi::SpinEntry& y) { return x.cls < y.cls; });
+  std::vector<double2> cls;
+  for (const cplx& c : ct.coefs) cls.push_back(make_double2(c.real(), c.imag()));
+  // linear groups by value
+  std::vector<hphi::LinGroup> lg;
+  for (int i = 0; i < N; ++i) {
+    if (lin[i] == 0.0) continue;
+    bool found = false;
+    for (auto& g : lg)
+      if (g.coef == lin[i]) { g.mask |= 1ull << i; found = true; break; }
+    if (!found) lg.push_back(hphi::LinGroup{1ull << i, lin[i]});
+  }
+  if ((int)lg.size() > hphi::kMaxLin) return {HPHI_ERR_UNSUPPORTED, "too many distinct field values"};
+  // pair groups by value
+  std::vector<double> pc;
+  std::vector<hphi::PairEntry> pe;
+  for (auto& kv : quad) {
+    if (kv.second == 0.0) continue;
+    int g = -1;
+    for (size_t k = 0; k < pc.size(); ++k)
+      if (pc[k] == kv.second) g = (int)k;
+    if (g < 0) { pc.push_back(kv.second); g = (int)pc.size() - 1; }
+    pe.push_back(hphi::PairEntry{(uint8_t)kv.first.first, (uint8_t)kv.first.second, (uint16_t)g});
+  }
+  if ((int)pc.size() > hphi::kMaxPairGroups || (int)pe.size() > hphi::kMaxPairs)
+    return {HPHI_ERR_UNSUPPORTED, "too many distinct S^z S^z couplings"};
+  std::stable_sort(pe.begin(), pe.end(), [](const hphi::PairEntry& x, const hphi::PairEntry& y) { return x.grp < y.grp; });
+
+  hphi::Status s;
+  if ((s = upload(m->d_entries, ents, st)).code) return s;
+  if ((s = upload(m->d_cls, cls, st)).code) return s;
+  if ((s = upload(m->d_lin, lg, st)).code) return s;
+  if ((s = upload(m->d_pairs, pe, st)).code) return s;
+  if ((s = upload(m->d_pcoef, pc, st)).code) return s;
+  hphi::SpinDev& d = m->sdev;
+  d = hphi::SpinDev{};
+  d.n_sites = N;
+  d.sector = sector ? 1 : 0;
+  d.n_entries = (int)ents.size();
+  d.n_classes = (int)cls.size();
+  d.n_lin = (int)lg.size();
+  d.n_pairs = (int)pe.size();
+  d.n_pair_groups = (int)pc.size();
+  d.c0 = c0;
+  d.entries = m->d_entries.as<hphi::SpinEntry>();
+  d.cls_coef = m->d_cls.as<double2>();
+  d.lin = m->d_lin.as<hphi::LinGroup>();
+  d.pairs = m->d_pairs.as<hphi::PairEntry>();
+  d.pair_coef = m->d_pcoef.as<double>();
+  m->cplx_model = cplx_model;
+  return {};
+}
+
+// ------------------------------------------------------------------ Hubbard term compiler
+hphi::Status compile_hub(hphi_model* m, cudaStream_t st) {
+  const int N = m->n_sites;
+  ClassTable ct;
+  std::vector<hphi::HopEntry> hops[2];
+  bool cplx_model = false;
+  for (const Hop& h : m->hop) {
+    const cplx t(h.tr, h.ti);
+    if (h.ti != 0.0) cplx_model = true;
+    hphi::HopEntry e{};
+    e.i = (uint8_t)h.i;
+    e.j = (uint8_t)h.j;
+    e.mask = (1u << h.i) | (1u << h.j);
+    const int lo = std::min(h.i, h.j), hi = std::max(h.i, h.j);
+    e.between = (hi - lo > 1) ? (((1u << hi) - 1u) & ~((1u << (lo + 1)) - 1u)) : 0u;
+    e.cls = (uint16_t)ct.get(-t);
+    hops[h.spin ? 1 : 0].push_back(e);
+  }
+  for (int s = 0; s < 2; ++s)
+    std::stable_sort(hops[s].begin(), hops[s].end(), [](const hphi::HopEntry& x, const hphi::HopEntry& y) { return x.cls < y.cls; });
+  std::vector<hphi::HopEntry> all = hops[0];
+  all.insert(all.end(), hops[1].begin(), hops[1].end());
+  if ((int)all.size() > hphi::kMaxHops) return {HPHI_ERR_UNSUPPORTED, "too many hopping terms"};
+  if ((int)ct.coefs.size() > hphi::kMaxClasses) return {HPHI_ERR_UNSUPPORTED, "too many distinct hopping values"};
+  // diagonal groups
+  std::vector<double> Usite(N, 0.0), musite(N, 0.0);
+  for (const Onsite& o : m->onsite) Usite[o.i] += o.U;
+  for (const Chem& c : m->chem) musite[c.i] += -c.mu;
+  std::vector<hphi::LinGroup> ul, ml;
+  for (int i = 0; i < N; ++i) {
+    if (Usite[i] != 0.0) {
+      bool f = false;
+      for (auto& g : ul) if (g.coef == Usite[i]) { g.mask |= 1ull << i; f = true; break; }
+      if (!f) ul.push_back(hphi::LinGroup{1ull << i, Usite[i]});
+    }
+    if (musite[i] != 0.0) {
+      bool f = false;
+      for (auto& g : ml) if (g.coef == musite[i]) { g.mask |= 1ull << i; f = true; break; }
+      if (!f) ml.push_back(hphi::LinGroup{1ull << i, musite[i]});
+    }
+  }
+  std::map<std::pair<int, int>, double> vp;
+  for (const Density& d : m->dens) vp[std::make_pair(std::min(d.i, d.j), std::max(d.i, d.j))] += d.V;
+  std::vector<double> pc;
+  std::vector<hphi::PairEntry> pe;
+  for (auto& kv : vp) {
+    if (kv.second == 0.0) continue;
+    int g = -1;
+    for (size_t k = 0; k < pc.size(); ++k) if (pc[k] == kv.second) g = (int)k;
+    if (g < 0) { pc.push_back(kv.second); g = (int)pc.size() - 1; }
+    pe.push_back(hphi::PairEntry{(uint8_t)kv.first.first, (uint8_t)kv.first.second, (uint16_t)g});
+  }
+  if ((int)ul.size() > hphi::kMaxLin || (int)ml.size() > hphi::kMaxLin || (int)pc.size() > hphi::kMaxPairGroups ||
+      (int)pe.size() > hphi::kMaxPairs)
+    return {HPHI_ERR_UNSUPPORTED, "too many distinct diagonal terms"};
+  std::stable_sort(pe.begin(), pe.end(), [](const hphi::PairEntry& x, const hphi::PairEntry& y) { return x.grp < y.grp; });
+  std::vector<double2> cls;
+  for (const cplx& c : ct.coefs) cls.push_back(make_double2(c.real(), c.imag()));
+  std::vector<hphi::LinGroup> lin_all = ul;
+  lin_all.insert(lin_all.end(), ml.begin(), ml.end());
+  hphi::Status s;
+  if ((s = upload(m->d_entries, all, st)).code) return s;
+  if ((s = upload(m->d_cls, cls, st)).code) return s;
+  if ((s = upload(m->d_lin, lin_all, st)).code) return s;
+  if ((s = upload(m->d_pairs, pe, st)).code) return s;
+  if ((s = upload(m->d_pcoef, pc, st)).code) return s;
+  hphi::HubDev& d = m->hdev;
+  d = hphi::HubDev{};
+  d.n_sites = N;
+  d.n_up_hops = (int)hops[0].size();
+  d.n_dn_hops = (int)hops[1].size();
+  d.n_classes = (int)cls.size();
+  d.n_ulin = (int)ul.size();
+  d.n_mulin = (int)ml.size();
+  d.n_pairs = (int)pe.size();
+  d.n_pair_groups = (int)pc.size();
+  d.c0 = 0.0;
+  d.hops = m->d_entries.as<hphi::HopEntry>();
+  d.cls_coef = m->d_cls.as<double2>();
+  d.ulin = m->d_lin.as<hphi::LinGroup>();
+  d.mulin = m->d_lin.as<hphi::LinGroup>() + ul.size();
+  d.pairs = m->d_pairs.as<hphi::PairEntry>();
+  d.pair_coef = m->d_pcoef.as<double>();
+  m->cplx_model = cplx_model;
+  return {};
+}
+
+// popcount-class tables over L bits: lo_rank, lo_list, lo_list_off
+hphi::Status build_lo_tables(hphi_model* m, int L, cudaStream_t st) {
+  std::vector<uint32_t> off(L + 2, 0);
+  for (int p = 0; p <= L; ++p) off[p + 1] = off[p] + (uint32_t)binom_host(L, p);
+  hphi::Status s;
+  if ((s = upload(m->d_lo_off, off, st)).code) return s;
+  if ((s = m->d_lo_rank.ensure(sizeof(uint32_t) << L)).code) return s;
+  if ((s = m->d_lo_list.ensure(sizeof(uint32_t) << L)).code) return s;
+  return hphi::build_popcount_tables(L, m->d_lo_rank.as<uint32_t>(), m->d_lo_list.as<uint32_t>(),
+                                     m->d_lo_off.as<uint32_t>(), st);
+}
+
+hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
+  HPHI_CUDA_TRY(cudaGetDevice(&m->device));
+  hphi::Status s;
+  const int N = m->n_sites;
+  if (m->kind == HPHI_SPIN_HALF) {
+    if ((s = compile_spin(m, st)).code) return s;
+    hphi::SpinDev& d = m->sdev;
+    if (m->basis == HPHI_BASIS_FULL) {
+      if (N > 34) return {HPHI_ERR_UNSUPPORTED, "full spin basis limited to 34 sites"};
+      d.dim = (int64_t)1 << N;
+    } else {
+      if (N > 40) return {HPHI_ERR_UNSUPPORTED, "Sz sectors limited to 40 sites"};
+      const int L = (N + 1) / 2, H = N - L;
+      if ((s = build_lo_tables(m, L, st)).code) return s;
+      if ((s = m->d_hi_off.ensure(sizeof(uint64_t) << H)).code) return s;
+      if ((s = hphi::build_hi_offsets(L, H, m->a, m->d_hi_off.as<uint64_t>(), st)).code) return s;
+      d.t.L = L;
+      d.t.H = H;
+      d.t.n_ones = m->a;
+      d.t.hi_off = m->d_hi_off.as<uint64_t>();
+      d.t.lo_rank = m->d_lo_rank.as<uint32_t>();
+      d.t.lo_list = m->d_lo_list.as<uint32_t>();
+      d.t.lo_list_off = m->d_lo_off.as<uint32_t>();
+      d.dim = (int64_t)binom_host(N, m->a);
+    }
+    m->dim = d.dim;
+  } else {
+    if ((s = compile_hub(m, st)).code) return s;
+    hphi::HubDev& d = m->hdev;
+    if (m->basis == HPHI_BASIS_FULL) {
+      if (2 * N > 34) return {HPHI_ERR_UNSUPPORTED, "full Hubbard basis limited to 17 sites"};
+      d.sector = 0;
+      d.dim_up = d.dim_dn = (int64_t)1 << N;
+    } else {
+      if ((s = build_lo_tables(m, N, st)).code) return s;
+      std::vector<uint32_t> off(N + 2, 0);
+      for (int p = 0; p <= N; ++p) off[p + 1] = off[p] + (uint32_t)binom_host(N, p);
+      d.sector = 1;
+      d.n_up = m->a;
+      d.n_dn = m->b;
+      d.dim_up = (int64_t)binom_host(N, m->a);
+      d.dim_dn = (int64_t)binom_host(N, m->b);
+      d.rank = m->d_lo_rank.as<uint32_t>();
+      d.list_up = m->d_lo_list.as<uint32_t>() + off[m->a];
+      d.list_dn = m->d_lo_list.as<uint32_t>() + off[m->b];
+    }
+    d.dim = d.dim_up * d.dim_dn;
+    m->dim = d.dim;
+  }
+  HPHI_CUDA_TRY(cudaStreamSynchronize(st));
+  return {};
+}
+
+int check_built(hphi_model* m) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (!m->built) return fail(m, HPHI_ERR_NOT_BUILT, "hphi_build_sector has not run since the model last changed");
+  return HPHI_OK;
+}
+
+const void* dev_model(hphi_model* m) {
+  return m->kind == HPHI_HUBBARD ? static_cast<const void*>(&m->hdev) : static_cast<const void*>(&m->sdev);
+}
+
+int launch_grid(int64_t work) {
+  const int64_t cap = (int64_t)hphi::hv_grid(1);
+  int64_t g = (work + hphi::kThreads - 1) / hphi::kThreads;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+// Hubbard kernels iterate over (down row, chunk) items; clamp the grid to the item count
+int hv_grid_for(hphi_model* m, int nvec) {
+  if (m->kind == HPHI_HUBBARD) {
+    const int64_t chunks = (m->hdev.dim_up * nvec + hphi::kThreads - 1) / hphi::kThreads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(chunks * m->hdev.dim_dn, hphi::hv_grid(nvec)));
+  }
+  return launch_grid(m->dim * nvec);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int hphi_create(hphi_model** out, int kind, int n_sites) {
+  if (!out) return fail(nullptr, HPHI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (kind != HPHI_SPIN_HALF && kind != HPHI_HUBBARD) return fail(nullptr, HPHI_ERR_INVALID_ARG, "unknown model kind");
+  if (n_sites < 1 || (kind == HPHI_SPIN_HALF && n_sites > 63) || (kind == HPHI_HUBBARD && n_sites > 24))
+    return fail(nullptr, HPHI_ERR_INVALID_ARG, "n_sites out of range");
+  hphi_model* m = new (std::nothrow) hphi_model();
+  if (!m) return fail(nullptr, HPHI_ERR_OUT_OF_MEMORY, "host allocation failed");
+  m->kind = kind;
+  m->n_sites = n_sites;
+  *out = m;
+  return HPHI_OK;
+}
+
+void hphi_destroy(hphi_model* m) { delete m; }
+
+const char* hphi_last_error(const hphi_model* m) {
+  if (m) return m->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_err.c_str();
+}
+
+int hphi_add_spin_coupling(hphi_model* m, int i, int j, const double J[9]) {
+  if (!m || !J) return HPHI_ERR_INVALID_ARG;
+  if (m->kind != HPHI_SPIN_HALF) return fail(m, HPHI_ERR_INVALID_ARG, "spin coupling on a Hubbard model");
+  if (i < 0 || j < 0 || i >= m->n_sites || j >= m->n_sites || i == j)
+    return fail(m, HPHI_ERR_INVALID_ARG, "coupling sites out of range or equal");
+  Coupling c{i, j, {}};
+  for (int k = 0; k < 9; ++k) {
+    if (!isfinite(J[k])) return fail(m, HPHI_ERR_INVALID_ARG, "non-finite coupling");
+    c.J[k] = J[k];
+  }
+  m->coup.push_back(c);
+  m->built = false;
+  return HPHI_OK;
+}
+
+int hphi_add_spin_field(hphi_model* m, int i, const double h[3]) {
+  if (!m || !h) return HPHI_ERR_INVALID_ARG;
+  if (m->kind != HPHI_SPIN_HALF) return fail(m, HPHI_ERR_INVALID_ARG, "spin field on a Hubbard model");
+  if (i < 0 || i >= m->n_sites) return fail(m, HPHI_ERR_INVALID_ARG, "field site out of range");
+  for (int k = 0; k < 3; ++k)
+    if (!isfinite(h[k])) return fail(m, HPHI_ERR_INVALID_ARG, "non-finite field");
+  m->field.push_back(Field{i, {h[0], h[1], h[2]}});
+  m->built = false;
+  return HPHI_OK;
+}
+
+int hphi_add_hopping(hphi_model* m, int i, int j, int spin, double t_re, double t_im) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (m->kind != HPHI_HUBBARD) return fail(m, HPHI_ERR_INVALID_ARG, "hopping on a spin model");
+  if (i < 0 || j < 0 || i >= m->n_sites || j >= m->n_sites || i == j || (spin != 0 && spin != 1))
+    return fail(m, HPHI_ERR_INVALID_ARG, "hopping sites/spin out of range");
+  if (!isfinite(t_re) || !isfinite(t_im)) return fail(m, HPHI_ERR_INVALID_ARG, "non-finite hopping");
+  m->hop.push_back(Hop{i, j, spin, t_re, t_im});
+  m->built = false;
+  return HPHI_OK;
+}
+
+int hphi_add_onsite_U(hphi_model* m, int i, double U) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (m->kind != HPHI_HUBBARD) return fail(m, HPHI_ERR_INVALID_ARG, "U on a spin model");
+  if (i < 0 || i >= m->n_sites || !isfinite(U)) return fail(m, HPHI_ERR_INVALID_ARG, "bad onsite U");
+  m->onsite.push_back(Onsite{i, U});
+  m->built = false;
+  return HPHI_OK;
+}
+
+int hphi_add_density(hphi_model* m, int i, int j, double V) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (m->kind != HPHI_HUBBARD) return fail(m, HPHI_ERR_INVALID_ARG, "V on a spin model");
+  if (i < 0 || j < 0 || i >= m->n_sites || j >= m->n_sites || i == j || !isfinite(V))
+    return fail(m, HPHI_ERR_INVALID_ARG, "bad density interaction");
+  m->dens.push_back(Density{i, j, V});
+  m->built = false;
+  return HPHI_OK;
+}
+
+int hphi_add_chemical_potential(hphi_model* m, int i, double mu) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (m->kind != HPHI_HUBBARD) return fail(m, HPHI_ERR_INVALID_ARG, "mu on a spin model");
+  if (i < 0 || i >= m->n_sites || !isfinite(mu)) return fail(m, HPHI_ERR_INVALID_ARG, "bad chemical potential");
+  m->chem.push_back(Chem{i, mu});
+  m->built = false;
+  return HPHI_OK;
+}
+
+int hphi_set_basis(hphi_model* m, int basis, int a, int b) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (m->kind == HPHI_SPIN_HALF) {
+    if (basis == HPHI_BASIS_FULL) { a = 0; b = 0; }
+    else if (basis == HPHI_BASIS_SZ) {
+      if (a < 0 || a > m->n_sites) return fail(m, HPHI_ERR_INVALID_ARG, "number of up spins out of range");
+      b = 0;
+    } else return fail(m, HPHI_ERR_INVALID_ARG, "spin models take HPHI_BASIS_FULL or HPHI_BASIS_SZ");
+  } else {
+    if (basis == HPHI_BASIS_FULL) { a = 0; b = 0; }
+    else if (basis == HPHI_BASIS_NUMBER) {
+      if (a < 0 || a > m->n_sites || b < 0 || b > m->n_sites)
+        return fail(m, HPHI_ERR_INVALID_ARG, "particle numbers out of range");
+    } else return fail(m, HPHI_ERR_INVALID_ARG, "Hubbard models take HPHI_BASIS_FULL or HPHI_BASIS_NUMBER");
+  }
+  m->basis = basis;
+  m->a = a;
+  m->b = b;
+  m->built = false;
+  return HPHI_OK;
+}
+
+int hphi_build_sector(hphi_model* m, int64_t* dim_out, void* stream) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  m->built = false;
+  hphi::Status s = build_sector_impl(m, (cudaStream_t)stream);
+  if (s.code) return fail(m, s);
+  m->built = true;
+  if (dim_out) *dim_out = m->dim;
+  return HPHI_OK;
+}
+
+int64_t hphi_dim(const hphi_model* m) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (!m->built) return HPHI_ERR_NOT_BUILT;
+  return m->dim;
+}
+
+int hphi_is_complex(const hphi_model* m) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (!m->built) return HPHI_ERR_NOT_BUILT;
+  return m->cplx_model ? 1 : 0;
+}
+
+int hphi_basis_states(hphi_model* m, int64_t r0, int64_t n, uint64_t* states, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (r0 < 0 || n < 0 || r0 + n > m->dim || (n > 0 && !states)) return fail(m, HPHI_ERR_INVALID_ARG, "row range");
+  hphi::Status s = m->kind == HPHI_HUBBARD ? hphi::launch_hub_states(m->hdev, r0, n, states, (cudaStream_t)stream)
+                                           : hphi::launch_spin_states(m->sdev, r0, n, states, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
+int hphi_basis_ranks(hphi_model* m, const uint64_t* states, int64_t n, int64_t* ranks, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!states || !ranks))) return fail(m, HPHI_ERR_INVALID_ARG, "bad arrays");
+  hphi::Status s = m->kind == HPHI_HUBBARD ? hphi::launch_hub_ranks(m->hdev, states, n, ranks, (cudaStream_t)stream)
+                                           : hphi::launch_spin_ranks(m->sdev, states, n, ranks, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
+int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (!v || !w || nvec < 1 || nvec > hphi::kMaxNvec || (prec != HPHI_FP64 && prec != HPHI_FP32))
+    return fail(m, HPHI_ERR_INVALID_ARG, "apply_H: bad vectors, nvec or precision");
+  if (v == w) return fail(m, HPHI_ERR_INVALID_ARG, "apply_H: v and w must not overlap");
+  hphi::FusedArgs fa;
+  hphi::Status s = hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec,
+                                   hphi::Epi::kStore, fa, hv_grid_for(m, nvec), (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
+int hphi_random_vector(hphi_model* m, void* v, int nvec, int prec, uint64_t seed, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (!v || nvec < 1 || (prec != HPHI_FP64 && prec != HPHI_FP32)) return fail(m, HPHI_ERR_INVALID_ARG, "bad vector");
+  hphi::Status s = hphi::launch_random(v, m->dim * nvec, m->cplx_model, prec == HPHI_FP64, seed, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
+int hphi_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(nullptr, HPHI_ERR_INVALID_ARG, "bad arrays");
+  hphi::Status s = hphi::launch_philox_raw(ctr, key, out, n, (cudaStream_t)stream);
+  return s.code ? fail(nullptr, s) : HPHI_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== Lanczos driver
+namespace {
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_result* r, cudaStream_t st) {
+  const int steps = p->steps;
+  const int prec = p->prec;
+  const bool cplx = m->cplx_model;
+  const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (cplx ? 2 : 1);
+  const int64_t n_real = m->dim * (cplx ? 2 : 1);
+  const size_t vbytes = esz * (size_t)m->dim;
+  const int grid = hv_grid_for(m, 1);
+  const int vgrid = launch_grid(n_real);
+  const int pgrid = std::max(grid, vgrid);
+  Workspace& ws = m->ws;
+  hphi::Status s;
+  // the refinement's fp64 H x reuses buffer A, which must then hold an fp64 vector
+  const size_t need_a = p->refine ? std::max(vbytes, (size_t)8 * (size_t)n_real) : vbytes;
+  if ((s = ws.vecA.ensure(need_a)).code) return s;
+  if ((s = ws.vecB.ensure(vbytes)).code) return s;
+  if (p->refine && (s = ws.x.ensure(8 * (size_t)n_real)).code) return s;
+  if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * hphi::kMaxRedQ)).code) return s;
+  // scalars: alpha[m], beta[m], sig[m+1], coef[m], s[16], tri[16 + 5m], done, steps_done
+  const size_t nsc = 3 * (size_t)steps + 1 + steps + 16 + 16 + 5 * (size_t)steps + 4;
+  if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;
+  double* base = ws.scal.as<double>();
+  hphi::LzDev lz;
+  lz.alpha = base;
+  lz.beta = lz.alpha + steps;
+  lz.sig = lz.beta + steps;
+  lz.coef = lz.sig + steps + 1;
+  lz.s = lz.coef + steps;
+  lz.tri = lz.s + 16;
+  int* flags = reinterpret_cast<int*>(lz.tri + 16 + 5 * (size_t)steps);
+  lz.done = flags;
+  lz.steps_done = flags + 1;
+  HPHI_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(double) * nsc, st));
+  double* partials = ws.partials.as<double>();
+  const bool hub = m->kind == HPHI_HUBBARD;
+  const double brk = p->breakdown > 0 ? p->breakdown : 1e-13;
+
+  int launches = 0;
+  // start vector (buffer A holds C_0)
+  const double* v0 = reinterpret_cast<const double*>(p->v0);
+  if (!v0) {
+    ++launches;
+    if (prec == HPHI_FP64) {
+      if ((s = hphi::launch_random(ws.vecA.p, m->dim, cplx, true, p->seed, st)).code) return s;
+    } else {
+      if ((s = hphi::launch_random(ws.vecA.p, m->dim, cplx, false, p->seed, st)).code) return s;
+    }
+  }
+
+  std::vector<cudaEvent_t> ev;
+  auto destroy_events = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    ev.clear();
+  };
+  if (p->profile) {
+    ev.assign(2 * (size_t)steps, nullptr);
+    for (auto& e : ev) {
+      cudaError_t ce = cudaEventCreate(&e);
+      if (ce != cudaSuccess) {
+        destroy_events();
+        return {HPHI_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce)};
+      }
+    }
+  }
+  auto run_pass = [&](bool with_x) -> hphi::Status {
+    hphi::Status q;
+    launches += 2 + 4 * steps;
+    if ((q = hphi::launch_lz_init(prec, cplx, v0, ws.vecA.p, ws.vecB.p, n_real, partials, vgrid, st)).code) return q;
+    if ((q = hphi::launch_lz_init_fin(lz, partials, vgrid, st)).code) return q;
+    if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)n_real, st));
+    void* C = ws.vecA.p;
+    void* P = ws.vecB.p;
+    for (int k = 0; k < steps; ++k) {
+      hphi::FusedArgs fa;
+      fa.out = P;
+      fa.scal = lz.s;
+      fa.partials = partials;
+      fa.done = lz.done;
+      const bool timed = p->profile && !with_x;
+      if (timed) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * k], st));
+      if ((q = hphi::launch_hv(hub, dev_model(m), prec, cplx, C, nullptr, 1, hphi::Epi::kLanczos1, fa, grid, st)).code)
+        return q;
+      if (timed) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * k + 1], st));
+      if ((q = hphi::launch_lz_fin1(lz, k, partials, grid, st)).code) return q;
+      if ((q = hphi::launch_lz_pass2(prec, cplx, lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, n_real, partials,
+                                     vgrid, st)).code)
+        return q;
+      if ((q = hphi::launch_lz_fin2(lz, k, brk, partials, vgrid, st)).code) return q;
+      std::swap(C, P);
+    }
+    return {};
+  };
+
+  Timer tm;
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
+  HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
+  // the loop is captured once into a CUDA graph and replayed on the caller's stream
+  cudaStream_t cap = nullptr;
+  HPHI_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    exec = nullptr; graph = nullptr; cap = nullptr;
+  };
+  auto capture_run = [&](bool with_x) -> hphi::Status {
+    // profiled runs launch eagerly: CUDA events recorded inside a captured graph cannot
+    // be queried with cudaEventElapsedTime
+    if (p->profile) return run_pass(with_x);
+    cudaStream_t saved = st;
+    st = cap;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { st = saved; return {HPHI_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)}; }
+    hphi::Status q = run_pass(with_x);
+    e = cudaStreamEndCapture(cap, &graph);
+    st = saved;
+    if (q.code) return q;
+    if (e != cudaSuccess) return {HPHI_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e)};
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) return {HPHI_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)};
+    e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) return {HPHI_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)};
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    return {};
+  };
+  // When a random start is generated, buffer A already holds it; keep a copy for the
+  // second pass by regenerating it (same seed, bit-identical).
+  auto fail_out = [&](hphi::Status q) {
+    cleanup();
+    destroy_events();
+    return q;
+  };
+  s = capture_run(false);
+  if (s.code) return fail_out(s);
+  ++launches;
+  s = hphi::launch_tridiag(lz, steps, std::max(1, std::min(8, p->n_eig)), p->refine != 0, st);
+  if (s.code) return fail_out(s);
+  HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
+  if (p->refine) {
+    if (!v0) {
+      ++launches;
+      s = hphi::launch_random(ws.vecA.p, m->dim, cplx, prec == HPHI_FP64, p->seed, st);
+      if (s.code) return fail_out(s);
+    }
+    s = capture_run(true);
+    if (s.code) return fail_out(s);
+    launches += 4;
+    // fp64 H x into the (now free) Lanczos buffers, then E, variance and residual
+    double* hx = ws.vecA.as<double>();
+    hphi::FusedArgs fa;
+    fa.out = hx;
+    fa.partials = partials;
+    s = hphi::launch_hv(hub, dev_model(m), HPHI_FP64, cplx, ws.x.p, nullptr, 1, hphi::Epi::kRefine, fa, grid, st);
+    if (s.code) return fail_out(s);
+    s = hphi::launch_refine_fin(lz, partials, grid, 0, st);
+    if (s.code) return fail_out(s);
+    s = hphi::launch_refine_resid(cplx, ws.x.as<double>(), hx, n_real, lz, partials, vgrid, st);
+    if (s.code) return fail_out(s);
+    s = hphi::launch_refine_fin(lz, partials, vgrid, 1, st);
+    if (s.code) return fail_out(s);
+  }
+  cleanup();
+  // results to the host
+  std::vector<double> host(nsc);
+  HPHI_CUDA_TRY(cudaMemcpyAsync(host.data(), base, sizeof(double) * nsc, cudaMemcpyDeviceToHost, st));
+  HPHI_CUDA_TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  HPHI_CUDA_TRY(cudaEventElapsedTime(&ms, tm.a, tm.b));
+  const int* hf = reinterpret_cast<const int*>(host.data() + (reinterpret_cast<double*>(flags) - base));
+  r->steps_done = hf[1];
+  if (r->alpha) memcpy(r->alpha, host.data() + (lz.alpha - base), sizeof(double) * steps);
+  if (r->beta) memcpy(r->beta, host.data() + (lz.beta - base), sizeof(double) * steps);
+  for (int k = 0; k < 8; ++k) r->eig[k] = (k < p->n_eig) ? host[(lz.tri - base) + k] : 0.0;
+  if (p->refine) {
+    r->e_refined = host[(lz.tri - base) + 8];
+    r->residual = host[(lz.tri - base) + 9];
+    r->variance = host[(lz.tri - base) + 10];
+  } else {
+    r->e_refined = r->residual = r->variance = 0.0;
+  }
+  r->device_ms = ms;
+  r->hv_ms = 0.f;
+  r->hv_launches = 0;
+  if (p->profile) {
+    for (int k = 0; k < steps; ++k) {
+      float t = 0.f;
+      if (k < r->steps_done) {
+        if (cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) r->hv_ms += t;
+        else cudaGetLastError();  // clear the error so later calls do not report it
+      }
+    }
+    r->hv_launches = std::min(steps, r->steps_done + 0);
+    destroy_events();
+  }
+  r->kernel_launches = launches;
+  return {};
+}
+
+hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* r, cudaStream_t st) {
+  const int nvec = p->n_starts;
+  const int K = p->steps;
+  const int prec = p->prec;
+  const bool cplx = m->cplx_model;
+  const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (cplx ? 2 : 1);
+  const size_t vbytes = esz * (size_t)m->dim * nvec;
+  const int grid = hv_grid_for(m, nvec);
+  const int vgrid = launch_grid(m->dim * nvec);
+  const int pgrid = std::max(grid, vgrid);
+  Workspace& ws = m->ws;
+  hphi::Status s;
+  if ((s = ws.vecA.ensure(vbytes)).code) return s;
+  if ((s = ws.vecB.ensure(vbytes)).code) return s;
+  if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * nvec * hphi::kMaxRedQ)).code) return s;
+  const size_t nsc = 2 * (size_t)nvec + 3 * (size_t)K * nvec;
+  if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;
+  hphi::TpqDev tq;
+  tq.n2 = ws.scal.as<double>();
+  tq.inv = tq.n2 + nvec;
+  tq.u = tq.inv + nvec;
+  tq.h2 = tq.u + (size_t)K * nvec;
+  tq.nrm = tq.h2 + (size_t)K * nvec;
+  double* partials = ws.partials.as<double>();
+  const bool hub = m->kind == HPHI_HUBBARD;
+  const double ns = p->n_s > 0 ? p->n_s : (double)m->n_sites;
+  const double inv_ns = 1.0 / ns;
+
+  Timer tm;
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
+  if (!p->psi0) {
+    if ((s = hphi::launch_random(ws.vecA.p, m->dim * nvec, cplx, prec == HPHI_FP64, p->seed, st)).code) return s;
+  }
+  HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
+  cudaStream_t cap = nullptr;
+  HPHI_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return {HPHI_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)};
+  }
+  auto body = [&]() -> hphi::Status {
+    hphi::Status q;
+    if ((q = hphi::launch_tpq_init(prec, cplx, p->psi0, ws.vecA.p, m->dim, nvec, partials, vgrid, cap)).code) return q;
+    if ((q = hphi::launch_tpq_init_fin(tq, nvec, partials, vgrid, cap)).code) return q;
+    void* X = ws.vecA.p;
+    void* Xn = ws.vecB.p;
+    for (int k = 0; k < K; ++k) {
+      hphi::FusedArgs fa;
+      fa.out = Xn;
+      fa.scal = tq.inv;
+      fa.partials = partials;
+      fa.l = p->l;
+      fa.inv_ns = inv_ns;
+      if ((q = hphi::launch_hv(hub, dev_model(m), prec, cplx, X, nullptr, nvec, hphi::Epi::kTpq, fa, grid, cap)).code)
+        return q;
+      if ((q = hphi::launch_tpq_fin(tq, k, nvec, inv_ns, partials, grid, cap)).code) return q;
+      std::swap(X, Xn);
+    }
+    return {};
+  };
+  s = body();
+  e = cudaStreamEndCapture(cap, &graph);
+  if (s.code == 0 && e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e)};
+  if (s.code == 0) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)};
+  }
+  if (s.code == 0) {
+    e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)};
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (s.code) return s;
+  HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
+  std::vector<double> host(3 * (size_t)K * nvec);
+  HPHI_CUDA_TRY(cudaMemcpyAsync(host.data(), tq.u, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, st));
+  HPHI_CUDA_TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  HPHI_CUDA_TRY(cudaEventElapsedTime(&ms, tm.a, tm.b));
+  const size_t kn = (size_t)K * nvec;
+  if (r->u) memcpy(r->u, host.data(), sizeof(double) * kn);
+  if (r->h2) memcpy(r->h2, host.data() + kn, sizeof(double) * kn);
+  if (r->norm) memcpy(r->norm, host.data() + 2 * kn, sizeof(double) * kn);
+  r->device_ms = ms;
+  r->kernel_launches = (p->psi0 ? 0 : 1) + 2 + 2 * K;
+  return {};
+}
+
+}  // namespace
+
+extern "C" {
+
+int hphi_lanczos_run(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_result* r, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (!p || !r) return fail(m, HPHI_ERR_INVALID_ARG, "params/result NULL");
+  if (p->steps < 1 || p->steps > 4096 || (p->prec != HPHI_FP64 && p->prec != HPHI_FP32) || p->n_eig < 1 || p->n_eig > 8)
+    return fail(m, HPHI_ERR_INVALID_ARG, "lanczos: steps in 1..4096, prec FP64/FP32, n_eig in 1..8");
+  hphi::Status s = lanczos_impl(m, p, r, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
+int hphi_tpq_run(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* r, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (!p || !r) return fail(m, HPHI_ERR_INVALID_ARG, "params/result NULL");
+  const int nv = p->n_starts;
+  if (nv < 1 || nv > hphi::kMaxNvec || (nv & (nv - 1)) != 0)
+    return fail(m, HPHI_ERR_INVALID_ARG, "tpq: n_starts must be a power of two in 1..256");
+  if (p->steps < 1 || (p->prec != HPHI_FP64 && p->prec != HPHI_FP32) || !isfinite(p->l))
+    return fail(m, HPHI_ERR_INVALID_ARG, "tpq: bad steps, precision or l");
+  hphi::Status s = tpq_impl(m, p, r, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
+}  // extern "C"

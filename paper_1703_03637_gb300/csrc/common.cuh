@@ -1,0 +1,202 @@
+// Shared declarations of the GB300 (sm_103a) Lanczos / mTPQ library: device-side model
+// descriptions, scalar traits, block reductions and the internal launch interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hphi_gpu.h"
+
+namespace hphi {
+
+// ------------------------------------------------------------------ limits
+constexpr int kThreads = 256;        // threads per CTA of every streaming kernel
+constexpr int kMaxSpinEntries = 640;  // off-diagonal XOR patterns staged in shared memory
+constexpr int kMaxClasses = 384;      // distinct coefficient classes
+constexpr int kMaxLin = 64;           // linear diagonal groups (coef * popcount(s & mask))
+constexpr int kMaxPairs = 512;        // bilinear diagonal pairs
+constexpr int kMaxPairGroups = 128;
+constexpr int kMaxHops = 512;         // Hubbard hop entries (both species)
+constexpr int kMaxRedQ = 4;           // reduced quantities per fused kernel
+constexpr int kMaxNvec = 256;
+
+// ------------------------------------------------------------------ device model
+// Off-diagonal spin pattern: w[s] += coef[cls] * phase(b_i + 2 b_j) * v[rank(s ^ mask)].
+struct SpinEntry {
+  uint64_t mask;
+  uint8_t i, j;      // sites whose bra bits select the phase (j == i for one-site terms)
+  uint16_t phases;   // four 3-bit codes: 0 none, 1 (+1), 2 (+i), 3 (-1), 4 (-i)
+  uint16_t cls;
+  uint16_t pad;
+};
+static_assert(sizeof(SpinEntry) == 16, "SpinEntry layout");
+
+struct LinGroup {   // coef * popcount(bits & mask)
+  uint64_t mask;
+  double coef;
+};
+
+struct PairEntry {  // one bilinear diagonal pair, counted as b_i & b_j (spin) or n_i n_j (Hubbard)
+  uint8_t i, j;
+  uint16_t grp;
+};
+
+// Hubbard hop: bra bits (i set, j empty) -> coef[cls]; (j set, i empty) -> conj(coef[cls]);
+// times (-1)^popcount(species bits & between).
+struct HopEntry {
+  uint32_t mask;
+  uint32_t between;
+  uint8_t i, j;
+  uint16_t cls;
+  uint32_t pad;
+};
+static_assert(sizeof(HopEntry) == 16, "HopEntry layout");
+
+struct SectorTables {
+  int L;                       // bits handled by the low table
+  int H;                       // high bits (n_bits - L)
+  int n_ones;                  // popcount of the sector
+  const uint64_t* hi_off;      // [2^H] sector states whose high part is smaller
+  const uint32_t* lo_rank;     // [2^L] rank among L-bit strings of the same popcount
+  const uint32_t* lo_list;     // [2^L] L-bit strings grouped by popcount, ascending
+  const uint32_t* lo_list_off; // [L + 2] start of each popcount group in lo_list
+};
+
+struct SpinDev {
+  int n_sites;
+  int sector;        // 0 full basis, 1 fixed popcount
+  int64_t dim;
+  int n_entries, n_classes, n_lin, n_pairs, n_pair_groups;
+  double c0;
+  const SpinEntry* entries;  // sorted by class
+  const double2* cls_coef;
+  const LinGroup* lin;
+  const PairEntry* pairs;
+  const double* pair_coef;   // [n_pair_groups]
+  SectorTables t;
+};
+
+struct HubDev {
+  int n_sites;
+  int sector;        // 0 full (2^N per species), 1 fixed (N_up, N_dn)
+  int n_up, n_dn;    // particle numbers of the sector
+  int64_t dim, dim_up, dim_dn;
+  int n_up_hops, n_dn_hops, n_classes;
+  int n_ulin, n_mulin, n_pairs, n_pair_groups;
+  double c0;
+  const HopEntry* hops;      // up hops first, then down hops; sorted by class in each part
+  const double2* cls_coef;
+  const LinGroup* ulin;      // U groups: coef * popcount(up & dn & mask)
+  const LinGroup* mulin;     // one-body groups: coef * (popcount(up & mask) + popcount(dn & mask))
+  const PairEntry* pairs;    // V n_i n_j
+  const double* pair_coef;
+  // species tables (rank / list over n_sites bits); null for the full basis
+  const uint32_t* rank;      // [2^N]
+  const uint32_t* list_up;   // [dim_up]
+  const uint32_t* list_dn;   // [dim_dn]
+};
+
+// ------------------------------------------------------------------ scalar traits
+template <class T> struct Cx { T x, y; };
+
+template <class S> struct Traits;
+template <> struct Traits<double> {
+  using R = double; static constexpr bool kCplx = false; static constexpr bool kF64 = true;
+};
+template <> struct Traits<float> {
+  using R = float; static constexpr bool kCplx = false; static constexpr bool kF64 = false;
+};
+template <> struct Traits<double2> {
+  using R = double; static constexpr bool kCplx = true; static constexpr bool kF64 = true;
+};
+template <> struct Traits<float2> {
+  using R = float; static constexpr bool kCplx = true; static constexpr bool kF64 = false;
+};
+
+// ------------------------------------------------------------------ runtime helpers
+struct Status {
+  int code = HPHI_OK;
+  std::string msg;
+};
+
+#define HPHI_CUDA_TRY(expr)                                                            \
+  do {                                                                                 \
+    cudaError_t _e = (expr);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      return ::hphi::Status{HPHI_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
+    }                                                                                  \
+  } while (0)
+
+int num_sms();
+
+// Launch interface (k_basis.cu) --------------------------------------------------------
+Status build_popcount_tables(int L, uint32_t* lo_rank, uint32_t* lo_list, const uint32_t* lo_list_off,
+                             cudaStream_t st);
+Status build_hi_offsets(int L, int H, int n_ones, uint64_t* hi_off, cudaStream_t st);
+Status launch_spin_states(const SpinDev& md, int64_t r0, int64_t n, uint64_t* out, cudaStream_t st);
+Status launch_spin_ranks(const SpinDev& md, const uint64_t* states, int64_t n, int64_t* out, cudaStream_t st);
+Status launch_hub_states(const HubDev& md, int64_t r0, int64_t n, uint64_t* out, cudaStream_t st);
+Status launch_hub_ranks(const HubDev& md, const uint64_t* states, int64_t n, int64_t* out, cudaStream_t st);
+Status launch_philox_raw(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);
+Status launch_random(void* v, int64_t n_elem, bool cplx, bool f64, uint64_t seed, cudaStream_t st);
+
+// H v and fused solver kernels (k_hv.cu) -----------------------------------------------
+enum class Epi { kStore = 0, kLanczos1 = 1, kTpq = 2, kRefine = 3 };
+
+struct FusedArgs {
+  // Lanczos pass 1: P <- c1 * Y - c2 * P; partial sum of self * Y.
+  // TPQ: Xn <- inv[c] * (l * X - Y / Ns); partial sums <X, Y>, |Y|^2, |Xn|^2 per column.
+  // Refine: stores Y and reduces <x, Y>, <x, x>.
+  void* out = nullptr;             // P (Lanczos) / X_{k+1} (TPQ) / Hx (refine)
+  const double* scal = nullptr;    // device scalars read at kernel start
+  double* partials = nullptr;      // [grid][nvec][kMaxRedQ]
+  const int* done = nullptr;       // device flag: skip all work when set
+  double l = 0.0, inv_ns = 0.0;
+};
+
+// Launches w = H v (or a fused step) over all rows; grid chosen by the library.
+Status launch_hv(bool hubbard, const void* md, int prec, bool cplx, const void* v, void* w, int nvec, Epi epi,
+                 const FusedArgs& fa, int grid, cudaStream_t st);
+int hv_grid(int nvec);  // persistent grid size used for fused launches (partials sizing)
+
+// Streaming vector kernels and finalisers (k_solver.cu) -------------------------------
+struct LzDev {           // device scalars of one Lanczos run
+  double* alpha;         // [m]
+  double* beta;          // [m]   beta[k] = beta_{k+1}
+  double* sig;           // [m+1] sigma_k = 1 / |C_k|
+  double* coef;          // [m]   Ritz coefficients (refinement pass)
+  double* s;             // [16]  scratch scalars for the next kernel (c1, c2, gamma, xcoef)
+  int* done;             // [1]   breakdown flag
+  int* steps_done;       // [1]
+  double* tri;           // [8 + 3]  eigenvalues and refinement results
+};
+
+Status launch_lz_init(int prec, bool cplx, const void* v0_f64, void* C, void* P, int64_t n_real, double* partials,
+                      int grid, cudaStream_t st);
+Status launch_lz_init_fin(const LzDev& lz, const double* partials, int grid, cudaStream_t st);
+Status launch_lz_fin1(const LzDev& lz, int k, const double* partials, int grid, cudaStream_t st);
+Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* C, void* P, double* x,
+                       int64_t n_real, double* partials, int grid, cudaStream_t st);
+Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, cudaStream_t st);
+Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, cudaStream_t st);
+Status launch_refine_fin(const LzDev& lz, const double* partials, int grid, int which, cudaStream_t st);
+Status launch_refine_resid(bool cplx, const double* x, const double* hx, int64_t n_real, const LzDev& lz,
+                           double* partials, int grid, cudaStream_t st);
+
+struct TpqDev {
+  double* n2;            // [nvec] |X_k|^2 of the current state
+  double* inv;           // [nvec] 1 / |X_k|
+  double* u;             // [K][nvec]
+  double* h2;            // [K][nvec]
+  double* nrm;           // [K][nvec]
+};
+Status launch_tpq_init(int prec, bool cplx, const void* psi0_f64, void* X, int64_t n_rows, int nvec,
+                       double* partials, int grid, cudaStream_t st);
+Status launch_tpq_init_fin(const TpqDev& tq, int nvec, const double* partials, int grid, cudaStream_t st);
+Status launch_tpq_fin(const TpqDev& tq, int k, int nvec, double inv_ns, const double* partials, int grid,
+                      cudaStream_t st);
+
+}  // namespace hphi

@@ -1,0 +1,447 @@
+// Streaming Lanczos / mTPQ vector kernels, scalar finalisers and the fp64 tridiagonal
+// eigensolver (sections 3.4, 3.5 and appendix A.3).
+//
+// Lanczos vectors are kept unnormalised: buffer C_k holds w_k with v_k = sigma_k C_k, so the
+// normalisation v_{k+1} = w / |w| costs no extra pass (the next H v multiplies by sigma).
+// Every reduction ends in a fixed-order fp64 sum over per-CTA partials.
+#include <math.h>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace hphi {
+
+namespace {
+
+// ------------------------------------------------------------------ reductions
+__device__ double block_sum(double x, double* sm) {
+  const int tid = threadIdx.x;
+  sm[tid] = x;
+  __syncthreads();
+  for (int off = kThreads / 2; off > 0; off >>= 1) {
+    if (tid < off) sm[tid] += sm[tid + off];
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+// sum over `grid` partial rows of quantity q of column c, fixed order
+__device__ double sum_partials(const double* __restrict__ partials, int grid, int nvec, int c, int q, double* sm) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < grid; b += kThreads) s += partials[((size_t)b * nvec + c) * kMaxRedQ + q];
+  return block_sum(s, sm);
+}
+
+template <class S> struct VT;
+template <> struct VT<double> { static constexpr int kW = 1; using R = double; };
+template <> struct VT<float> { static constexpr int kW = 1; using R = float; };
+
+// ------------------------------------------------------------------ Lanczos start
+// C <- (storage precision) v0 (if given); P <- 0; partial |C|^2.  Elements counted as reals.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_lz_init(const double* __restrict__ v0, R* __restrict__ C, R* __restrict__ P,
+                                                       int64_t n_real, double* __restrict__ partials) {
+  __shared__ double sm[kThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += (int64_t)gridDim.x * kThreads) {
+    R x;
+    if (v0 != nullptr) {
+      x = (R)v0[i];
+      C[i] = x;
+    } else {
+      x = C[i];
+    }
+    P[i] = (R)0;
+    acc = fma((double)x, (double)x, acc);
+  }
+  const double t = block_sum(acc, sm);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kMaxRedQ] = t;
+}
+
+// mode 0: after init (sigma_0); mode 1: after pass 1 (alpha_k); mode 2: after pass 2 (beta_{k+1})
+__global__ void __launch_bounds__(kThreads) k_lz_fin(LzDev lz, int mode, int k, double brk,
+                                                      const double* __restrict__ partials, int grid) {
+  __shared__ double sm[kThreads];
+  if (mode != 0 && *lz.done) return;
+  const double sum = sum_partials(partials, grid, 1, 0, 0, sm);
+  if (threadIdx.x != 0) return;
+  if (mode == 0) {
+    const double sg = (sum > 0.0) ? 1.0 / sqrt(sum) : 0.0;
+    lz.sig[0] = sg;
+    lz.s[0] = sg;    // c1 = sigma_0
+    lz.s[1] = 0.0;   // c2 = beta_0 sigma_{-1} = 0
+    *lz.done = (sum > 0.0) ? 0 : 1;
+    *lz.steps_done = 0;
+  } else if (mode == 1) {
+    const double sg = lz.sig[k];
+    const double a = sum * sg * sg;  // alpha_k = (H v_k, v_k)
+    lz.alpha[k] = a;
+    lz.s[2] = a * sg;                // gamma: P <- P - alpha_k v_k = P - gamma C_k
+    lz.s[3] = lz.coef[k] * sg;       // Ritz coefficient of v_k (refinement pass)
+  } else {
+    const double b = sqrt(sum);      // beta_{k+1} = |w|
+    const double a = lz.alpha[k];
+    lz.beta[k] = b;
+    *lz.steps_done = k + 1;
+    if (!(b > brk * fmax(1.0, fabs(a)))) {
+      *lz.done = 1;
+    } else {
+      const double sg = 1.0 / b;
+      lz.sig[k + 1] = sg;
+      lz.s[0] = sg;                  // c1 = sigma_{k+1}
+      lz.s[1] = b * lz.sig[k];       // c2 = beta_{k+1} sigma_k
+    }
+  }
+}
+
+// P <- P - gamma C ; partial |P|^2 ; optionally x += xc * C (fp64 accumulator)
+template <class R, bool X>
+__global__ void __launch_bounds__(kThreads) k_lz_pass2(LzDev lz, const R* __restrict__ C, R* __restrict__ P,
+                                                        double* __restrict__ x, int64_t n_real,
+                                                        double* __restrict__ partials) {
+  constexpr bool F64 = sizeof(R) == 8;
+  __shared__ double sm[kThreads];
+  if (*lz.done) return;
+  const double g = lz.s[2];
+  const R gr = (R)g;
+  const double xc = X ? lz.s[3] : 0.0;
+  Red<F64> red;
+  red.zero();
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += (int64_t)gridDim.x * kThreads) {
+    const R c = C[i];
+    const R p = P[i] - gr * c;
+    P[i] = p;
+    red.add(0, p, p);
+    red.tick();
+    if (X) x[i] = fma(xc, (double)c, x[i]);
+  }
+  const double t = block_sum(red.get(0), sm);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kMaxRedQ] = t;
+}
+
+// ------------------------------------------------------------------ tridiagonal eigensolver
+// Number of eigenvalues of T (diag a[0..n-1], off-diag b[0..n-2]) smaller than x, by the
+// Sturm sequence of the LDL^T pivots.
+__device__ int sturm_count(const double* __restrict__ a, const double* __restrict__ b, int n, double x, double pivmin) {
+  int cnt = 0;
+  double q = a[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = (a[i] - x) - (b[i - 1] * b[i - 1]) / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// One warp per wanted eigenvalue: 33-section of the Gershgorin interval until the bracket is
+// a few ulps wide.  Then (warp 0, lane 0, if asked) inverse iteration for the lowest
+// eigenvector of T with partial-pivoting tridiagonal LU.
+__global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double* __restrict__ work) {
+  const int n = *lz.steps_done;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* a = lz.alpha;
+  const double* b = lz.beta;
+  if (n <= 0) return;
+  double lo = a[0], hi = a[0], bmax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+    if (i + 1 < n) bmax = fmax(bmax, fabs(b[i]));
+  }
+  const double scale = fmax(fabs(lo), fabs(hi));
+  const double pivmin = fmax(1e-300, 2.2250738585072014e-308 * fmax(1.0, bmax * bmax));
+  lo -= 2.2e-16 * scale + 1e-300;
+  hi += 2.2e-16 * scale + 1e-300;
+  if (warp < n_eig) {
+    const int j = warp;
+    if (j >= n) {
+      if (lane == 0) lz.tri[j] = nan("");
+    } else {
+      double x0 = lo, x1 = hi;
+      for (int it = 0; it < 64; ++it) {
+        if (x1 - x0 <= 4.0 * 2.2204460492503131e-16 * fmax(fabs(x0), fabs(x1)) + 1e-300) break;
+        const double x = x0 + (x1 - x0) * (double)(lane + 1) / 33.0;
+        const int cnt = sturm_count(a, b, n, x, pivmin);
+        // points with cnt <= j lie left of eigenvalue j
+        const unsigned left = __ballot_sync(0xffffffffu, cnt <= j);
+        const int nl = __popc(left);  // points are increasing in lane order
+        double nx0 = x0, nx1 = x1;
+        const double xl = __shfl_sync(0xffffffffu, x, nl > 0 ? nl - 1 : 0);
+        const double xr = __shfl_sync(0xffffffffu, x, nl < 32 ? nl : 31);
+        if (nl > 0) nx0 = xl;
+        if (nl < 32) nx1 = xr;
+        x0 = nx0;
+        x1 = nx1;
+      }
+      if (lane == 0) lz.tri[j] = 0.5 * (x0 + x1);
+    }
+  }
+  if (!want_vec) return;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // inverse iteration: (T - lambda I) y = y_prev, LU with partial pivoting (two superdiagonals)
+  const double lam = lz.tri[0];
+  double* d = work;            // diagonal of U
+  double* e1 = work + n;       // first superdiagonal of U
+  double* e2 = work + 2 * n;   // second superdiagonal of U (from pivoting)
+  double* l = work + 3 * n;    // multipliers
+  int* piv = reinterpret_cast<int*>(work + 4 * n);
+  double* y = lz.coef;
+  const double eps = 2.2204460492503131e-16 * fmax(scale, 1e-300);
+  // factor
+  double dd = a[0] - lam, ee = (n > 1) ? b[0] : 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (i == n - 1) {
+      d[i] = (fabs(dd) < eps) ? eps : dd;
+      e1[i] = 0.0;
+      e2[i] = 0.0;
+      piv[i] = 0;
+      break;
+    }
+    const double sub = b[i];
+    const double nd = a[i + 1] - lam;
+    const double ne = (i + 2 < n) ? b[i + 1] : 0.0;
+    if (fabs(dd) >= fabs(sub)) {
+      const double piv_d = (fabs(dd) < eps) ? eps : dd;
+      const double m = sub / piv_d;
+      d[i] = piv_d; e1[i] = ee; e2[i] = 0.0; l[i] = m; piv[i] = 0;
+      dd = nd - m * ee;
+      ee = ne;
+    } else {
+      const double m = dd / sub;
+      d[i] = sub; e1[i] = nd; e2[i] = ne; l[i] = m; piv[i] = 1;
+      dd = ee - m * nd;
+      ee = -m * ne;
+    }
+  }
+  for (int i = 0; i < n; ++i) y[i] = 1.0;
+  for (int iter = 0; iter < 3; ++iter) {
+    // forward: apply L^{-1} with the recorded row swaps
+    for (int i = 0; i + 1 < n; ++i) {
+      if (piv[i]) {
+        const double t = y[i];
+        y[i] = y[i + 1];
+        y[i + 1] = t - l[i] * y[i];
+      } else {
+        y[i + 1] -= l[i] * y[i];
+      }
+    }
+    // back substitution with U
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      if (i + 1 < n) t -= e1[i] * y[i + 1];
+      if (i + 2 < n) t -= e2[i] * y[i + 2];
+      y[i] = t / d[i];
+    }
+    double nrm = 0.0, big = 0.0;
+    for (int i = 0; i < n; ++i) {
+      nrm += y[i] * y[i];
+      if (fabs(y[i]) > fabs(big)) big = y[i];
+    }
+    const double sc = (big < 0 ? -1.0 : 1.0) / sqrt(nrm);
+    for (int i = 0; i < n; ++i) y[i] *= sc;
+  }
+}
+
+// ------------------------------------------------------------------ refinement
+__global__ void k_refine_fin(LzDev lz, const double* __restrict__ partials, int grid, int which) {
+  __shared__ double sm[kThreads];
+  if (which == 0) {
+    const double xh = sum_partials(partials, grid, 1, 0, 0, sm);
+    const double xx = sum_partials(partials, grid, 1, 0, 1, sm);
+    const double hh = sum_partials(partials, grid, 1, 0, 2, sm);
+    if (threadIdx.x == 0) {
+      const double e = xh / xx;
+      lz.tri[8] = e;
+      lz.tri[10] = hh / xx - e * e;
+      lz.tri[11] = xx;
+    }
+  } else {
+    const double rr = sum_partials(partials, grid, 1, 0, 0, sm);
+    if (threadIdx.x == 0) lz.tri[9] = sqrt(rr / lz.tri[11]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_refine_resid(const double* __restrict__ x, const double* __restrict__ hx,
+                                                            int64_t n_real, LzDev lz, double* __restrict__ partials) {
+  __shared__ double sm[kThreads];
+  const double e = lz.tri[8];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += (int64_t)gridDim.x * kThreads) {
+    const double r = hx[i] - e * x[i];
+    acc = fma(r, r, acc);
+  }
+  const double t = block_sum(acc, sm);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kMaxRedQ] = t;
+}
+
+// ------------------------------------------------------------------ mTPQ
+// X <- (storage precision) psi0 (if given); per-column partial |X|^2.  nvec divides kThreads.
+template <class R, bool CPLX>
+__global__ void __launch_bounds__(kThreads) k_tpq_init(const double* __restrict__ psi0, R* __restrict__ X,
+                                                        int64_t n_rows, int nvec, double* __restrict__ partials) {
+  __shared__ double sm[kThreads];
+  const int W = CPLX ? 2 : 1;
+  const int64_t n_elem = n_rows * nvec;
+  double acc = 0.0;
+  const int c = threadIdx.x % nvec;
+  for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * kThreads) {
+    for (int w = 0; w < W; ++w) {
+      const int64_t i = e * W + w;
+      R x;
+      if (psi0 != nullptr) {
+        x = (R)psi0[i];
+        X[i] = x;
+      } else {
+        x = X[i];
+      }
+      acc = fma((double)x, (double)x, acc);
+    }
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = kThreads / 2; off >= nvec; off >>= 1) {
+    if (threadIdx.x < off) sm[threadIdx.x] += sm[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x < nvec) partials[((size_t)blockIdx.x * nvec + c) * kMaxRedQ] = sm[threadIdx.x];
+}
+
+// one CTA per column; mode 0: initial norms; mode 1: records of step k
+__global__ void __launch_bounds__(kThreads) k_tpq_fin(TpqDev tq, int mode, int k, int nvec, double inv_ns,
+                                                       const double* __restrict__ partials, int grid) {
+  __shared__ double sm[kThreads];
+  const int c = blockIdx.x;
+  if (mode == 0) {
+    const double n2 = sum_partials(partials, grid, nvec, c, 0, sm);
+    if (threadIdx.x == 0) {
+      tq.n2[c] = n2;
+      tq.inv[c] = 1.0 / sqrt(n2);
+    }
+    return;
+  }
+  const double xy = sum_partials(partials, grid, nvec, c, 0, sm);
+  const double yy = sum_partials(partials, grid, nvec, c, 1, sm);
+  const double nn = sum_partials(partials, grid, nvec, c, 2, sm);
+  if (threadIdx.x == 0) {
+    const double n2 = tq.n2[c];
+    const size_t o = (size_t)k * nvec + c;
+    tq.u[o] = xy * inv_ns / n2;
+    tq.h2[o] = yy * inv_ns * inv_ns / n2;
+    tq.nrm[o] = sqrt(nn);
+    tq.n2[c] = nn;
+    tq.inv[c] = 1.0 / sqrt(nn);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+Status launch_lz_init(int prec, bool cplx, const void* v0_f64, void* C, void* P, int64_t n_real, double* partials,
+                      int grid, cudaStream_t st) {
+  (void)cplx;
+  if (prec == HPHI_FP64)
+    k_lz_init<double><<<grid, kThreads, 0, st>>>(reinterpret_cast<const double*>(v0_f64), reinterpret_cast<double*>(C),
+                                                 reinterpret_cast<double*>(P), n_real, partials);
+  else
+    k_lz_init<float><<<grid, kThreads, 0, st>>>(reinterpret_cast<const double*>(v0_f64), reinterpret_cast<float*>(C),
+                                                reinterpret_cast<float*>(P), n_real, partials);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_lz_init_fin(const LzDev& lz, const double* partials, int grid, cudaStream_t st) {
+  k_lz_fin<<<1, kThreads, 0, st>>>(lz, 0, 0, 0.0, partials, grid);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_lz_fin1(const LzDev& lz, int k, const double* partials, int grid, cudaStream_t st) {
+  k_lz_fin<<<1, kThreads, 0, st>>>(lz, 1, k, 0.0, partials, grid);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* C, void* P, double* x, int64_t n_real,
+                       double* partials, int grid, cudaStream_t st) {
+  (void)cplx;
+  (void)k;
+  if (prec == HPHI_FP64) {
+    if (x)
+      k_lz_pass2<double, true><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const double*>(C),
+                                                          reinterpret_cast<double*>(P), x, n_real, partials);
+    else
+      k_lz_pass2<double, false><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const double*>(C),
+                                                           reinterpret_cast<double*>(P), x, n_real, partials);
+  } else {
+    if (x)
+      k_lz_pass2<float, true><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const float*>(C),
+                                                         reinterpret_cast<float*>(P), x, n_real, partials);
+    else
+      k_lz_pass2<float, false><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const float*>(C),
+                                                          reinterpret_cast<float*>(P), x, n_real, partials);
+  }
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, cudaStream_t st) {
+  k_lz_fin<<<1, kThreads, 0, st>>>(lz, 2, k, brk, partials, grid);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, cudaStream_t st) {
+  (void)m_max;
+  k_tridiag<<<1, 32 * 8, 0, st>>>(lz, n_eig, want_vec ? 1 : 0, lz.tri + 16);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_refine_fin(const LzDev& lz, const double* partials, int grid, int which, cudaStream_t st) {
+  k_refine_fin<<<1, kThreads, 0, st>>>(lz, partials, grid, which);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_refine_resid(bool cplx, const double* x, const double* hx, int64_t n_real, const LzDev& lz,
+                           double* partials, int grid, cudaStream_t st) {
+  (void)cplx;
+  k_refine_resid<<<grid, kThreads, 0, st>>>(x, hx, n_real, lz, partials);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_tpq_init(int prec, bool cplx, const void* psi0_f64, void* X, int64_t n_rows, int nvec, double* partials,
+                       int grid, cudaStream_t st) {
+  const double* p = reinterpret_cast<const double*>(psi0_f64);
+  if (prec == HPHI_FP64) {
+    if (cplx) k_tpq_init<double, true><<<grid, kThreads, 0, st>>>(p, reinterpret_cast<double*>(X), n_rows, nvec, partials);
+    else k_tpq_init<double, false><<<grid, kThreads, 0, st>>>(p, reinterpret_cast<double*>(X), n_rows, nvec, partials);
+  } else {
+    if (cplx) k_tpq_init<float, true><<<grid, kThreads, 0, st>>>(p, reinterpret_cast<float*>(X), n_rows, nvec, partials);
+    else k_tpq_init<float, false><<<grid, kThreads, 0, st>>>(p, reinterpret_cast<float*>(X), n_rows, nvec, partials);
+  }
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_tpq_init_fin(const TpqDev& tq, int nvec, const double* partials, int grid, cudaStream_t st) {
+  k_tpq_fin<<<nvec, kThreads, 0, st>>>(tq, 0, 0, nvec, 0.0, partials, grid);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_tpq_fin(const TpqDev& tq, int k, int nvec, double inv_ns, const double* partials, int grid,
+                      cudaStream_t st) {
+  k_tpq_fin<<<nvec, kThreads, 0, st>>>(tq, 1, k, nvec, inv_ns, partials, grid);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+}  // namespace hphi

@@ -1,0 +1,298 @@
+"""Parity of the CUDA path with the CPU oracle, element by element, through the C ABI.
+
+Tolerances (fp64): H v agrees to 1e-12 relative to max|H v|; Lanczos alpha/beta of the first
+steps to 1e-12 relative; converged energies to 1e-10 relative; TPQ records to 1e-11 relative.
+fp32 storage paths: 2e-5 relative (single-precision vectors).  Integer work (basis states,
+ranks, Philox words) is compared bit for bit.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+hp = pytest.importorskip("paper_1703_03637_gb300")
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _to_dev(model, v, prec=hp.FP64):
+    return torch.as_tensor(np.ascontiguousarray(v)).to(device="cuda", dtype=model.dtype(prec))
+
+
+# ----------------------------------------------------------------------------- Philox
+def test_philox_known_answers_on_device():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                rows.append([int(x, 16) for x in line[1:]])
+    rows = np.array(rows, dtype=np.uint64)
+    out = hp.philox4x32_10(rows[:, 0:4].astype(np.uint32), rows[:, 4:6].astype(np.uint32))
+    assert np.array_equal(out, rows[:, 6:10].astype(np.uint32))
+
+
+def test_philox_random_counters_bit_exact():
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
+    out = hp.philox4x32_10(ctr, key)
+    ref = np.array([oracle.philox4x32_10(c, k) for c, k in zip(ctr[:512], key[:512])])
+    assert np.array_equal(out[:512], ref)
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_start_vector_matches_oracle_generator(complex_):
+    spec = wl.kitaev_honeycomb(2, 2) if complex_ else wl.heisenberg_ring(10)
+    m = hp.Model.from_spec(spec)
+    assert m.is_complex == complex_
+    v = m.random_vector(123432, nvec=2).cpu().numpy()
+    idx = np.arange(v.size, dtype=np.uint64)
+    ref = oracle.gauss_at(123432, idx, complex_).reshape(v.shape)
+    assert np.max(np.abs(v - ref)) < 1e-13
+
+
+# ----------------------------------------------------------------------------- basis
+@pytest.mark.parametrize("n,k", [(4, 2), (12, 6), (13, 4), (20, 10), (24, 12), (16, 0), (16, 16)])
+def test_sector_states_and_ranks_bit_exact(n, k):
+    m = hp.Model.from_spec(wl.heisenberg_ring(n).with_basis(wl.BASIS_SZ, k))
+    st = m.basis_states().cpu().numpy().astype(np.uint64)
+    ref = oracle.sector_list(n, k)
+    assert np.array_equal(st, ref)
+    rk = m.basis_ranks(torch.as_tensor(ref.astype(np.int64))).cpu().numpy()
+    assert np.array_equal(rk, np.arange(len(ref)))
+    bad = torch.as_tensor(np.array([(1 << n) - 1 if k != n else 0], dtype=np.int64))
+    assert m.basis_ranks(bad).cpu().numpy()[0] == -1
+
+
+def test_sector_36_sites_sampled():
+    n, k = 36, 18
+    m = hp.Model.from_spec(wl.heisenberg_square(6, 6).with_basis(wl.BASIS_SZ, k))
+    D = math.comb(n, k)
+    assert m.dim == D
+    rng = np.random.default_rng(3)
+    rows = np.concatenate([[0, 1, D - 2, D - 1], rng.integers(0, D, size=3000)])
+    got = []
+    for r in rows:
+        got.append(int(m.basis_states(int(r), 1).cpu().numpy()[0]))
+    want = [oracle.unrank(int(r), n, k) for r in rows]
+    assert got == want
+    rk = m.basis_ranks(torch.as_tensor(np.array(want, dtype=np.int64))).cpu().numpy()
+    assert np.array_equal(rk, rows)
+
+
+def test_hubbard_states_and_ranks():
+    spec = wl.hubbard_square(4, 4).with_basis(wl.BASIS_NUMBER, 8, 8)
+    m = hp.Model.from_spec(spec)
+    assert m.dim == 165636900
+    lst = oracle.sector_list(16, 8).astype(np.int64)
+    rng = np.random.default_rng(9)
+    rows = rng.integers(0, m.dim, size=2000)
+    st = np.array([int(m.basis_states(int(r), 1).cpu().numpy()[0]) for r in rows[:200]])
+    D = len(lst)
+    want = (lst[rows[:200] // D] << 32) | lst[rows[:200] % D]
+    assert np.array_equal(st, want)
+    rk = m.basis_ranks(torch.as_tensor(want)).cpu().numpy()
+    assert np.array_equal(rk, rows[:200])
+
+
+# ----------------------------------------------------------------------------- H v
+HV_CASES = [
+    ("heisenberg_ring12_full", lambda: wl.heisenberg_ring(12)),
+    ("random_spin_full_complex", lambda: wl.random_spin_model(9, 14, seed=1)),
+    ("random_spin_full_real", lambda: wl.random_spin_model(9, 14, seed=2, complex_=False)),
+    ("xxz_sector", lambda: wl.random_xxz_model(14, 30, seed=3).with_basis(wl.BASIS_SZ, 6)),
+    ("heisenberg_4x4_sz8", lambda: wl.heisenberg_square(4, 4).with_basis(wl.BASIS_SZ, 8)),
+    ("j1j2_ring18_sz7", lambda: wl.j1j2_ring(18).with_basis(wl.BASIS_SZ, 7)),
+    ("kitaev_3x2", lambda: wl.kitaev_honeycomb(3, 2)),
+    ("hubbard_3x4_66", lambda: wl.hubbard_square(4, 3).with_basis(wl.BASIS_NUMBER, 6, 6)),
+    ("hubbard_random_complex", lambda: wl.random_hubbard_model(6, 12, seed=4).with_basis(wl.BASIS_NUMBER, 3, 2)),
+    ("hubbard_full", lambda: wl.random_hubbard_model(5, 9, seed=6, complex_=False)),
+]
+
+
+@pytest.mark.parametrize("name,mk", HV_CASES, ids=[c[0] for c in HV_CASES])
+@pytest.mark.parametrize("nvec", [1, 3, 4])
+def test_apply_H_fp64(name, mk, nvec):
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    D = m.dim
+    assert D == oracle.dim(spec)
+    v = wl.gaussian_vector(11 + nvec, D, nvec, complex_=m.is_complex)
+    w = m.apply_H(_to_dev(m, v)).cpu().numpy()
+    ref = oracle.apply_H(spec, v)
+    if not m.is_complex:
+        assert np.max(np.abs(ref.imag)) == 0.0
+        ref = ref.real
+    assert _rel(w, ref) < 1e-12
+
+
+@pytest.mark.parametrize("name,mk", HV_CASES[:8], ids=[c[0] for c in HV_CASES[:8]])
+def test_apply_H_fp32(name, mk):
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    v = wl.gaussian_vector(21, m.dim, 2, complex_=m.is_complex)
+    vf = _to_dev(m, v, hp.FP32)
+    w = m.apply_H(vf).cpu().numpy()
+    ref = oracle.apply_H(spec, vf.cpu().numpy().astype(np.complex128))
+    ref = ref if m.is_complex else ref.real
+    assert _rel(w, ref) < 2e-5
+
+
+def test_basis_mismatch_is_an_error():
+    spec = wl.kitaev_honeycomb(2, 2).with_basis(wl.BASIS_SZ, 4)
+    with pytest.raises(hp.LibraryError) as e:
+        hp.Model.from_spec(spec)
+    assert e.value.code == -2
+
+
+# ----------------------------------------------------------------------------- full-size sampled H v
+FULL_CASES = [
+    ("hubbard_4x4_8u8d", lambda: wl.workload("hubbard_4x4_8u8d")["model"], 1),
+    ("heisenberg_ring12_full", lambda: wl.workload("heisenberg_ring12_full")["model"], 1),
+    ("j1j2_ring28_sz14", lambda: wl.j1j2_ring(28).with_basis(wl.BASIS_SZ, 14), 1),
+    ("kitaev_24_64starts", lambda: wl.workload("kitaev_24_tpq64")["model"], 64),
+]
+
+
+@pytest.mark.parametrize("name,mk,nvec", FULL_CASES, ids=[c[0] for c in FULL_CASES])
+def test_apply_H_full_size_sampled_rows(name, mk, nvec):
+    """Full-size H v in the launch configuration the solvers use; sampled rows (and the
+    first and last) recomputed by the oracle from the Philox definition of v."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    seed = 777
+    v = m.random_vector(seed, nvec=nvec)
+    w = m.apply_H(v)
+    rng = np.random.default_rng(2)
+    rows = np.unique(np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, size=1500)])).astype(np.int64)
+    cols = [0, nvec - 1] if nvec > 1 else [0]
+    for c in cols:
+        got = w[torch.as_tensor(rows, device="cuda"), c].cpu().numpy()
+        ref = oracle.apply_H_rows_philox(spec, rows.astype(np.uint64), seed, m.is_complex, nvec, c)
+        ref = ref if m.is_complex else ref.real
+        assert _rel(got, ref) < 1e-12
+    del v, w
+    torch.cuda.empty_cache()
+
+
+# ----------------------------------------------------------------------------- Lanczos
+LZ_CASES = [
+    ("heisenberg_ring12_full", lambda: wl.heisenberg_ring(12), 100),
+    ("heisenberg_ring16_sz8", lambda: wl.heisenberg_ring(16).with_basis(wl.BASIS_SZ, 8), 90),
+    ("hubbard_2x4_44", lambda: wl.hubbard_square(4, 2).with_basis(wl.BASIS_NUMBER, 4, 4), 80),
+    ("kitaev_2x2", lambda: wl.kitaev_honeycomb(2, 2), 60),
+]
+
+
+@pytest.mark.parametrize("name,mk,steps", LZ_CASES, ids=[c[0] for c in LZ_CASES])
+def test_lanczos_fp64_parity(name, mk, steps):
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    v0 = wl.gaussian_vector(31, m.dim, complex_=m.is_complex)[:, 0]
+    res = m.lanczos(steps, v0=torch.as_tensor(v0), n_eig=4)
+    a, b = oracle.lanczos(spec, v0, steps)
+    n = min(12, len(a))
+    assert res["steps"] == len(a)
+    assert _rel(res["alpha"][:n], a[:n]) < 1e-12
+    assert _rel(res["beta"][:n], b[:n]) < 1e-12
+    ev = oracle.ritz_values(a, b)
+    e0 = ev[0]
+    assert abs(res["eig"][0] - e0) <= 1e-10 * abs(e0)
+    # the device tridiagonal solver on the device's own alpha/beta, all four values
+    evd = oracle.ritz_values(res["alpha"], res["beta"])
+    k = min(4, len(evd))
+    assert np.max(np.abs(res["eig"][:k] - evd[:k])) <= 1e-12 * np.max(np.abs(evd))
+    H = oracle.dense_H(spec) if m.dim <= 4096 else None
+    if H is not None:
+        assert abs(res["eig"][0] - np.linalg.eigvalsh(H)[0]) <= 1e-10 * abs(e0)
+
+
+def test_lanczos_breakdown_one_state_sector():
+    spec = wl.j1j2_ring(10).with_basis(wl.BASIS_SZ, 10)
+    m = hp.Model.from_spec(spec)
+    res = m.lanczos(20, seed=5)
+    assert res["steps"] == 1
+    assert abs(res["eig"][0] - 10 * 1.5 / 4) < 1e-14
+
+
+def test_lanczos_random_start_is_seeded():
+    m = hp.Model.from_spec(wl.heisenberg_ring(12))
+    r1 = m.lanczos(30, seed=99)
+    r2 = m.lanczos(30, seed=99)
+    assert np.array_equal(r1["alpha"], r2["alpha"]) and np.array_equal(r1["beta"], r2["beta"])
+    v0 = m.random_vector(99)[:, 0]
+    r3 = m.lanczos(30, v0=v0)
+    assert np.array_equal(r1["alpha"], r3["alpha"])
+
+
+def test_lanczos_mixed_with_fp64_refinement():
+    spec = wl.heisenberg_ring(16).with_basis(wl.BASIS_SZ, 8)
+    m = hp.Model.from_spec(spec)
+    v0 = wl.gaussian_vector(41, m.dim)[:, 0]
+    a, b = oracle.lanczos(spec, v0, 120)
+    e0 = oracle.ritz_values(a, b)[0]
+    r = m.lanczos(120, prec=hp.FP32, v0=torch.as_tensor(v0), refine=True)
+    assert abs(r["e_refined"] - e0) <= 1e-8 * abs(e0)
+    assert r["e_refined"] >= e0 - 1e-12 * abs(e0)  # variational
+    assert r["residual"] < 1e-3
+    r64 = m.lanczos(120, prec=hp.FP64, v0=torch.as_tensor(v0), refine=True)
+    assert abs(r64["e_refined"] - e0) <= 1e-10 * abs(e0)
+    assert r64["residual"] < 1e-5
+
+
+# ----------------------------------------------------------------------------- TPQ
+TPQ_CASES = [
+    ("kitaev_2x2", lambda: wl.kitaev_honeycomb(2, 2), 4, 40),
+    ("kitaev_3x2", lambda: wl.kitaev_honeycomb(3, 2), 8, 25),
+    ("hubbard_ring6_33", lambda: wl.hubbard_ring(6, 1.0, 4.0).with_basis(wl.BASIS_NUMBER, 3, 3), 2, 30),
+    ("heisenberg_ring10_full", lambda: wl.heisenberg_ring(10), 1, 30),
+]
+
+
+@pytest.mark.parametrize("name,mk,nv,K", TPQ_CASES, ids=[c[0] for c in TPQ_CASES])
+def test_tpq_fp64_parity(name, mk, nv, K):
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    psi0 = wl.gaussian_vector(51, m.dim, nv, complex_=m.is_complex)
+    res = m.tpq(nv, K, l=1.0, psi0=torch.as_tensor(psi0))
+    for c in range(nv):
+        u, h2, nrm = oracle.tpq(spec, psi0[:, c], K, 1.0)
+        assert _rel(res["u"][:, c], u) < 1e-11
+        assert _rel(res["h2"][:, c], h2) < 1e-11
+        assert _rel(res["norm"][:, c], nrm) < 1e-11
+
+
+def test_tpq_fp32_parity():
+    spec = wl.kitaev_honeycomb(3, 2)
+    m = hp.Model.from_spec(spec)
+    psi0 = wl.gaussian_vector(52, m.dim, 4, complex_=True)
+    res = m.tpq(4, 20, l=1.0, prec=hp.FP32, psi0=torch.as_tensor(psi0))
+    for c in range(4):
+        u, h2, nrm = oracle.tpq(spec, psi0[:, c], 20, 1.0)
+        assert _rel(res["u"][:, c], u) < 2e-5
+        assert _rel(res["norm"][:, c], nrm) < 2e-5
+
+
+def test_tpq_64_starts_layout():
+    """64 interleaved starts (the batched layout) agree with single-start runs."""
+    spec = wl.kitaev_honeycomb(3, 2)
+    m = hp.Model.from_spec(spec)
+    psi0 = wl.gaussian_vector(53, m.dim, 64, complex_=True)
+    res = m.tpq(64, 10, l=1.0, psi0=torch.as_tensor(psi0))
+    for c in (0, 17, 63):
+        one = m.tpq(1, 10, l=1.0, psi0=torch.as_tensor(np.ascontiguousarray(psi0[:, c:c + 1])))
+        assert _rel(res["u"][:, c], one["u"][:, 0]) < 1e-12
+    assert np.all(np.abs(res["u"][0]) < 0.2)  # infinite-temperature energy ~ Tr H / D = 0
