@@ -114,6 +114,7 @@ struct hphi_model {
   int device = 0;
   // device data
   DBuf d_entries, d_cls, d_lin, d_pairs, d_pcoef, d_hi_off, d_lo_rank, d_lo_list, d_lo_off;
+  DBuf d_nbr_up, d_deg_up, d_nbr_dn, d_deg_dn;
   hphi::SpinDev sdev{};
   hphi::HubDev hdev{};
   Workspace ws;
@@ -421,6 +422,53 @@ hphi::Status build_lo_tables(hphi_model* m, int L, cudaStream_t st) {
                                      m->d_lo_off.as<uint32_t>(), st);
 }
 
+// Two-pass Hubbard path: real model with one hopping value per species.  Builds the
+// per-species neighbour tables on the device.
+hphi::Status build_hub_fast(hphi_model* m, cudaStream_t st) {
+  hphi::HubDev& d = m->hdev;
+  d.fast = 0;
+  if (m->cplx_model) return {};
+  int cls[2] = {-1, -1};
+  int cnt[2] = {0, 0};
+  for (int sp = 0; sp < 2; ++sp) {
+    for (const Hop& h : m->hop) {
+      if ((h.spin ? 1 : 0) != sp) continue;
+      ++cnt[sp];
+    }
+  }
+  if (cnt[0] > 255 || cnt[1] > 255) return {};
+  std::vector<hphi::HopEntry> host(cnt[0] + cnt[1]);
+  if (!host.empty())
+    HPHI_CUDA_TRY(cudaMemcpyAsync(host.data(), d.hops, sizeof(hphi::HopEntry) * host.size(), cudaMemcpyDeviceToHost, st));
+  std::vector<double2> cc(std::max(1, d.n_classes));
+  HPHI_CUDA_TRY(cudaMemcpyAsync(cc.data(), d.cls_coef, sizeof(double2) * cc.size(), cudaMemcpyDeviceToHost, st));
+  HPHI_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < (int)host.size(); ++k) {
+    const int sp = k < cnt[0] ? 0 : 1;
+    if (cls[sp] < 0) cls[sp] = host[k].cls;
+    else if (cls[sp] != host[k].cls) return {};  // several hopping values: generic path
+  }
+  const size_t tab = (size_t)4 * (d.dim_up * std::max(1, cnt[0]) + d.dim_dn * std::max(1, cnt[1]));
+  if (tab > ((size_t)1 << 30)) return {};
+  hphi::Status s;
+  d.maxdeg_up = std::max(1, cnt[0]);
+  d.maxdeg_dn = std::max(1, cnt[1]);
+  d.c_up = cls[0] >= 0 ? cc[cls[0]].x : 0.0;
+  d.c_dn = cls[1] >= 0 ? cc[cls[1]].x : 0.0;
+  if ((s = m->d_nbr_up.ensure((size_t)4 * d.dim_up * d.maxdeg_up)).code) return s;
+  if ((s = m->d_deg_up.ensure((size_t)d.dim_up)).code) return s;
+  if ((s = m->d_nbr_dn.ensure((size_t)4 * d.dim_dn * d.maxdeg_dn)).code) return s;
+  if ((s = m->d_deg_dn.ensure((size_t)d.dim_dn)).code) return s;
+  d.nbr_up = m->d_nbr_up.as<uint32_t>();
+  d.deg_up = m->d_deg_up.as<uint8_t>();
+  d.nbr_dn = m->d_nbr_dn.as<uint32_t>();
+  d.deg_dn = m->d_deg_dn.as<uint8_t>();
+  if ((s = hphi::build_hub_neighbours(d, 0, m->d_nbr_up.as<uint32_t>(), m->d_deg_up.as<uint8_t>(), st)).code) return s;
+  if ((s = hphi::build_hub_neighbours(d, 1, m->d_nbr_dn.as<uint32_t>(), m->d_deg_dn.as<uint8_t>(), st)).code) return s;
+  d.fast = 1;
+  return {};
+}
+
 hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
   HPHI_CUDA_TRY(cudaGetDevice(&m->device));
   hphi::Status s;
@@ -469,6 +517,7 @@ hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
     }
     d.dim = d.dim_up * d.dim_dn;
     m->dim = d.dim;
+    if ((s = build_hub_fast(m, st)).code) return s;
   }
   HPHI_CUDA_TRY(cudaStreamSynchronize(st));
   return {};
@@ -490,13 +539,29 @@ int launch_grid(int64_t work) {
   return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
-// Hubbard kernels iterate over (down row, chunk) items; clamp the grid to the item count
-int hv_grid_for(hphi_model* m, int nvec) {
-  if (m->kind == HPHI_HUBBARD) {
-    const int64_t chunks = (m->hdev.dim_up * nvec + hphi::kThreads - 1) / hphi::kThreads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(chunks * m->hdev.dim_dn, hphi::hv_grid(nvec)));
-  }
-  return launch_grid(m->dim * nvec);
+// Grid of an H v launch: every resident CTA slot of the kernel instance, clamped to the
+// number of work items (Hubbard: (down row, chunk) items; spin: kThreads-element chunks).
+bool use_hub_fast(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
+  return m->kind == HPHI_HUBBARD && hphi::hub_fast_ok(m->hdev, prec, m->cplx_model, nvec, epi);
+}
+
+int hv_grid_for(hphi_model* m, int nvec, int prec, hphi::Epi epi) {
+  if (use_hub_fast(m, prec, nvec, epi)) return hphi::hub_up_grid(m->hdev, prec, epi);
+  const bool hub = m->kind == HPHI_HUBBARD;
+  const int64_t cap = hphi::hv_resident_grid(hub, prec, m->cplx_model, epi);
+  int64_t work;
+  if (hub) work = ((m->hdev.dim_up * nvec + hphi::kThreads - 1) / hphi::kThreads) * m->hdev.dim_dn;
+  else work = (m->dim * nvec + hphi::kThreads - 1) / hphi::kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(work, cap));
+}
+
+// One H v (or fused step) launch: the two-pass Hubbard kernels when they apply (they need
+// a scratch vector for the fused steps), else the generic gather kernel.
+hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec, hphi::Epi epi,
+                       const hphi::FusedArgs& fa, int grid, void* scratch, cudaStream_t st) {
+  if (use_hub_fast(m, prec, nvec, epi) && (epi == hphi::Epi::kStore || scratch != nullptr))
+    return hphi::launch_hub_fast(m->hdev, prec, v, w, scratch, epi, fa, grid, st);
+  return hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec, epi, fa, grid, st);
 }
 
 }  // namespace
@@ -660,8 +725,8 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
     return fail(m, HPHI_ERR_INVALID_ARG, "apply_H: bad vectors, nvec or precision");
   if (v == w) return fail(m, HPHI_ERR_INVALID_ARG, "apply_H: v and w must not overlap");
   hphi::FusedArgs fa;
-  hphi::Status s = hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec,
-                                   hphi::Epi::kStore, fa, hv_grid_for(m, nvec), (cudaStream_t)stream);
+  hphi::Status s = hv_launch(m, prec, v, w, nvec, hphi::Epi::kStore, fa, hv_grid_for(m, nvec, prec, hphi::Epi::kStore),
+                             nullptr, (cudaStream_t)stream);
   return s.code ? fail(m, s) : HPHI_OK;
 }
 
@@ -699,9 +764,10 @@ hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanc
   const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (cplx ? 2 : 1);
   const int64_t n_real = m->dim * (cplx ? 2 : 1);
   const size_t vbytes = esz * (size_t)m->dim;
-  const int grid = hv_grid_for(m, 1);
+  const int grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
+  const int rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);
   const int vgrid = launch_grid(n_real);
-  const int pgrid = std::max(grid, vgrid);
+  const int pgrid = std::max(std::max(grid, rgrid), vgrid);
   Workspace& ws = m->ws;
   hphi::Status s;
   // the refinement's fp64 H x reuses buffer A, which must then hold an fp64 vector
@@ -709,6 +775,9 @@ hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanc
   if ((s = ws.vecA.ensure(need_a)).code) return s;
   if ((s = ws.vecB.ensure(vbytes)).code) return s;
   if (p->refine && (s = ws.x.ensure(8 * (size_t)n_real)).code) return s;
+  const bool fast = use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1);
+  if (fast && (s = ws.work.ensure(p->refine ? std::max(vbytes, (size_t)8 * (size_t)n_real) : vbytes)).code) return s;
+  void* scratch = fast ? ws.work.p : nullptr;
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * hphi::kMaxRedQ)).code) return s;
   // scalars: alpha[m], beta[m], sig[m+1], coef[m], s[16], tri[16 + 5m], done, steps_done
   const size_t nsc = 3 * (size_t)steps + 1 + steps + 16 + 16 + 5 * (size_t)steps + 4;
@@ -726,7 +795,6 @@ hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanc
   lz.steps_done = flags + 1;
   HPHI_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(double) * nsc, st));
   double* partials = ws.partials.as<double>();
-  const bool hub = m->kind == HPHI_HUBBARD;
   const double brk = p->breakdown > 0 ? p->breakdown : 1e-13;
 
   int launches = 0;
@@ -773,8 +841,7 @@ hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanc
       fa.done = lz.done;
       const bool timed = p->profile && !with_x;
       if (timed) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * k], st));
-      if ((q = hphi::launch_hv(hub, dev_model(m), prec, cplx, C, nullptr, 1, hphi::Epi::kLanczos1, fa, grid, st)).code)
-        return q;
+      if ((q = hv_launch(m, prec, C, nullptr, 1, hphi::Epi::kLanczos1, fa, grid, scratch, st)).code) return q;
       if (timed) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * k + 1], st));
       if ((q = hphi::launch_lz_fin1(lz, k, partials, grid, st)).code) return q;
       if ((q = hphi::launch_lz_pass2(prec, cplx, lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, n_real, partials,
@@ -851,9 +918,9 @@ hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanc
     hphi::FusedArgs fa;
     fa.out = hx;
     fa.partials = partials;
-    s = hphi::launch_hv(hub, dev_model(m), HPHI_FP64, cplx, ws.x.p, nullptr, 1, hphi::Epi::kRefine, fa, grid, st);
+    s = hv_launch(m, HPHI_FP64, ws.x.p, nullptr, 1, hphi::Epi::kRefine, fa, rgrid, scratch, st);
     if (s.code) return fail_out(s);
-    s = hphi::launch_refine_fin(lz, partials, grid, 0, st);
+    s = hphi::launch_refine_fin(lz, partials, rgrid, 0, st);
     if (s.code) return fail_out(s);
     s = hphi::launch_refine_resid(cplx, ws.x.as<double>(), hx, n_real, lz, partials, vgrid, st);
     if (s.code) return fail_out(s);
@@ -904,7 +971,7 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   const bool cplx = m->cplx_model;
   const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (cplx ? 2 : 1);
   const size_t vbytes = esz * (size_t)m->dim * nvec;
-  const int grid = hv_grid_for(m, nvec);
+  const int grid = hv_grid_for(m, nvec, prec, hphi::Epi::kTpq);
   const int vgrid = launch_grid(m->dim * nvec);
   const int pgrid = std::max(grid, vgrid);
   Workspace& ws = m->ws;
@@ -912,6 +979,9 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   if ((s = ws.vecA.ensure(vbytes)).code) return s;
   if ((s = ws.vecB.ensure(vbytes)).code) return s;
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * nvec * hphi::kMaxRedQ)).code) return s;
+  const bool tfast = use_hub_fast(m, prec, nvec, hphi::Epi::kTpq);
+  if (tfast && (s = ws.work.ensure(vbytes)).code) return s;
+  void* tscratch = tfast ? ws.work.p : nullptr;
   const size_t nsc = 2 * (size_t)nvec + 3 * (size_t)K * nvec;
   if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;
   hphi::TpqDev tq;
@@ -921,7 +991,6 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   tq.h2 = tq.u + (size_t)K * nvec;
   tq.nrm = tq.h2 + (size_t)K * nvec;
   double* partials = ws.partials.as<double>();
-  const bool hub = m->kind == HPHI_HUBBARD;
   const double ns = p->n_s > 0 ? p->n_s : (double)m->n_sites;
   const double inv_ns = 1.0 / ns;
 
@@ -954,8 +1023,7 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
       fa.partials = partials;
       fa.l = p->l;
       fa.inv_ns = inv_ns;
-      if ((q = hphi::launch_hv(hub, dev_model(m), prec, cplx, X, nullptr, nvec, hphi::Epi::kTpq, fa, grid, cap)).code)
-        return q;
+      if ((q = hv_launch(m, prec, X, nullptr, nvec, hphi::Epi::kTpq, fa, grid, tscratch, cap)).code) return q;
       if ((q = hphi::launch_tpq_fin(tq, k, nvec, inv_ns, partials, grid, cap)).code) return q;
       std::swap(X, Xn);
     }

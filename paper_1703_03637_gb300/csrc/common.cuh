@@ -97,6 +97,15 @@ struct HubDev {
   const uint32_t* rank;      // [2^N]
   const uint32_t* list_up;   // [dim_up]
   const uint32_t* list_dn;   // [dim_dn]
+  // two-pass path (real model, one hopping value per species): neighbour tables
+  // nbr[k * maxdeg + q] = rank of the q-th hop target of species state k | sign << 31
+  int fast;
+  int maxdeg_up, maxdeg_dn;
+  double c_up, c_dn;         // the hopping coefficient of each species
+  const uint32_t* nbr_up;
+  const uint8_t* deg_up;
+  const uint32_t* nbr_dn;
+  const uint8_t* deg_dn;
 };
 
 // ------------------------------------------------------------------ scalar traits
@@ -160,7 +169,17 @@ struct FusedArgs {
 // Launches w = H v (or a fused step) over all rows; grid chosen by the library.
 Status launch_hv(bool hubbard, const void* md, int prec, bool cplx, const void* v, void* w, int nvec, Epi epi,
                  const FusedArgs& fa, int grid, cudaStream_t st);
-int hv_grid(int nvec);  // persistent grid size used for fused launches (partials sizing)
+int hv_grid(int nvec);  // upper bound of any H v grid (partials sizing)
+
+// Two-pass Hubbard path (k_hub.cu): neighbour tables, and H v = diag + up hops (row tiles
+// in shared memory) + down hops (stripe-major row combinations into the scratch vector W).
+Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, cudaStream_t st);
+bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi);
+int hub_up_grid(const HubDev& md, int prec, Epi epi);
+Status launch_hub_fast(const HubDev& md, int prec, const void* v, void* w, void* scratch, Epi epi,
+                       const FusedArgs& fa, int grid_up, cudaStream_t st);
+// resident CTAs of the chosen kernel instance over the whole GPU (occupancy API)
+int hv_resident_grid(bool hubbard, int prec, bool cplx, Epi epi);
 
 // Streaming vector kernels and finalisers (k_solver.cu) -------------------------------
 struct LzDev {           // device scalars of one Lanczos run

@@ -1,0 +1,399 @@
+// Two-pass H v for Hubbard models with real hopping and one hopping value per spin
+// species (the half-filled square-lattice workloads): section 3.3's on-the-fly product,
+// laid out for GB300's memory hierarchy.
+//
+// The amplitudes form a matrix X[d][u] (down-spin rank d, up-spin rank u).  Down-spin
+// hops combine whole rows (W[d][:] = sum_q +-X[d'_q][:]) and up-spin hops act inside a row
+// (sum_q +-X[d][u'_q]).  So:
+//   pass D  walks column stripes in stripe-major order; the stripe of every row stays in
+//           L2 while all rows of that stripe are combined, so X is read from HBM about once.
+//           W receives the plain signed sums.
+//   pass U  stages K whole rows of X in shared memory, applies the up-spin neighbour table
+//           (built once per sector on the device) to all K rows at once, adds diag * X and
+//           coef * W, and runs the fused Lanczos / mTPQ epilogue.
+// fp64 sums use the exact fixed-point accumulator (integer pipes); fp32 sums are plain.
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "reduce.cuh"
+
+namespace hphi {
+
+namespace {
+
+constexpr int kUpThreads = 1024;
+// columns per thread in pass D (stripe = kThreads * EPT columns); the stripe of all rows is
+// the L2 working set of pass D
+#ifndef HPHI_DN_EPT32
+#define HPHI_DN_EPT32 4
+#endif
+#ifndef HPHI_DN_EPT64
+#define HPHI_DN_EPT64 1
+#endif
+
+// K consecutive values of a shared-memory row tile with the widest aligned accesses
+template <class R, int K>
+__device__ __forceinline__ void load_k(const R* p, R* out) {
+  if constexpr (sizeof(R) * K == 16) {
+    if constexpr (sizeof(R) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p);
+      out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+    } else {
+      const double2 t = *reinterpret_cast<const double2*>(p);
+      out[0] = t.x; out[1] = t.y;
+    }
+  } else if constexpr (sizeof(R) * K == 8 && sizeof(R) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    out[0] = t.x; out[1] = t.y;
+  } else {
+#pragma unroll
+    for (int m = 0; m < K; ++m) out[m] = p[m];
+  }
+}
+
+template <class R, int K>
+__device__ __forceinline__ void store_k(R* p, const R* v) {
+  if constexpr (sizeof(R) * K == 16) {
+    if constexpr (sizeof(R) == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else if constexpr (sizeof(R) * K == 8 && sizeof(R) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < K; ++m) p[m] = v[m];
+  }
+}
+constexpr int kSmemBudget = 208000;  // shared-memory bytes for the row tile (plus ~21 KB static)
+
+// neighbour table of one species, hop-slot major: nbr[q * n + k] is the q-th active hop
+// target of state k (rank | sign << 31), so threads of consecutive states read
+// consecutive words
+__global__ void k_hub_nbr(const HubDev md, int species, uint32_t* __restrict__ nbr, uint8_t* __restrict__ deg) {
+  const int64_t n = species ? md.dim_dn : md.dim_up;
+  const int e0 = species ? md.n_up_hops : 0;
+  const int ne = species ? md.n_dn_hops : md.n_up_hops;
+  const uint32_t* list = species ? md.list_dn : md.list_up;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = md.sector ? list[k] : (uint32_t)k;
+    int cnt = 0;
+    for (int q = 0; q < ne; ++q) {
+      const HopEntry h = md.hops[e0 + q];
+      if (((b >> h.i) ^ (b >> h.j)) & 1u) {
+        const uint32_t b2 = b ^ h.mask;
+        const uint32_t r2 = md.sector ? md.rank[b2] : b2;
+        const uint32_t sg = (uint32_t)(__popc(b & h.between) & 1);
+        nbr[(int64_t)cnt * n + k] = r2 | (sg << 31);
+        ++cnt;
+      }
+    }
+    deg[k] = (uint8_t)cnt;
+  }
+}
+
+// pass D: W[d][u] = sum over down-spin neighbours d' of d of +-X[d'][u].  Items run
+// stripe-major (stripe = kThreads * EPT columns) so one stripe of all rows is the L2
+// working set.  Each warp loads the row's neighbour list once (lane q holds entry q) and
+// broadcasts it with shuffles, so the data loads of four neighbours issue back to back.
+template <class R, int EPT>
+__global__ void __launch_bounds__(kThreads) k_hub_dn(const HubDev md, const R* __restrict__ X, R* __restrict__ W,
+                                                     const int* __restrict__ done) {
+  using A = typename SumAcc<R>::T;
+  if (done != nullptr && *done) return;
+  const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int SW = kThreads * EPT;
+  const int64_t dim_up = md.dim_up, dim_dn = md.dim_dn;
+  const int n_str = (int)((dim_up + SW - 1) / SW);
+  const int64_t n_items = (int64_t)n_str * dim_dn;
+  const int last_full = (int)(dim_up / SW);  // stripes [0, last_full) need no bounds checks
+
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int s = (int)(item / dim_dn);
+    const int64_t d = item - (int64_t)s * dim_dn;
+    const int deg = md.deg_dn[d];
+    const int u0 = s * SW + tid;
+    const bool full = s < last_full;
+    A acc[EPT];
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) acc[j].zero();
+    for (int qb = 0; qb < deg; qb += 32) {
+      const int nq = (deg - qb < 32) ? (deg - qb) : 32;
+      const uint32_t mine = (lane < nq) ? __ldg(md.nbr_dn + (int64_t)(qb + lane) * dim_dn + d) : 0u;
+      for (int q0 = 0; q0 < nq; q0 += 4) {
+        R x[4][EPT];
+        bool ng[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t e = __shfl_sync(0xffffffffu, mine, (q0 + t) & 31);
+          const bool on = q0 + t < nq;
+          ng[t] = (e >> 31) != 0;
+          const R* src = X + (int64_t)(e & 0x7fffffffu) * dim_up + u0;
+#pragma unroll
+          for (int j = 0; j < EPT; ++j) {
+            x[t][j] = (R)0;
+            if (on && (full || u0 + j * kThreads < dim_up)) x[t][j] = __ldg(src + j * kThreads);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int j = 0; j < EPT; ++j) acc[j].add(x[t][j], ng[t]);
+      }
+    }
+    R* dst = W + d * dim_up + u0;
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+      if (full || u0 + j * kThreads < dim_up) __stcs(dst + j * kThreads, (R)acc[j].value());
+    }
+  }
+}
+
+// pass U: up-spin hops on K rows staged in shared memory, diag, + c_dn W, fused epilogue
+template <class R, int K, Epi E>
+__global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R* __restrict__ X,
+                                                       const R* __restrict__ W, R* __restrict__ w, FusedArgs fa) {
+  using A = typename SumAcc<R>::T;
+  constexpr bool F64 = sizeof(R) == 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* tile = reinterpret_cast<R*>(smem_raw);
+  __shared__ LinGroup s_ulin[kMaxLin];
+  __shared__ LinGroup s_mlin[kMaxLin];
+  __shared__ PairEntry s_pair[kMaxPairs];
+  __shared__ R s_uc[kMaxLin], s_mc[kMaxLin], s_pcoef[kMaxPairGroups];  // coefficients in R
+  __shared__ double s_inv[1];
+  __shared__ double s_red[(kUpThreads / 32) * kMaxRedQ];
+
+  if (fa.done != nullptr && *fa.done) return;
+  const int tid = threadIdx.x;
+  for (int k = tid; k < md.n_ulin; k += kUpThreads) { s_ulin[k] = md.ulin[k]; s_uc[k] = (R)md.ulin[k].coef; }
+  for (int k = tid; k < md.n_mulin; k += kUpThreads) { s_mlin[k] = md.mulin[k]; s_mc[k] = (R)md.mulin[k].coef; }
+  for (int k = tid; k < md.n_pairs; k += kUpThreads) s_pair[k] = md.pairs[k];
+  for (int k = tid; k < md.n_pair_groups; k += kUpThreads) s_pcoef[k] = (R)md.pair_coef[k];
+  if constexpr (E == Epi::kTpq) {
+    if (tid == 0) s_inv[0] = fa.scal[0];
+  }
+  EpiScalars es{0.0, 0.0};
+  if constexpr (E == Epi::kLanczos1) {
+    es.c1 = fa.scal[0];
+    es.c2 = fa.scal[1];
+  }
+  const R c_up = (R)md.c_up, c_dn = (R)md.c_dn;
+  const bool same_c = md.c_up == md.c_dn;
+  Red<F64> red;
+  red.zero();
+  const int64_t dim_up = md.dim_up, dim_dn = md.dim_dn;
+  const int64_t n_tiles = (dim_dn + K - 1) / K;
+
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t d0 = t * K;
+    const int nk = (int)((dim_dn - d0 < K) ? (dim_dn - d0) : K);
+    __syncthreads();
+    // tile[u * K + m] = X[d0 + m][u]: the K rows interleaved, so one vector load per
+    // neighbour fetches the value of all K rows
+    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+      R vals[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) vals[m] = (m < nk) ? __ldg(X + (d0 + m) * dim_up + u) : (R)0;
+      store_k<R, K>(tile + u * K, vals);
+    }
+    __syncthreads();
+    uint32_t dn[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) dn[m] = (m < nk) ? (md.sector ? __ldg(md.list_dn + d0 + m) : (uint32_t)(d0 + m)) : 0u;
+    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+      const uint32_t up = md.sector ? __ldg(md.list_up + u) : (uint32_t)u;
+      const int deg = md.deg_up[u];
+      const uint32_t* nb = md.nbr_up + u;
+      A acc[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) acc[m].zero();
+      const int du = (int)dim_up;  // neighbour tables hold < 2^28 entries
+      int q = 0;
+      for (; q + 2 <= deg; q += 2) {
+        const uint32_t e0 = __ldg(nb + q * du), e1 = __ldg(nb + (q + 1) * du);
+        R v0[K], v1[K];
+        load_k<R, K>(tile + (int)(e0 & 0x7fffffffu) * K, v0);
+        load_k<R, K>(tile + (int)(e1 & 0x7fffffffu) * K, v1);
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          acc[m].add(v0[m], (e0 >> 31) != 0);
+          acc[m].add(v1[m], (e1 >> 31) != 0);
+        }
+      }
+      if (q < deg) {
+        const uint32_t e0 = __ldg(nb + q * du);
+        R v0[K];
+        load_k<R, K>(tile + (int)(e0 & 0x7fffffffu) * K, v0);
+#pragma unroll
+        for (int m = 0; m < K; ++m) acc[m].add(v0[m], (e0 >> 31) != 0);
+      }
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        if (m >= nk) break;
+        const int64_t idx = (d0 + m) * dim_up + u;
+        const R x = tile[u * K + m];
+        // diagonal: integer counts times the class coefficients
+        R dg = (R)md.c0;
+        for (int g = 0; g < md.n_ulin; ++g) dg += s_uc[g] * (R)__popc(up & dn[m] & (uint32_t)s_ulin[g].mask);
+        for (int g = 0; g < md.n_mulin; ++g) {
+          const uint32_t mk = (uint32_t)s_mlin[g].mask;
+          dg += s_mc[g] * (R)(__popc(up & mk) + __popc(dn[m] & mk));
+        }
+        if (md.n_pairs) {
+          int grp = s_pair[0].grp, cnt = 0;
+          for (int p = 0; p < md.n_pairs; ++p) {
+            const PairEntry pe = s_pair[p];
+            if (pe.grp != grp) {
+              dg += s_pcoef[grp] * (R)cnt;
+              cnt = 0;
+              grp = pe.grp;
+            }
+            const int ni = (int)((up >> pe.i) & 1u) + (int)((dn[m] >> pe.i) & 1u);
+            const int nj = (int)((up >> pe.j) & 1u) + (int)((dn[m] >> pe.j) & 1u);
+            cnt += ni * nj;
+          }
+          dg += s_pcoef[grp] * (R)cnt;
+        }
+        R hv;
+        if (same_c) {
+          acc[m].add(W[idx], false);
+          hv = dg * x + c_up * (R)acc[m].value();
+        } else {
+          hv = dg * x + c_up * (R)acc[m].value() + c_dn * W[idx];
+        }
+        epilogue<R, E>(idx, 0, x, (R)0, hv, (R)0, w, fa, es, s_inv, red);
+      }
+    }
+  }
+  if constexpr (E != Epi::kStore) {
+    // fixed-order reduction: warp shuffles, then the warps' sums in warp order
+    constexpr int nq = n_red<E>();
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < nq; ++q) {
+      double x = red.get(q);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) s_red[wid * kMaxRedQ + q] = x;
+    }
+    __syncthreads();
+    if (tid < nq) {
+      double x = 0.0;
+      for (int k = 0; k < kUpThreads / 32; ++k) x += s_red[k * kMaxRedQ + tid];
+      fa.partials[(size_t)blockIdx.x * kMaxRedQ + tid] = x;
+    }
+  }
+}
+
+template <class R>
+int pick_k(const HubDev& md) {
+  const int64_t row = md.dim_up * (int64_t)sizeof(R);
+  if (4 * row <= kSmemBudget) return 4;
+  if (2 * row <= kSmemBudget) return 2;
+  return 1;
+}
+
+template <class R, int K, Epi E>
+int up_occupancy() {
+  static int b = 0;
+  if (b == 0) {
+    // the dynamic tile size varies per model; occupancy is computed for the budget
+    int n = 0;
+    cudaFuncSetAttribute(k_hub_up<R, K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hub_up<R, K, E>, kUpThreads, kSmemBudget) != cudaSuccess ||
+        n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    b = n;
+  }
+  return b;
+}
+
+template <class R, int K, Epi E>
+Status launch_up(const HubDev& md, const R* X, const R* W, R* w, const FusedArgs& fa, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)K * md.dim_up * sizeof(R);
+  HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up<R, K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+  k_hub_up<R, K, E><<<grid, kUpThreads, smem, st>>>(md, X, W, w, fa);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+template <class R, Epi E>
+Status launch_r(const HubDev& md, const void* v, void* w, void* scratch, const FusedArgs& fa, int grid_up,
+                cudaStream_t st) {
+  const R* X = reinterpret_cast<const R*>(v);
+  // kStore writes the down-spin sums into w and finishes them in place; the fused steps
+  // use the scratch vector
+  R* W = (E == Epi::kStore) ? reinterpret_cast<R*>(w) : reinterpret_cast<R*>(scratch);
+  constexpr int EPT = sizeof(R) == 8 ? HPHI_DN_EPT64 : HPHI_DN_EPT32;
+  const int64_t sw = (int64_t)kThreads * EPT;
+  const int64_t items = ((md.dim_up + sw - 1) / sw) * md.dim_dn;
+  const int gd = (int)std::min<int64_t>(items, (int64_t)num_sms() * 8);
+  k_hub_dn<R, EPT><<<gd, kThreads, 0, st>>>(md, X, W, fa.done);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  R* out = reinterpret_cast<R*>(w);
+  switch (pick_k<R>(md)) {
+    case 4: return launch_up<R, 4, E>(md, X, W, out, fa, grid_up, st);
+    case 2: return launch_up<R, 2, E>(md, X, W, out, fa, grid_up, st);
+    default: return launch_up<R, 1, E>(md, X, W, out, fa, grid_up, st);
+  }
+}
+
+template <class R>
+int up_grid_r(const HubDev& md, Epi epi) {
+  int occ = 1;
+  const int k = pick_k<R>(md);
+#define HPHI_OCC(KK)                                                         \
+  switch (epi) {                                                             \
+    case Epi::kStore: occ = up_occupancy<R, KK, Epi::kStore>(); break;       \
+    case Epi::kLanczos1: occ = up_occupancy<R, KK, Epi::kLanczos1>(); break; \
+    case Epi::kTpq: occ = up_occupancy<R, KK, Epi::kTpq>(); break;           \
+    case Epi::kRefine: occ = up_occupancy<R, KK, Epi::kRefine>(); break;     \
+  }
+  if (k == 4) { HPHI_OCC(4) } else if (k == 2) { HPHI_OCC(2) } else { HPHI_OCC(1) }
+#undef HPHI_OCC
+  const int64_t tiles = (md.dim_dn + k - 1) / k;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * occ));
+}
+
+}  // namespace
+
+Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, cudaStream_t st) {
+  const int64_t n = species ? md.dim_dn : md.dim_up;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)num_sms() * 8));
+  k_hub_nbr<<<g, kThreads, 0, st>>>(md, species, nbr, deg);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi) {
+  if (!md.fast || cplx || nvec != 1) return false;
+  if (epi == Epi::kRefine && prec != HPHI_FP64) return false;
+  const int64_t row = md.dim_up * (int64_t)(prec == HPHI_FP64 ? 8 : 4);
+  return row <= kSmemBudget;
+}
+
+int hub_up_grid(const HubDev& md, int prec, Epi epi) {
+  return prec == HPHI_FP64 ? up_grid_r<double>(md, epi) : up_grid_r<float>(md, epi);
+}
+
+Status launch_hub_fast(const HubDev& md, int prec, const void* v, void* w, void* scratch, Epi epi,
+                       const FusedArgs& fa, int grid_up, cudaStream_t st) {
+  if (prec == HPHI_FP64) {
+    switch (epi) {
+      case Epi::kStore: return launch_r<double, Epi::kStore>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kLanczos1: return launch_r<double, Epi::kLanczos1>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kTpq: return launch_r<double, Epi::kTpq>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kRefine: return launch_r<double, Epi::kRefine>(md, v, w, scratch, fa, grid_up, st);
+    }
+  } else {
+    switch (epi) {
+      case Epi::kStore: return launch_r<float, Epi::kStore>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kLanczos1: return launch_r<float, Epi::kLanczos1>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kTpq: return launch_r<float, Epi::kTpq>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kRefine: break;
+    }
+  }
+  return {HPHI_ERR_INVALID_ARG, "two-pass Hubbard path: unsupported precision / epilogue"};
+}
+
+}  // namespace hphi

@@ -13,128 +13,25 @@
 #include "basis.cuh"
 #include "common.cuh"
 #include "reduce.cuh"
+#include "epilogue.cuh"
 
 namespace hphi {
 
 namespace {
 
-// Per-column CTA reduction in a fixed tree order; partials[(block * nvec + c) * kMaxRedQ + q].
-template <bool F64>
-__device__ void block_finish(const Red<F64>& red, int nq, int nvec, double* __restrict__ partials, double* sm) {
-  const int tid = threadIdx.x;
-  for (int q = 0; q < nq; ++q) sm[q * kThreads + tid] = red.get(q);
-  __syncthreads();
-  for (int off = kThreads / 2; off >= nvec; off >>= 1) {
-    if (tid < off) {
-      for (int q = 0; q < nq; ++q) sm[q * kThreads + tid] += sm[q * kThreads + tid + off];
-    }
-    __syncthreads();
-  }
-  if (tid < nvec) {
-    for (int q = 0; q < nq; ++q) partials[((size_t)blockIdx.x * nvec + tid) * kMaxRedQ + q] = sm[q * kThreads + tid];
-  }
-}
-
-// ------------------------------------------------------------------ element access
-template <class S>
-__device__ __forceinline__ void ld(const S* __restrict__ p, int64_t i, typename Traits<S>::R& re,
-                                   typename Traits<S>::R& im) {
-  if constexpr (Traits<S>::kCplx) {
-    const S x = p[i];
-    re = x.x;
-    im = x.y;
-  } else {
-    re = p[i];
-    im = 0;
-  }
-}
-
-template <class S>
-__device__ __forceinline__ void st(S* __restrict__ p, int64_t i, typename Traits<S>::R re, typename Traits<S>::R im) {
-  if constexpr (Traits<S>::kCplx) {
-    S x;
-    x.x = re;
-    x.y = im;
-    p[i] = x;
-  } else {
-    p[i] = re;
-  }
-}
-
-// acc += phase(code) * x, code: 1 (+1), 2 (+i), 3 (-1), 4 (-i)
-template <class R>
-__device__ __forceinline__ void acc_phase(int code, R xr, R xi, R& ar, R& ai) {
-  switch (code) {
-    case 1: ar += xr; ai += xi; break;
-    case 2: ar -= xi; ai += xr; break;
-    case 3: ar -= xr; ai -= xi; break;
-    default: ar += xi; ai -= xr; break;
-  }
-}
-
-// ------------------------------------------------------------------ epilogues
-struct EpiScalars {
-  double c1, c2;  // Lanczos pass 1
-};
-
-template <class S, Epi E>
-__device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>::R sr, typename Traits<S>::R si,
-                                         typename Traits<S>::R hr, typename Traits<S>::R hi, S* __restrict__ w,
-                                         const FusedArgs& fa, const EpiScalars& es, const double* s_inv,
-                                         Red<Traits<S>::kF64>& red) {
-  using R = typename Traits<S>::R;
-  constexpr bool C = Traits<S>::kCplx;
-  if constexpr (E == Epi::kStore) {
-    st<S>(w, idx, hr, hi);
-  } else if constexpr (E == Epi::kLanczos1) {
-    // P <- sigma_k * (H C) - beta_k sigma_{k-1} * P ;  partial <C, H C>
-    S* P = reinterpret_cast<S*>(fa.out);
-    R pr, pi;
-    ld<S>(P, idx, pr, pi);
-    const R c1 = (R)es.c1, c2 = (R)es.c2;
-    st<S>(P, idx, c1 * hr - c2 * pr, c1 * hi - c2 * pi);
-    red.add(0, sr, hr);
-    if constexpr (C) red.add(0, si, hi);
-    red.tick();
-  } else if constexpr (E == Epi::kTpq) {
-    // X_{k+1} = (l X_k - H X_k / N_s) / |X_k| ; partials <X, HX>, |HX|^2, |X_{k+1}|^2
-    S* Xn = reinterpret_cast<S*>(fa.out);
-    const R inv = (R)s_inv[c], l = (R)fa.l, ins = (R)fa.inv_ns;
-    const R nr = inv * (l * sr - hr * ins);
-    const R ni = inv * (l * si - hi * ins);
-    st<S>(Xn, idx, nr, ni);
-    red.add(0, sr, hr);
-    red.add(1, hr, hr);
-    red.add(2, nr, nr);
-    if constexpr (C) {
-      red.add(0, si, hi);
-      red.add(1, hi, hi);
-      red.add(2, ni, ni);
-    }
-    red.tick();
-  } else {  // kRefine: Hx stored; partials <x, Hx>, <x, x>, <Hx, Hx>
-    st<S>(reinterpret_cast<S*>(fa.out), idx, hr, hi);
-    red.add(0, sr, hr);
-    red.add(1, sr, sr);
-    red.add(2, hr, hr);
-    if constexpr (C) {
-      red.add(0, si, hi);
-      red.add(1, si, si);
-      red.add(2, hi, hi);
-    }
-    red.tick();
-  }
-}
-
-template <Epi E> __host__ __device__ constexpr int n_red() {
-  return E == Epi::kStore ? 0 : (E == Epi::kLanczos1 ? 1 : 3);
-}
-
 // ------------------------------------------------------------------ spin kernel
+// One thread per output element.  Patterns are visited in unrolled batches of kBatch:
+// the active test, rank and address of every pattern in a batch are computed first and
+// the batch's loads are issued together (predicated on the phase code), so each thread
+// keeps kBatch gathers in flight instead of one.  Class boundaries are the same for every
+// thread (patterns are sorted by class), so class flushes never diverge.
+constexpr int kBatch = 8;
+
 template <class S, Epi E>
 __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S* __restrict__ v, S* __restrict__ w,
                                                       int nvec, int lg_nvec, FusedArgs fa) {
   using R = typename Traits<S>::R;
+  using A = typename SumAcc<R>::T;
   constexpr bool C = Traits<S>::kCplx;
   constexpr bool F64 = Traits<S>::kF64;
   __shared__ SpinEntry s_ent[kMaxSpinEntries];
@@ -215,43 +112,63 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
     ld<S>(v, idx, sr, si);
     R hr = d * sr, hi = d * si;
 
-    // off-diagonal XOR patterns, summed per coefficient class
-    R ar = 0, ai = 0;
+    A ar, ai;
+    ar.zero();
+    ai.zero();
     int cur = n_ent ? s_ent[0].cls : 0;
-    for (int e = 0; e < n_ent; ++e) {
-      const SpinEntry en = s_ent[e];
-      if (en.cls != cur) {
-        const double2 cc = s_cls[cur];
-        if constexpr (C) {
-          hr += (R)cc.x * ar - (R)cc.y * ai;
-          hi += (R)cc.x * ai + (R)cc.y * ar;
-        } else {
-          hr += (R)cc.x * ar;
+    for (int e0 = 0; e0 < n_ent; e0 += kBatch) {
+      R xr[kBatch], xi[kBatch];
+      int code[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = e0 + j;
+        code[j] = 0;
+        xr[j] = 0;
+        xi[j] = 0;
+        if (k < n_ent) {
+          const SpinEntry en = s_ent[k];
+          const int sel = (int)((s >> en.i) & 1ull) | ((int)((s >> en.j) & 1ull) << 1);
+          code[j] = (en.phases >> (3 * sel)) & 7;
+          if (code[j]) {
+            const uint64_t s2 = s ^ en.mask;
+            const uint64_t r2 = md.sector ? sector_rank(md.t, s2) : s2;
+            ld<S>(v, (int64_t)r2 * nvec + c, xr[j], xi[j]);
+          }
         }
-        ar = 0;
-        ai = 0;
-        cur = en.cls;
       }
-      const int sel = (int)((s >> en.i) & 1ull) | ((int)((s >> en.j) & 1ull) << 1);
-      const int code = (en.phases >> (3 * sel)) & 7;
-      if (!code) continue;
-      const uint64_t s2 = s ^ en.mask;
-      const uint64_t r2 = md.sector ? sector_rank(md.t, s2) : s2;
-      R xr, xi;
-      ld<S>(v, (int64_t)r2 * nvec + c, xr, xi);
-      if constexpr (C) {
-        acc_phase<R>(code, xr, xi, ar, ai);
-      } else {
-        ar += (code == 1) ? xr : -xr;
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = e0 + j;
+        if (k < n_ent) {
+          const int cls = s_ent[k].cls;
+          if (cls != cur) {
+            const double2 cc = s_cls[cur];
+            const R vr = (R)ar.value(), vi = (R)ai.value();
+            if constexpr (C) {
+              hr += (R)cc.x * vr - (R)cc.y * vi;
+              hi += (R)cc.x * vi + (R)cc.y * vr;
+            } else {
+              hr += (R)cc.x * vr;
+            }
+            ar.zero();
+            ai.zero();
+            cur = cls;
+          }
+          if (code[j]) {
+            if constexpr (C) acc_phase<A, R>(code[j], xr[j], xi[j], ar, ai);
+            else ar.add(xr[j], code[j] != 1);
+          }
+        }
       }
     }
     if (n_ent) {
       const double2 cc = s_cls[cur];
+      const R vr = (R)ar.value(), vi = (R)ai.value();
       if constexpr (C) {
-        hr += (R)cc.x * ar - (R)cc.y * ai;
-        hi += (R)cc.x * ai + (R)cc.y * ar;
+        hr += (R)cc.x * vr - (R)cc.y * vi;
+        hi += (R)cc.x * vi + (R)cc.y * vr;
       } else {
-        hr += (R)cc.x * ar;
+        hr += (R)cc.x * vr;
       }
     }
     epilogue<S, E>(idx, c, sr, si, hr, hi, w, fa, es, s_inv, red);
@@ -260,10 +177,16 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
 }
 
 // ------------------------------------------------------------------ Hubbard kernel
+// Work item = (down-spin row d, chunk of kThreads consecutive (up, vector) elements).
+// Down-spin hops depend only on d, so warp 0 builds the row's compacted neighbour list
+// (source row, sign, direction, class) in shared memory once per item and every thread
+// walks it uniformly in batches of kBatch coalesced loads.  Up-spin hops depend on each
+// thread's up configuration and are visited in predicated batches of kBatch.
 template <class S, Epi E>
 __global__ void __launch_bounds__(kThreads) k_hv_hub(const HubDev md, const S* __restrict__ v, S* __restrict__ w,
                                                      int nvec, int lg_nvec, FusedArgs fa) {
   using R = typename Traits<S>::R;
+  using A = typename SumAcc<R>::T;
   constexpr bool C = Traits<S>::kCplx;
   constexpr bool F64 = Traits<S>::kF64;
   __shared__ HopEntry s_hop[kMaxHops];
@@ -273,11 +196,15 @@ __global__ void __launch_bounds__(kThreads) k_hv_hub(const HubDev md, const S* _
   __shared__ PairEntry s_pair[kMaxPairs];
   __shared__ double s_pcoef[kMaxPairGroups];
   __shared__ double s_inv[kMaxNvec];
+  __shared__ int64_t s_dl_src[kMaxHops];   // source element offset of neighbour row d'
+  __shared__ uint32_t s_dl_meta[kMaxHops];  // bit 0 negative sign, bit 1 direction b, class << 2
+  __shared__ int s_dl_n;
   __shared__ double s_red[(E == Epi::kStore) ? 1 : kThreads * kMaxRedQ];
 
   if (fa.done != nullptr && *fa.done) return;
   const int tid = threadIdx.x;
-  const int n_hops = md.n_up_hops + md.n_dn_hops;
+  const int n_up = md.n_up_hops, n_dn = md.n_dn_hops;
+  const int n_hops = n_up + n_dn;
   for (int k = tid; k < n_hops; k += kThreads) s_hop[k] = md.hops[k];
   for (int k = tid; k < md.n_classes; k += kThreads) s_cls[k] = md.cls_coef[k];
   for (int k = tid; k < md.n_ulin; k += kThreads) s_ulin[k] = md.ulin[k];
@@ -303,6 +230,38 @@ __global__ void __launch_bounds__(kThreads) k_hv_hub(const HubDev md, const S* _
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int64_t d = item / nchunk;
     const int64_t e = (item - d * nchunk) * kThreads + tid;
+    const uint32_t dn = md.sector ? __ldg(md.list_dn + d) : (uint32_t)d;
+    // neighbour list of row d (ordered, so classes stay grouped)
+    __syncthreads();
+    if (tid < 32) {
+      int cnt = 0;
+      for (int k0 = 0; k0 < n_dn; k0 += 32) {
+        const int k = k0 + tid;
+        bool on = false;
+        int64_t src = 0;
+        uint32_t meta = 0;
+        if (k < n_dn) {
+          const HopEntry h = s_hop[n_up + k];
+          const uint32_t bi = (dn >> h.i) & 1u, bj = (dn >> h.j) & 1u;
+          if (bi != bj) {
+            on = true;
+            const uint32_t b2 = dn ^ h.mask;
+            const int64_t d2 = md.sector ? (int64_t)__ldg(md.rank + b2) : (int64_t)b2;
+            src = d2 * md.dim_up * nvec;
+            meta = (uint32_t)(__popc(dn & h.between) & 1) | ((bi ? 0u : 1u) << 1) | ((uint32_t)h.cls << 2);
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (on) {
+          const int pos = cnt + __popc(bal & ((1u << tid) - 1u));
+          s_dl_src[pos] = src;
+          s_dl_meta[pos] = meta;
+        }
+        cnt += __popc(bal);
+      }
+      if (tid == 0) s_dl_n = cnt;
+    }
+    __syncthreads();
     if (e >= row_elems) continue;
     int64_t u;
     int c;
@@ -314,7 +273,6 @@ __global__ void __launch_bounds__(kThreads) k_hv_hub(const HubDev md, const S* _
       c = (int)(e - u * nvec);
     }
     const uint32_t up = md.sector ? __ldg(md.list_up + u) : (uint32_t)u;
-    const uint32_t dn = md.sector ? __ldg(md.list_dn + d) : (uint32_t)d;
     const int64_t row_base = d * md.dim_up;
     const int64_t idx = (row_base + u) * nvec + c;
 
@@ -344,53 +302,128 @@ __global__ void __launch_bounds__(kThreads) k_hv_hub(const HubDev md, const S* _
     ld<S>(v, idx, sr, si);
     R hr = dg * sr, hi = dg * si;
 
-    // hops: (i set, j empty) -> coef, (j set, i empty) -> conj(coef); sign from the bits between
-    for (int part = 0; part < 2; ++part) {
-      const int e0 = part ? md.n_up_hops : 0;
-      const int e1 = part ? n_hops : md.n_up_hops;
-      if (e0 == e1) continue;
-      const uint32_t bits = part ? dn : up;
-      R a_r = 0, a_i = 0, b_r = 0, b_i = 0;
-      int cur = s_hop[e0].cls;
-      for (int k = e0; k <= e1; ++k) {
-        const bool last = (k == e1);
-        if (last || s_hop[k].cls != cur) {
-          const double2 cc = s_cls[cur];
-          if constexpr (C) {
-            // coef * a + conj(coef) * b
-            hr += (R)cc.x * (a_r + b_r) - (R)cc.y * (a_i - b_i);
-            hi += (R)cc.x * (a_i + b_i) + (R)cc.y * (a_r - b_r);
-          } else {
-            hr += (R)cc.x * a_r;
+    // coef * a + conj(coef) * b for one class
+    A ar, ai, br, bi_;
+    ar.zero(); ai.zero(); br.zero(); bi_.zero();
+    auto flush = [&](int cls) {
+      const double2 cc = s_cls[cls];
+      if constexpr (C) {
+        const R a_r = (R)ar.value(), a_i = (R)ai.value(), b_r = (R)br.value(), b_i = (R)bi_.value();
+        hr += (R)cc.x * (a_r + b_r) - (R)cc.y * (a_i - b_i);
+        hi += (R)cc.x * (a_i + b_i) + (R)cc.y * (a_r - b_r);
+        br.zero();
+        bi_.zero();
+      } else {
+        hr += (R)cc.x * (R)ar.value();
+      }
+      ar.zero();
+      ai.zero();
+    };
+
+    // up hops: predicated batches
+    int cur = n_up ? s_hop[0].cls : 0;
+    for (int k0 = 0; k0 < n_up; k0 += kBatch) {
+      R xr[kBatch], xi[kBatch];
+      uint32_t fl[kBatch];  // bit 0 active, bit 1 negative, bit 2 direction b
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j;
+        fl[j] = 0;
+        xr[j] = 0;
+        xi[j] = 0;
+        if (k < n_up) {
+          const HopEntry h = s_hop[k];
+          const uint32_t bi = (up >> h.i) & 1u, bj = (up >> h.j) & 1u;
+          if (bi != bj) {
+            const uint32_t b2 = up ^ h.mask;
+            const int64_t u2 = md.sector ? (int64_t)__ldg(md.rank + b2) : (int64_t)b2;
+            ld<S>(v, (row_base + u2) * nvec + c, xr[j], xi[j]);
+            fl[j] = 1u | ((uint32_t)(__popc(up & h.between) & 1) << 1) | ((bi ? 0u : 1u) << 2);
           }
-          a_r = a_i = b_r = b_i = 0;
-          if (last) break;
-          cur = s_hop[k].cls;
         }
-        const HopEntry h = s_hop[k];
-        const uint32_t bi = (bits >> h.i) & 1u, bj = (bits >> h.j) & 1u;
-        if (bi == bj) continue;
-        const uint32_t b2 = bits ^ h.mask;
-        const int64_t k2 = md.sector ? (int64_t)__ldg(md.rank + b2) : (int64_t)b2;
-        const int64_t src = part ? ((k2 * md.dim_up + u) * nvec + c) : ((row_base + k2) * nvec + c);
-        R xr, xi;
-        ld<S>(v, src, xr, xi);
-        const bool neg = (__popc(bits & h.between) & 1) != 0;
-        if (neg) {
-          xr = -xr;
-          xi = -xi;
-        }
-        if constexpr (C) {
-          if (bi) { a_r += xr; a_i += xi; }
-          else { b_r += xr; b_i += xi; }
-        } else {
-          a_r += xr;
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j;
+        if (k < n_up) {
+          const int cls = s_hop[k].cls;
+          if (cls != cur) {
+            flush(cur);
+            cur = cls;
+          }
+          if (fl[j] & 1u) {
+            const bool neg = (fl[j] & 2u) != 0;
+            if constexpr (C) {
+              if (!(fl[j] & 4u)) { ar.add(xr[j], neg); ai.add(xi[j], neg); }
+              else { br.add(xr[j], neg); bi_.add(xi[j], neg); }
+            } else {
+              ar.add(xr[j], neg);
+            }
+          }
         }
       }
     }
+    if (n_up) flush(cur);
+
+    // down hops: row-uniform compacted list, batches of coalesced loads
+    const int ndl = s_dl_n;
+    const int64_t off = u * nvec + c;
+    cur = ndl ? (int)(s_dl_meta[0] >> 2) : 0;
+    for (int q0 = 0; q0 < ndl; q0 += kBatch) {
+      R xr[kBatch], xi[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        xr[j] = 0;
+        xi[j] = 0;
+        if (q0 + j < ndl) ld<S>(v, s_dl_src[q0 + j] + off, xr[j], xi[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int q = q0 + j;
+        if (q < ndl) {
+          const uint32_t meta = s_dl_meta[q];
+          const int cls = (int)(meta >> 2);
+          if (cls != cur) {
+            flush(cur);
+            cur = cls;
+          }
+          const bool neg = (meta & 1u) != 0;
+          if constexpr (C) {
+            if (!(meta & 2u)) { ar.add(xr[j], neg); ai.add(xi[j], neg); }
+            else { br.add(xr[j], neg); bi_.add(xi[j], neg); }
+          } else {
+            ar.add(xr[j], neg);
+          }
+        }
+      }
+    }
+    if (ndl) flush(cur);
     epilogue<S, E>(idx, c, sr, si, hr, hi, w, fa, es, s_inv, red);
   }
   if constexpr (E != Epi::kStore) block_finish<F64>(red, n_red<E>(), nvec, fa.partials, s_red);
+}
+
+template <class S, Epi E>
+int occupancy_t(bool hub) {
+  static int cache[2] = {0, 0};
+  int& b = cache[hub ? 1 : 0];
+  if (b == 0) {
+    int n = 0;
+    cudaError_t e = hub ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hv_hub<S, E>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hv_spin<S, E>, kThreads, 0);
+    if (e != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 2;
+    }
+    b = n;
+  }
+  return b;
+}
+
+template <Epi E>
+int occupancy_e(bool hub, int prec, bool cplx) {
+  if (prec == HPHI_FP64) return cplx ? occupancy_t<double2, E>(hub) : occupancy_t<double, E>(hub);
+  return cplx ? occupancy_t<float2, E>(hub) : occupancy_t<float, E>(hub);
 }
 
 template <class S, Epi E>
@@ -427,7 +460,18 @@ Status launch_e(bool hub, const void* md, int prec, bool cplx, const void* v, vo
 
 int hv_grid(int nvec) {
   (void)nvec;
-  return num_sms() * 4;
+  return num_sms() * (2048 / kThreads);
+}
+
+int hv_resident_grid(bool hubbard, int prec, bool cplx, Epi epi) {
+  int b = 2;
+  switch (epi) {
+    case Epi::kStore: b = occupancy_e<Epi::kStore>(hubbard, prec, cplx); break;
+    case Epi::kLanczos1: b = occupancy_e<Epi::kLanczos1>(hubbard, prec, cplx); break;
+    case Epi::kTpq: b = occupancy_e<Epi::kTpq>(hubbard, prec, cplx); break;
+    case Epi::kRefine: b = occupancy_e<Epi::kRefine>(hubbard, HPHI_FP64, cplx); break;
+  }
+  return num_sms() * b;
 }
 
 Status launch_hv(bool hubbard, const void* md, int prec, bool cplx, const void* v, void* w, int nvec, Epi epi,

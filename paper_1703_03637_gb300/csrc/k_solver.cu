@@ -34,10 +34,6 @@ __device__ double sum_partials(const double* __restrict__ partials, int grid, in
   return block_sum(s, sm);
 }
 
-template <class S> struct VT;
-template <> struct VT<double> { static constexpr int kW = 1; using R = double; };
-template <> struct VT<float> { static constexpr int kW = 1; using R = float; };
-
 // ------------------------------------------------------------------ Lanczos start
 // C <- (storage precision) v0 (if given); P <- 0; partial |C|^2.  Elements counted as reals.
 template <class R>

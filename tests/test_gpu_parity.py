@@ -120,6 +120,8 @@ HV_CASES = [
     ("hubbard_3x4_66", lambda: wl.hubbard_square(4, 3).with_basis(wl.BASIS_NUMBER, 6, 6)),
     ("hubbard_random_complex", lambda: wl.random_hubbard_model(6, 12, seed=4).with_basis(wl.BASIS_NUMBER, 3, 2)),
     ("hubbard_full", lambda: wl.random_hubbard_model(5, 9, seed=6, complex_=False)),
+    ("hubbard_ring7_full_two_pass", lambda: wl.hubbard_ring(7, 1.0, 4.0)),
+    ("hubbard_2x5_54_two_pass", lambda: wl.hubbard_square(5, 2, 1.0, 8.0).with_basis(wl.BASIS_NUMBER, 5, 4)),
 ]
 
 
@@ -139,7 +141,10 @@ def test_apply_H_fp64(name, mk, nvec):
     assert _rel(w, ref) < 1e-12
 
 
-@pytest.mark.parametrize("name,mk", HV_CASES[:8], ids=[c[0] for c in HV_CASES[:8]])
+FP32_CASES = HV_CASES[:8] + HV_CASES[10:]
+
+
+@pytest.mark.parametrize("name,mk", FP32_CASES, ids=[c[0] for c in FP32_CASES])
 def test_apply_H_fp32(name, mk):
     spec = mk()
     m = hp.Model.from_spec(spec)
@@ -236,6 +241,17 @@ def test_lanczos_random_start_is_seeded():
     v0 = m.random_vector(99)[:, 0]
     r3 = m.lanczos(30, v0=v0)
     assert np.array_equal(r1["alpha"], r3["alpha"])
+
+
+def test_lanczos_hubbard_two_pass_fp32_refined():
+    spec = wl.hubbard_square(4, 3, 1.0, 8.0).with_basis(wl.BASIS_NUMBER, 6, 6)
+    m = hp.Model.from_spec(spec)
+    v0 = wl.gaussian_vector(43, m.dim)[:, 0]
+    a, b = oracle.lanczos(spec, v0, 20)
+    r64 = m.lanczos(20, prec=hp.FP64, v0=torch.as_tensor(v0))
+    assert _rel(r64["alpha"][:12], a[:12]) < 1e-12 and _rel(r64["beta"][:12], b[:12]) < 1e-12
+    r32 = m.lanczos(20, prec=hp.FP32, v0=torch.as_tensor(v0))
+    assert _rel(r32["alpha"][:8], a[:8]) < 1e-5
 
 
 def test_lanczos_mixed_with_fp64_refinement():
