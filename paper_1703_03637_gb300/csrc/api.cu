@@ -559,7 +559,7 @@ int hv_grid_for(hphi_model* m, int nvec, int prec, hphi::Epi epi) {
 // a scratch vector for the fused steps), else the generic gather kernel.
 hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec, hphi::Epi epi,
                        const hphi::FusedArgs& fa, int grid, void* scratch, cudaStream_t st) {
-  if (use_hub_fast(m, prec, nvec, epi) && (epi == hphi::Epi::kStore || scratch != nullptr))
+  if (use_hub_fast(m, prec, nvec, epi) && (hphi::hub_scratch_bytes(m->hdev, prec, epi) == 0 || scratch != nullptr))
     return hphi::launch_hub_fast(m->hdev, prec, v, w, scratch, epi, fa, grid, st);
   return hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec, epi, fa, grid, st);
 }
@@ -725,8 +725,17 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
     return fail(m, HPHI_ERR_INVALID_ARG, "apply_H: bad vectors, nvec or precision");
   if (v == w) return fail(m, HPHI_ERR_INVALID_ARG, "apply_H: v and w must not overlap");
   hphi::FusedArgs fa;
+  void* scratch = nullptr;
+  if (use_hub_fast(m, prec, nvec, hphi::Epi::kStore)) {
+    const size_t need = hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kStore);
+    if (need) {
+      hphi::Status a = m->ws.work.ensure(need);
+      if (a.code) return fail(m, a);
+      scratch = m->ws.work.p;
+    }
+  }
   hphi::Status s = hv_launch(m, prec, v, w, nvec, hphi::Epi::kStore, fa, hv_grid_for(m, nvec, prec, hphi::Epi::kStore),
-                             nullptr, (cudaStream_t)stream);
+                             scratch, (cudaStream_t)stream);
   return s.code ? fail(m, s) : HPHI_OK;
 }
 
@@ -776,7 +785,11 @@ hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanc
   if ((s = ws.vecB.ensure(vbytes)).code) return s;
   if (p->refine && (s = ws.x.ensure(8 * (size_t)n_real)).code) return s;
   const bool fast = use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1);
-  if (fast && (s = ws.work.ensure(p->refine ? std::max(vbytes, (size_t)8 * (size_t)n_real) : vbytes)).code) return s;
+  if (fast) {
+    size_t need = hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kLanczos1);
+    if (p->refine) need = std::max(need, hphi::hub_scratch_bytes(m->hdev, HPHI_FP64, hphi::Epi::kRefine));
+    if ((s = ws.work.ensure(need)).code) return s;
+  }
   void* scratch = fast ? ws.work.p : nullptr;
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * hphi::kMaxRedQ)).code) return s;
   // scalars: alpha[m], beta[m], sig[m+1], coef[m], s[16], tri[16 + 5m], done, steps_done
@@ -980,7 +993,7 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   if ((s = ws.vecB.ensure(vbytes)).code) return s;
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * nvec * hphi::kMaxRedQ)).code) return s;
   const bool tfast = use_hub_fast(m, prec, nvec, hphi::Epi::kTpq);
-  if (tfast && (s = ws.work.ensure(vbytes)).code) return s;
+  if (tfast && (s = ws.work.ensure(hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kTpq))).code) return s;
   void* tscratch = tfast ? ws.work.p : nullptr;
   const size_t nsc = 2 * (size_t)nvec + 3 * (size_t)K * nvec;
   if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;

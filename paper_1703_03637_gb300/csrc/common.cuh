@@ -176,6 +176,7 @@ int hv_grid(int nvec);  // upper bound of any H v grid (partials sizing)
 Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, cudaStream_t st);
 bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi);
 int hub_up_grid(const HubDev& md, int prec, Epi epi);
+size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi);  // scratch the launch needs
 Status launch_hub_fast(const HubDev& md, int prec, const void* v, void* w, void* scratch, Epi epi,
                        const FusedArgs& fa, int grid_up, cudaStream_t st);
 // resident CTAs of the chosen kernel instance over the whole GPU (occupancy API)

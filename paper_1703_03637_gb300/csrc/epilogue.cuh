@@ -51,6 +51,31 @@ __device__ __forceinline__ void st(S* __restrict__ p, int64_t i, typename Traits
   }
 }
 
+// m * 2^eoff rounded to nearest even, assembled with integer ops (no fp64 issue slot)
+__device__ __forceinline__ double fix_to_double(long long m, int eoff) {
+  if (m == 0) return 0.0;
+  const bool negv = m < 0;
+  unsigned long long a = negv ? (unsigned long long)(-m) : (unsigned long long)m;
+  int lz = __clzll((long long)a);
+  a <<= lz;
+  unsigned long long mant = a >> 11;
+  const unsigned rem = (unsigned)(a & 0x7ffull);
+  if (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      --lz;
+    }
+  }
+  // value = mant * 2^(eoff - lz + 11), mant in [2^52, 2^53)
+  const int biased = eoff - lz + 11 + 52 + 1023;
+  if (biased > 0 && biased < 2047) {
+    const int hiw = (negv ? (int)0x80000000 : 0) | (biased << 20) | (int)((mant >> 32) & 0xfffffull);
+    return __hiloint2double(hiw, (int)(unsigned)(mant & 0xffffffffull));
+  }
+  return ldexp((double)m, eoff);
+}
+
 // ------------------------------------------------------------------ gather sums
 // fp64 terms are summed in an exact-alignment fixed-point accumulator: every term's
 // 53-bit significand is shifted to the running largest exponent and added as a 64-bit
@@ -65,31 +90,8 @@ struct FixAcc {
   double spill;  // flushed part (only after 128 terms)
   bool sp;       // spill holds something
   __device__ __forceinline__ void zero() { m = 0; e = 0; n = 0; spill = 0.0; sp = false; }
-  // m * 2^(e - 1077) rounded to nearest even, assembled with integer ops (no fp64 issue)
   __device__ __forceinline__ double value() const {
-    double r = 0.0;
-    if (m != 0) {
-      const bool negv = m < 0;
-      unsigned long long a = negv ? (unsigned long long)(-m) : (unsigned long long)m;
-      int lz = __clzll((long long)a);
-      a <<= lz;
-      unsigned long long mant = a >> 11;
-      const unsigned rem = (unsigned)(a & 0x7ffull);
-      if (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) {
-        ++mant;
-        if (mant >> 53) {
-          mant >>= 1;
-          --lz;
-        }
-      }
-      const int biased = e - 1077 - lz + 11 + 52 + 1023;
-      if (biased > 0 && biased < 2047) {
-        const int hiw = (negv ? (int)0x80000000 : 0) | (biased << 20) | (int)((mant >> 32) & 0xfffffull);
-        r = __hiloint2double(hiw, (int)(unsigned)(mant & 0xffffffffull));
-      } else {
-        r = ldexp((double)m, e - 1077);
-      }
-    }
+    const double r = fix_to_double(m, e - 1077);
     return sp ? r + spill : r;
   }
   __device__ __forceinline__ void add(double x, bool neg) {
@@ -124,9 +126,19 @@ struct F32Acc {
   __device__ __forceinline__ void add(float x, bool neg) { s += neg ? -x : x; }
 };
 
+// exact sums of 64-bit fixed-point terms (the quantised fp64 path; no overflow below
+// 128 terms of magnitude < 2^56)
+struct IntAcc {
+  long long s;
+  __device__ __forceinline__ void zero() { s = 0; }
+  __device__ __forceinline__ long long value() const { return s; }
+  __device__ __forceinline__ void add(long long x, bool neg) { s += neg ? -x : x; }
+};
+
 template <class R> struct SumAcc;
 template <> struct SumAcc<double> { using T = FixAcc; };
 template <> struct SumAcc<float> { using T = F32Acc; };
+template <> struct SumAcc<long long> { using T = IntAcc; };
 
 // (ar, ai) += phase(code) * (xr, xi), code: 1 (+1), 2 (+i), 3 (-1), 4 (-i)
 template <class A, class R>

@@ -177,6 +177,10 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
   }
   const R c_up = (R)md.c_up, c_dn = (R)md.c_dn;
   const bool same_c = md.c_up == md.c_dn;
+  __shared__ R s_dtab[33];
+  const bool dtab = md.n_ulin == 1 && md.n_mulin == 0 && md.n_pairs == 0;
+  if (dtab && tid <= 32) s_dtab[tid] = (R)(md.c0 + md.ulin[0].coef * (double)tid);
+  __syncthreads();
   Red<F64> red;
   red.zero();
   const int64_t dim_up = md.dim_up, dim_dn = md.dim_dn;
@@ -231,7 +235,11 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
         const int64_t idx = (d0 + m) * dim_up + u;
         const R x = tile[u * K + m];
         // diagonal: integer counts times the class coefficients
-        R dg = (R)md.c0;
+        R dg;
+        if (dtab) {
+          dg = s_dtab[__popc(up & dn[m] & (uint32_t)s_ulin[0].mask)];
+        } else {
+        dg = (R)md.c0;
         for (int g = 0; g < md.n_ulin; ++g) dg += s_uc[g] * (R)__popc(up & dn[m] & (uint32_t)s_ulin[g].mask);
         for (int g = 0; g < md.n_mulin; ++g) {
           const uint32_t mk = (uint32_t)s_mlin[g].mask;
@@ -252,6 +260,7 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
           }
           dg += s_pcoef[grp] * (R)cnt;
         }
+        }
         R hv;
         if (same_c) {
           acc[m].add(W[idx], false);
@@ -265,6 +274,178 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
   }
   if constexpr (E != Epi::kStore) {
     // fixed-order reduction: warp shuffles, then the warps' sums in warp order
+    constexpr int nq = n_red<E>();
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < nq; ++q) {
+      double x = red.get(q);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) s_red[wid * kMaxRedQ + q] = x;
+    }
+    __syncthreads();
+    if (tid < nq) {
+      double x = 0.0;
+      for (int k = 0; k < kUpThreads / 32; ++k) x += s_red[k * kMaxRedQ + tid];
+      fa.partials[(size_t)blockIdx.x * kMaxRedQ + tid] = x;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ fp64 via fixed point
+// fp64 vectors take the gather passes as 64-bit integers on one scale per vector:
+// q = round(x * 2^(1078 - E)), E = the largest exponent field of x, so |q| < 2^56 and the
+// signed sums of up to 127 terms are exact integer additions (two instructions a term on
+// the integer pipes instead of one fp64 add each at 1/64 rate).  Each element is rounded
+// once, by at most 2^-57 max|x|; the final sums convert back to fp64 exactly rounded.
+
+__global__ void __launch_bounds__(kThreads) k_maxexp(const double* __restrict__ X, int64_t n, int* __restrict__ E,
+                                                      const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  int mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    mx = max(mx, (__double2hiint(__ldg(X + i)) >> 20) & 0x7ff);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(E, mx);
+}
+
+__global__ void __launch_bounds__(kThreads) k_quant(const double* __restrict__ X, long long* __restrict__ Q, int64_t n,
+                                                     const int* __restrict__ Ep, const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int E = *Ep;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const double x = __ldg(X + i);
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int ex = (hi >> 20) & 0x7ff;
+    long long q = 0;
+    if (ex != 0) {
+      const long long M = ((long long)((hi & 0xfffff) | 0x100000) << 32) | (long long)lo;  // x = M 2^(ex-1075)
+      const int sh = E - ex - 3;                                                           // q = M 2^-sh
+      if (sh <= 0) q = M << (-sh);
+      else if (sh < 62) q = (M + (1ll << (sh - 1))) >> sh;
+      if (hi < 0) q = -q;
+    }
+    Q[i] = q;
+  }
+}
+
+// pass U on quantised rows: K int64 rows interleaved in shared memory; the fp64 value of
+// each element (for the diagonal and the reductions) is read from X itself
+template <int K, Epi E>
+__global__ void __launch_bounds__(kUpThreads) k_hub_up_q(const HubDev md, const double* __restrict__ X,
+                                                         const long long* __restrict__ Q,
+                                                         const long long* __restrict__ WQ, const int* __restrict__ Ep,
+                                                         double* __restrict__ w, FusedArgs fa) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long* tile = reinterpret_cast<long long*>(smem_raw);
+  __shared__ LinGroup s_ulin[kMaxLin];
+  __shared__ LinGroup s_mlin[kMaxLin];
+  __shared__ PairEntry s_pair[kMaxPairs];
+  __shared__ double s_pcoef[kMaxPairGroups];
+  __shared__ double s_inv[1];
+  __shared__ double s_red[(kUpThreads / 32) * kMaxRedQ];
+
+  if (fa.done != nullptr && *fa.done) return;
+  const int tid = threadIdx.x;
+  for (int k = tid; k < md.n_ulin; k += kUpThreads) s_ulin[k] = md.ulin[k];
+  for (int k = tid; k < md.n_mulin; k += kUpThreads) s_mlin[k] = md.mulin[k];
+  for (int k = tid; k < md.n_pairs; k += kUpThreads) s_pair[k] = md.pairs[k];
+  for (int k = tid; k < md.n_pair_groups; k += kUpThreads) s_pcoef[k] = md.pair_coef[k];
+  if constexpr (E == Epi::kTpq) {
+    if (tid == 0) s_inv[0] = fa.scal[0];
+  }
+  EpiScalars es{0.0, 0.0};
+  if constexpr (E == Epi::kLanczos1) {
+    es.c1 = fa.scal[0];
+    es.c2 = fa.scal[1];
+  }
+  const int eoff = *Ep - 1078;
+  const bool same_c = md.c_up == md.c_dn;
+  // diagonal = c0 + U * popcount(up & dn & mask) in the common single-group case: table
+  __shared__ double s_dtab[33];
+  const bool dtab = md.n_ulin == 1 && md.n_mulin == 0 && md.n_pairs == 0;
+  if (dtab && tid <= 32) s_dtab[tid] = md.c0 + md.ulin[0].coef * (double)tid;
+  __syncthreads();
+  Red<true> red;
+  red.zero();
+  const int64_t dim_up = md.dim_up, dim_dn = md.dim_dn;
+  const int64_t n_tiles = (dim_dn + K - 1) / K;
+  const int du = (int)dim_up;
+
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t d0 = t * K;
+    const int nk = (int)((dim_dn - d0 < K) ? (dim_dn - d0) : K);
+    __syncthreads();
+    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+#pragma unroll
+      for (int m = 0; m < K; ++m) tile[u * K + m] = (m < nk) ? __ldg(Q + (d0 + m) * dim_up + u) : 0ll;
+    }
+    __syncthreads();
+    uint32_t dn[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) dn[m] = (m < nk) ? (md.sector ? __ldg(md.list_dn + d0 + m) : (uint32_t)(d0 + m)) : 0u;
+    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+      const uint32_t up = md.sector ? __ldg(md.list_up + u) : (uint32_t)u;
+      const int deg = md.deg_up[u];
+      const uint32_t* nb = md.nbr_up + u;
+      long long acc[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) acc[m] = 0;
+      for (int q = 0; q < deg; ++q) {
+        const uint32_t e = __ldg(nb + q * du);
+        const long long* src = tile + (int)(e & 0x7fffffffu) * K;
+        const bool neg = (e >> 31) != 0;
+        if constexpr (K == 2) {
+          const longlong2 v2 = *reinterpret_cast<const longlong2*>(src);
+          acc[0] += neg ? -v2.x : v2.x;
+          acc[1] += neg ? -v2.y : v2.y;
+        } else {
+#pragma unroll
+          for (int m = 0; m < K; ++m) acc[m] += neg ? -src[m] : src[m];
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        if (m >= nk) break;
+        const int64_t idx = (d0 + m) * dim_up + u;
+        const double x = __ldg(X + idx);
+        double dg;
+        if (dtab) {
+          dg = s_dtab[__popc(up & dn[m] & (uint32_t)s_ulin[0].mask)];
+        } else {
+        dg = md.c0;
+        for (int g = 0; g < md.n_ulin; ++g) dg += s_ulin[g].coef * (double)__popc(up & dn[m] & (uint32_t)s_ulin[g].mask);
+        for (int g = 0; g < md.n_mulin; ++g) {
+          const uint32_t mk = (uint32_t)s_mlin[g].mask;
+          dg += s_mlin[g].coef * (double)(__popc(up & mk) + __popc(dn[m] & mk));
+        }
+        if (md.n_pairs) {
+          int grp = s_pair[0].grp, cnt = 0;
+          for (int p = 0; p < md.n_pairs; ++p) {
+            const PairEntry pe = s_pair[p];
+            if (pe.grp != grp) {
+              dg += s_pcoef[grp] * (double)cnt;
+              cnt = 0;
+              grp = pe.grp;
+            }
+            const int ni = (int)((up >> pe.i) & 1u) + (int)((dn[m] >> pe.i) & 1u);
+            const int nj = (int)((up >> pe.j) & 1u) + (int)((dn[m] >> pe.j) & 1u);
+            cnt += ni * nj;
+          }
+          dg += s_pcoef[grp] * (double)cnt;
+        }
+        }
+        const long long wq = __ldg(WQ + idx);
+        double hv;
+        if (same_c) hv = fma(dg, x, md.c_up * fix_to_double(acc[m] + wq, eoff));
+        else hv = fma(dg, x, fma(md.c_up, fix_to_double(acc[m], eoff), md.c_dn * fix_to_double(wq, eoff)));
+        epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, w, fa, es, s_inv, red);
+      }
+    }
+  }
+  if constexpr (E != Epi::kStore) {
     constexpr int nq = n_red<E>();
     const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
@@ -317,6 +498,74 @@ Status launch_up(const HubDev& md, const R* X, const R* W, R* w, const FusedArgs
   return {};
 }
 
+template <int K, Epi E>
+int upq_occupancy() {
+  static int b = 0;
+  if (b == 0) {
+    int n = 0;
+    cudaFuncSetAttribute(k_hub_up_q<K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hub_up_q<K, E>, kUpThreads, kSmemBudget) != cudaSuccess ||
+        n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    b = n;
+  }
+  return b;
+}
+
+// scratch layout of the quantised fp64 path: [Q: dim int64][WQ: dim int64][E: int]
+size_t quant_scratch_bytes(const HubDev& md) { return (size_t)16 * md.dim + 256; }
+
+template <Epi E>
+Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const FusedArgs& fa, int grid_up,
+                cudaStream_t st) {
+  const double* X = reinterpret_cast<const double*>(v);
+  long long* Q = reinterpret_cast<long long*>(scratch);
+  long long* WQ = Q + md.dim;
+  int* Ep = reinterpret_cast<int*>(WQ + md.dim);
+  const int gv = (int)std::max<int64_t>(1, std::min<int64_t>((md.dim + kThreads - 1) / kThreads, (int64_t)num_sms() * 8));
+  HPHI_CUDA_TRY(cudaMemsetAsync(Ep, 0, sizeof(int), st));
+  k_maxexp<<<gv, kThreads, 0, st>>>(X, md.dim, Ep, fa.done);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  constexpr int EPT = HPHI_DN_EPT64;
+  const int64_t sw = (int64_t)kThreads * EPT;
+  const int64_t items = ((md.dim_up + sw - 1) / sw) * md.dim_dn;
+  const int gd = (int)std::min<int64_t>(items, (int64_t)num_sms() * 8);
+  k_hub_dn<long long, EPT><<<gd, kThreads, 0, st>>>(md, Q, WQ, fa.done);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  double* out = reinterpret_cast<double*>(w);
+  const int K = (2 * md.dim_up * 8 <= kSmemBudget) ? 2 : 1;
+  const size_t smem = (size_t)K * md.dim_up * 8;
+  if (K == 2) {
+    HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up_q<2, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    k_hub_up_q<2, E><<<grid_up, kUpThreads, smem, st>>>(md, X, Q, WQ, Ep, out, fa);
+  } else {
+    HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up_q<1, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    k_hub_up_q<1, E><<<grid_up, kUpThreads, smem, st>>>(md, X, Q, WQ, Ep, out, fa);
+  }
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+int upq_grid(const HubDev& md, Epi epi) {
+  const int K = (2 * md.dim_up * 8 <= kSmemBudget) ? 2 : 1;
+  int occ = 1;
+#define HPHI_OCCQ(KK)                                                          \
+  switch (epi) {                                                               \
+    case Epi::kStore: occ = upq_occupancy<KK, Epi::kStore>(); break;           \
+    case Epi::kLanczos1: occ = upq_occupancy<KK, Epi::kLanczos1>(); break;     \
+    case Epi::kTpq: occ = upq_occupancy<KK, Epi::kTpq>(); break;               \
+    case Epi::kRefine: occ = upq_occupancy<KK, Epi::kRefine>(); break;         \
+  }
+  if (K == 2) { HPHI_OCCQ(2) } else { HPHI_OCCQ(1) }
+#undef HPHI_OCCQ
+  const int64_t tiles = (md.dim_dn + K - 1) / K;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * occ));
+}
+
 template <class R, Epi E>
 Status launch_r(const HubDev& md, const void* v, void* w, void* scratch, const FusedArgs& fa, int grid_up,
                 cudaStream_t st) {
@@ -367,23 +616,30 @@ Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_
 
 bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi) {
   if (!md.fast || cplx || nvec != 1) return false;
+  // fixed-point sums of at most 127 terms (|q| < 2^56) stay exact in 64 bits
+  if (prec == HPHI_FP64 && md.maxdeg_up + md.maxdeg_dn > 126) return false;
   if (epi == Epi::kRefine && prec != HPHI_FP64) return false;
   const int64_t row = md.dim_up * (int64_t)(prec == HPHI_FP64 ? 8 : 4);
   return row <= kSmemBudget;
 }
 
 int hub_up_grid(const HubDev& md, int prec, Epi epi) {
-  return prec == HPHI_FP64 ? up_grid_r<double>(md, epi) : up_grid_r<float>(md, epi);
+  return prec == HPHI_FP64 ? upq_grid(md, epi) : up_grid_r<float>(md, epi);
+}
+
+size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi) {
+  if (prec == HPHI_FP64) return quant_scratch_bytes(md);
+  return epi == Epi::kStore ? 0 : (size_t)4 * md.dim;
 }
 
 Status launch_hub_fast(const HubDev& md, int prec, const void* v, void* w, void* scratch, Epi epi,
                        const FusedArgs& fa, int grid_up, cudaStream_t st) {
   if (prec == HPHI_FP64) {
     switch (epi) {
-      case Epi::kStore: return launch_r<double, Epi::kStore>(md, v, w, scratch, fa, grid_up, st);
-      case Epi::kLanczos1: return launch_r<double, Epi::kLanczos1>(md, v, w, scratch, fa, grid_up, st);
-      case Epi::kTpq: return launch_r<double, Epi::kTpq>(md, v, w, scratch, fa, grid_up, st);
-      case Epi::kRefine: return launch_r<double, Epi::kRefine>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kStore: return launch_q<Epi::kStore>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kLanczos1: return launch_q<Epi::kLanczos1>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kTpq: return launch_q<Epi::kTpq>(md, v, w, scratch, fa, grid_up, st);
+      case Epi::kRefine: return launch_q<Epi::kRefine>(md, v, w, scratch, fa, grid_up, st);
     }
   } else {
     switch (epi) {
