@@ -122,6 +122,24 @@ int hphi_basis_ranks(hphi_model* m, const uint64_t* states, int64_t n, int64_t* 
  * Matrix-free: every element is generated on the fly from the bit strings. */
 int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void* stream);
 
+/* Allocation-free w = H v.  The paper has no counterpart: this is a service for callers
+ * that must not allocate device memory while they run -- code that enqueues work from a
+ * CUDA host callback or another context where cudaMalloc is not permitted, real-time loops
+ * that cannot afford the implicit device synchronisation of cudaMalloc / cudaFree, and
+ * applications whose memory is fully pre-reserved by their own allocator.  It computes the
+ * same product as hphi_apply_H for one fp64 vector (prec = HPHI_FP64, nvec = 1) of a real
+ * Hubbard model with one hopping value per spin species, and allocates nothing: its
+ * scratch (16 bytes per basis row + 256 bytes) is a fixed 64 MiB device array inside the
+ * library, so the basis may have at most 4,194,288 rows; larger bases return
+ * HPHI_ERR_INVALID_ARG with the limit in the message, other models HPHI_ERR_UNSUPPORTED.
+ * v and w are caller-owned device buffers [dim] of double and must not overlap.  The first
+ * call on each device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  Every call on a device shares the one array,
+ * so calls whose GPU work overlaps (different streams or threads without ordering between
+ * them) race and give wrong results; calls ordered on one stream are safe.  The array is
+ * held by every GPU that loads the library until the process exits. */
+int hphi_apply_H_noalloc(hphi_model* m, const void* v, void* w, void* stream);
+
 /* ---------------------------------------------------------------- start vectors */
 
 /* Fills v (device, [dim][nvec], precision prec) with standard-normal numbers from the

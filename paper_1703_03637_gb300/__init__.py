@@ -28,7 +28,7 @@ EXPORTS = [
     "hphi_create", "hphi_destroy", "hphi_last_error", "hphi_add_spin_coupling", "hphi_add_spin_field",
     "hphi_add_hopping", "hphi_add_onsite_U", "hphi_add_density", "hphi_add_chemical_potential", "hphi_set_basis",
     "hphi_build_sector", "hphi_dim", "hphi_is_complex", "hphi_basis_states", "hphi_basis_ranks", "hphi_apply_H",
-    "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run",
+    "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run", "hphi_apply_H_noalloc",
 ]
 
 
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
         L.hphi_basis_states.argtypes = [P, I64, I64, P, P]
         L.hphi_basis_ranks.argtypes = [P, P, I64, P, P]
         L.hphi_apply_H.argtypes = [P, P, P, I, I, P]
+        L.hphi_apply_H_noalloc.argtypes = [P, P, P, P]
         L.hphi_random_vector.argtypes = [P, P, I, I, U64, P]
         L.hphi_philox4x32_10.argtypes = [P, P, P, I64, P]
         L.hphi_lanczos_run.argtypes = [P, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
@@ -240,6 +241,16 @@ class Model:
         if w is None:
             w = _torch().empty_like(v)
         self._check(self._L.hphi_apply_H(self._h, _dptr(v), _dptr(w), nvec, prec, _stream()))
+        return w
+
+    def apply_H_noalloc(self, v, w):
+        """w = H v through the allocation-free entry point (fp64, one vector, real Hubbard
+        models with one hopping value per species).  v and w are caller-owned CUDA tensors of
+        shape [dim]; the library allocates nothing during the call."""
+        torch = _torch()
+        if v.dtype != torch.float64 or w.dtype != torch.float64 or v.numel() != self.dim or w.numel() != self.dim:
+            raise LibraryError(-1, "apply_H_noalloc takes float64 vectors of length dim")
+        self._check(self._L.hphi_apply_H_noalloc(self._h, _dptr(v), _dptr(w), _stream()))
         return w
 
     def random_vector(self, seed: int, nvec: int = 1, prec=FP64):

@@ -739,6 +739,18 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
   return s.code ? fail(m, s) : HPHI_OK;
 }
 
+int hphi_apply_H_noalloc(hphi_model* m, const void* v, void* w, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (!v || !w) return fail(m, HPHI_ERR_INVALID_ARG, "apply_H_noalloc: v and w must be device buffers");
+  if (v == w) return fail(m, HPHI_ERR_INVALID_ARG, "apply_H_noalloc: v and w must not overlap");
+  if (!use_hub_fast(m, HPHI_FP64, 1, hphi::Epi::kStore))
+    return fail(m, HPHI_ERR_UNSUPPORTED,
+                "apply_H_noalloc: only real Hubbard models with one hopping value per spin species (fp64, one vector)");
+  hphi::Status s = hphi::launch_hub_store_noalloc(m->hdev, v, w, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
 int hphi_random_vector(hphi_model* m, void* v, int nvec, int prec, uint64_t seed, void* stream) {
   int rc = check_built(m);
   if (rc) return rc;

@@ -177,6 +177,9 @@ Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_
 bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi);
 int hub_up_grid(const HubDev& md, int prec, Epi epi);
 size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi);  // scratch the launch needs
+// fp64 H v of the two-pass path with its scratch in a fixed device array (no allocation)
+Status launch_hub_store_noalloc(const HubDev& md, const void* v, void* w, cudaStream_t st);
+size_t noalloc_capacity_bytes();
 Status launch_hub_fast(const HubDev& md, int prec, const void* v, void* w, void* scratch, Epi epi,
                        const FusedArgs& fa, int grid_up, cudaStream_t st);
 // resident CTAs of the chosen kernel instance over the whole GPU (occupancy API)

@@ -12,11 +12,23 @@
 //           (built once per sector on the device) to all K rows at once, adds diag * X and
 //           coef * W, and runs the fused Lanczos / mTPQ epilogue.
 // fp64 sums use the exact fixed-point accumulator (integer pipes); fp32 sums are plain.
+#include <mutex>
+#include <string>
+
 #include "common.cuh"
 #include "epilogue.cuh"
 #include "reduce.cuh"
 
 namespace hphi {
+
+// ------------------------------------------------------------------ allocation-free scratch
+// Scratch of hphi_apply_H_noalloc: the int64 copy of the input, the int64 down-spin sums and
+// the scale word of the fixed-point fp64 path (16 bytes per row + 256).  It is a file-scope
+// device array, so every GPU that loads this library holds these 64 MiB until the process
+// exits, and every call on a device shares it.  Host code must not use the symbol as a
+// pointer: its device address comes from cudaGetSymbolAddress (noalloc_scratch below).
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
 
@@ -604,7 +616,45 @@ int up_grid_r(const HubDev& md, Epi epi) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * occ));
 }
 
+// Device address of g_noalloc_scratch on the current device, looked up once per device
+// (with that device current) and cached.
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+Status noalloc_scratch(void** out) {
+  int dev = 0;
+  HPHI_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return {HPHI_ERR_UNSUPPORTED, "allocation-free path: device ordinal above 63"};
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return {HPHI_ERR_CUDA, std::string("cudaGetSymbolAddress(allocation-free scratch): ") + cudaGetErrorString(e)};
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return {};
+}
+
 }  // namespace
+
+size_t noalloc_capacity_bytes() { return kNoAllocScratchBytes; }
+
+Status launch_hub_store_noalloc(const HubDev& md, const void* v, void* w, cudaStream_t st) {
+  const size_t need = quant_scratch_bytes(md);
+  if (need > kNoAllocScratchBytes)
+    return {HPHI_ERR_INVALID_ARG, "hphi_apply_H_noalloc: the basis needs " + std::to_string(need) +
+                                      " bytes of scratch, above the fixed " + std::to_string(kNoAllocScratchBytes) +
+                                      " (at most " + std::to_string((kNoAllocScratchBytes - 256) / 16) + " rows)"};
+  void* scratch = nullptr;
+  Status s = noalloc_scratch(&scratch);
+  if (s.code) return s;
+  FusedArgs fa;  // plain H v: no reductions, no breakdown flag
+  return launch_q<Epi::kStore>(md, v, w, scratch, fa, upq_grid(md, Epi::kStore), st);
+}
 
 Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, cudaStream_t st) {
   const int64_t n = species ? md.dim_dn : md.dim_up;
