@@ -180,7 +180,7 @@ typedef struct {
   double e_refined;    /* refine = 1: <x|H|x> / <x|x> in fp64                            */
   double residual;     /* refine = 1: |H x - E x| / |x|                                   */
   double variance;     /* refine = 1: <H^2> - <H>^2 for x / |x|                            */
-  float device_ms;     /* device time of the Lanczos loop (CUDA events on the stream)     */
+  float device_ms;     /* device time of the call's GPU work (CUDA events on the stream)  */
   float hv_ms;         /* profile = 1: summed device time of the fused H v launches       */
   int hv_launches;     /* number of fused H v launches timed in hv_ms                      */
   int kernel_launches; /* CUDA kernels this call launched                                   */
@@ -191,6 +191,19 @@ typedef struct {
  * fused with the vector update and every reduction accumulated in fp64; then the lowest
  * eigenvalues of the tridiagonal T_m by Sturm bisection in fp64 on the device. */
 int hphi_lanczos_run(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_result* r, void* stream);
+
+/* Lanczos in several S^z sectors at once (spin models; the model's own basis setting is not
+ * used).  Sector i has n_up_list[i] up spins; its tables are built on first use and kept
+ * until the terms change.  All sectors' runs -- fused steps, eigensolve and optional
+ * refinement -- are captured into one CUDA graph as parallel branches and launched once, so
+ * sectors of very different dimension (1 .. C(N, N/2)) run side by side.  Each sector's
+ * start vector is hphi_random_vector with seed p->seed + n_up_list[i]; p->v0 must be NULL
+ * and p->profile is ignored.  results: caller host array [n_sectors], each filled as by
+ * hphi_lanczos_run (alpha / beta host arrays of p->steps entries, or NULL); device_ms is the
+ * time of the whole graph.  1 <= n_sectors <= 64, sectors distinct, n_sites <= 40.  The
+ * paper runs one sector per job; batching sectors is this library's. */
+int hphi_lanczos_run_sectors(hphi_model* m, const int* n_up_list, int n_sectors, const hphi_lanczos_params* p,
+                             hphi_lanczos_result* results, void* stream);
 
 /* ---------------------------------------------------------------- mTPQ (section 3.5) */
 

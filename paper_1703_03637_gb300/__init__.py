@@ -29,6 +29,7 @@ EXPORTS = [
     "hphi_add_hopping", "hphi_add_onsite_U", "hphi_add_density", "hphi_add_chemical_potential", "hphi_set_basis",
     "hphi_build_sector", "hphi_dim", "hphi_is_complex", "hphi_basis_states", "hphi_basis_ranks", "hphi_apply_H",
     "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run", "hphi_apply_H_noalloc",
+    "hphi_lanczos_run_sectors",
 ]
 
 
@@ -104,6 +105,7 @@ def load(build_if_missing: bool = True):
         L.hphi_philox4x32_10.argtypes = [P, P, P, I64, P]
         L.hphi_lanczos_run.argtypes = [P, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         L.hphi_tpq_run.argtypes = [P, ctypes.POINTER(TpqParams), ctypes.POINTER(TpqResult), P]
+        L.hphi_lanczos_run_sectors.argtypes = [P, P, I, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         _lib = L
         return L
 
@@ -290,6 +292,28 @@ class Model:
         return dict(alpha=a[:n], beta=b[:n], steps=n, eig=np.array(r.eig[:n_eig]), e_refined=r.e_refined,
                     residual=r.residual, variance=r.variance, ms=r.device_ms, hv_ms=r.hv_ms,
                     hv_launches=r.hv_launches, launches=r.kernel_launches)
+
+    def lanczos_sectors(self, n_up_list, steps: int, prec=FP64, seed: int = 123432, n_eig: int = 1,
+                        refine: bool = False, breakdown: float = 0.0):
+        """Lanczos in several S^z sectors captured as one CUDA graph; one result dict per sector."""
+        _torch()
+        nu = np.ascontiguousarray(n_up_list, dtype=np.int32)
+        ns = len(nu)
+        al = [np.zeros(steps) for _ in range(ns)]
+        be = [np.zeros(steps) for _ in range(ns)]
+        res = (LanczosResult * ns)()
+        for i in range(ns):
+            res[i].alpha = al[i].ctypes.data
+            res[i].beta = be[i].ctypes.data
+        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0)
+        self._check(self._L.hphi_lanczos_run_sectors(self._h, nu.ctypes.data, ns, ctypes.byref(p), res, _stream()))
+        out = []
+        for i in range(ns):
+            n = res[i].steps_done
+            out.append(dict(n_up=int(nu[i]), alpha=al[i][:n], beta=be[i][:n], steps=n, eig=np.array(res[i].eig[:n_eig]),
+                            e_refined=res[i].e_refined, residual=res[i].residual, variance=res[i].variance,
+                            ms=res[i].device_ms, launches=res[i].kernel_launches))
+        return out
 
     def tpq(self, n_starts: int, steps: int, l: float = 1.0, n_s: float = 0.0, prec=FP64, seed: int = 123432,
             psi0=None):

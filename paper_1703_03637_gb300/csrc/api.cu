@@ -118,6 +118,9 @@ struct hphi_model {
   hphi::SpinDev sdev{};
   hphi::HubDev hdev{};
   Workspace ws;
+  // sector sub-models of hphi_lanczos_run_sectors, rebuilt when the terms change
+  uint64_t gen = 0, sub_gen = ~0ull;
+  std::map<int, std::unique_ptr<hphi_model>> sub;
 };
 
 namespace {
@@ -603,6 +606,7 @@ int hphi_add_spin_coupling(hphi_model* m, int i, int j, const double J[9]) {
   }
   m->coup.push_back(c);
   m->built = false;
+  ++m->gen;
   return HPHI_OK;
 }
 
@@ -614,6 +618,7 @@ int hphi_add_spin_field(hphi_model* m, int i, const double h[3]) {
     if (!isfinite(h[k])) return fail(m, HPHI_ERR_INVALID_ARG, "non-finite field");
   m->field.push_back(Field{i, {h[0], h[1], h[2]}});
   m->built = false;
+  ++m->gen;
   return HPHI_OK;
 }
 
@@ -625,6 +630,7 @@ int hphi_add_hopping(hphi_model* m, int i, int j, int spin, double t_re, double 
   if (!isfinite(t_re) || !isfinite(t_im)) return fail(m, HPHI_ERR_INVALID_ARG, "non-finite hopping");
   m->hop.push_back(Hop{i, j, spin, t_re, t_im});
   m->built = false;
+  ++m->gen;
   return HPHI_OK;
 }
 
@@ -634,6 +640,7 @@ int hphi_add_onsite_U(hphi_model* m, int i, double U) {
   if (i < 0 || i >= m->n_sites || !isfinite(U)) return fail(m, HPHI_ERR_INVALID_ARG, "bad onsite U");
   m->onsite.push_back(Onsite{i, U});
   m->built = false;
+  ++m->gen;
   return HPHI_OK;
 }
 
@@ -644,6 +651,7 @@ int hphi_add_density(hphi_model* m, int i, int j, double V) {
     return fail(m, HPHI_ERR_INVALID_ARG, "bad density interaction");
   m->dens.push_back(Density{i, j, V});
   m->built = false;
+  ++m->gen;
   return HPHI_OK;
 }
 
@@ -653,6 +661,7 @@ int hphi_add_chemical_potential(hphi_model* m, int i, double mu) {
   if (i < 0 || i >= m->n_sites || !isfinite(mu)) return fail(m, HPHI_ERR_INVALID_ARG, "bad chemical potential");
   m->chem.push_back(Chem{i, mu});
   m->built = false;
+  ++m->gen;
   return HPHI_OK;
 }
 
@@ -675,6 +684,7 @@ int hphi_set_basis(hphi_model* m, int basis, int a, int b) {
   m->a = a;
   m->b = b;
   m->built = false;
+  ++m->gen;
   return HPHI_OK;
 }
 
@@ -778,214 +788,318 @@ struct Timer {
   }
 };
 
-hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_result* r, cudaStream_t st) {
-  const int steps = p->steps;
-  const int prec = p->prec;
-  const bool cplx = m->cplx_model;
-  const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (cplx ? 2 : 1);
-  const int64_t n_real = m->dim * (cplx ? 2 : 1);
+// One Lanczos run, split so several runs can be captured as parallel branches of one graph:
+// lz_prepare allocates (no launches), lz_enqueue issues every kernel in stream order
+// (capturable), lz_collect copies the scalars back after the stream has run.
+struct LzPlan {
+  hphi_model* m = nullptr;
+  int steps = 0, prec = 0, n_eig = 1;
+  bool cplx = false, refine = false, profile = false;
+  int64_t n_real = 0;
+  int grid = 1, rgrid = 1, vgrid = 1;
+  double* partials = nullptr;
+  void* scratch = nullptr;
+  hphi::LzDev lz{};
+  double* base = nullptr;
+  size_t nsc = 0;
+  int* flags = nullptr;
+  double brk = 1e-13;
+  const double* v0 = nullptr;
+  uint64_t seed = 0;
+  int launches = 0;
+  std::vector<cudaEvent_t> ev;  // profile: events around every fused H v launch
+  ~LzPlan() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) {
+  L.m = m;
+  L.steps = p->steps;
+  L.prec = p->prec;
+  L.n_eig = std::max(1, std::min(8, p->n_eig));
+  L.cplx = m->cplx_model;
+  L.refine = p->refine != 0;
+  L.profile = p->profile != 0;
+  L.v0 = reinterpret_cast<const double*>(p->v0);
+  L.seed = p->seed;
+  L.brk = p->breakdown > 0 ? p->breakdown : 1e-13;
+  const int steps = L.steps, prec = L.prec;
+  const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (L.cplx ? 2 : 1);
+  L.n_real = m->dim * (L.cplx ? 2 : 1);
   const size_t vbytes = esz * (size_t)m->dim;
-  const int grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
-  const int rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);
-  const int vgrid = launch_grid(n_real);
-  const int pgrid = std::max(std::max(grid, rgrid), vgrid);
+  L.grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
+  L.rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);
+  L.vgrid = launch_grid(L.n_real);
+  const int pgrid = std::max(std::max(L.grid, L.rgrid), L.vgrid);
   Workspace& ws = m->ws;
   hphi::Status s;
   // the refinement's fp64 H x reuses buffer A, which must then hold an fp64 vector
-  const size_t need_a = p->refine ? std::max(vbytes, (size_t)8 * (size_t)n_real) : vbytes;
+  const size_t need_a = L.refine ? std::max(vbytes, (size_t)8 * (size_t)L.n_real) : vbytes;
   if ((s = ws.vecA.ensure(need_a)).code) return s;
   if ((s = ws.vecB.ensure(vbytes)).code) return s;
-  if (p->refine && (s = ws.x.ensure(8 * (size_t)n_real)).code) return s;
-  const bool fast = use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1);
-  if (fast) {
+  if (L.refine && (s = ws.x.ensure(8 * (size_t)L.n_real)).code) return s;
+  if (use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1)) {
     size_t need = hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kLanczos1);
-    if (p->refine) need = std::max(need, hphi::hub_scratch_bytes(m->hdev, HPHI_FP64, hphi::Epi::kRefine));
+    if (L.refine) need = std::max(need, hphi::hub_scratch_bytes(m->hdev, HPHI_FP64, hphi::Epi::kRefine));
     if ((s = ws.work.ensure(need)).code) return s;
+    L.scratch = ws.work.p;
   }
-  void* scratch = fast ? ws.work.p : nullptr;
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * hphi::kMaxRedQ)).code) return s;
+  L.partials = ws.partials.as<double>();
   // scalars: alpha[m], beta[m], sig[m+1], coef[m], s[16], tri[16 + 5m], done, steps_done
-  const size_t nsc = 3 * (size_t)steps + 1 + steps + 16 + 16 + 5 * (size_t)steps + 4;
-  if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;
-  double* base = ws.scal.as<double>();
-  hphi::LzDev lz;
-  lz.alpha = base;
-  lz.beta = lz.alpha + steps;
-  lz.sig = lz.beta + steps;
-  lz.coef = lz.sig + steps + 1;
-  lz.s = lz.coef + steps;
-  lz.tri = lz.s + 16;
-  int* flags = reinterpret_cast<int*>(lz.tri + 16 + 5 * (size_t)steps);
-  lz.done = flags;
-  lz.steps_done = flags + 1;
-  HPHI_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(double) * nsc, st));
-  double* partials = ws.partials.as<double>();
-  const double brk = p->breakdown > 0 ? p->breakdown : 1e-13;
-
-  int launches = 0;
-  // start vector (buffer A holds C_0)
-  const double* v0 = reinterpret_cast<const double*>(p->v0);
-  if (!v0) {
-    ++launches;
-    if (prec == HPHI_FP64) {
-      if ((s = hphi::launch_random(ws.vecA.p, m->dim, cplx, true, p->seed, st)).code) return s;
-    } else {
-      if ((s = hphi::launch_random(ws.vecA.p, m->dim, cplx, false, p->seed, st)).code) return s;
+  L.nsc = 3 * (size_t)steps + 1 + steps + 16 + 16 + 5 * (size_t)steps + 4;
+  if ((s = ws.scal.ensure(sizeof(double) * L.nsc)).code) return s;
+  L.base = ws.scal.as<double>();
+  L.lz.alpha = L.base;
+  L.lz.beta = L.lz.alpha + steps;
+  L.lz.sig = L.lz.beta + steps;
+  L.lz.coef = L.lz.sig + steps + 1;
+  L.lz.s = L.lz.coef + steps;
+  L.lz.tri = L.lz.s + 16;
+  L.flags = reinterpret_cast<int*>(L.lz.tri + 16 + 5 * (size_t)steps);
+  L.lz.done = L.flags;
+  L.lz.steps_done = L.flags + 1;
+  if (L.profile) {
+    L.ev.assign(2 * (size_t)steps, nullptr);
+    for (auto& e : L.ev) {
+      const cudaError_t ce = cudaEventCreate(&e);
+      if (ce != cudaSuccess) return {HPHI_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce)};
     }
   }
+  return {};
+}
 
-  std::vector<cudaEvent_t> ev;
-  auto destroy_events = [&]() {
-    for (cudaEvent_t e : ev)
-      if (e) cudaEventDestroy(e);
-    ev.clear();
+// Lanczos recurrence of section 3.4 (m fused steps), the tridiagonal eigensolve and, if asked,
+// the second pass with the fp64 Ritz vector and its Rayleigh quotient / residual.
+hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
+  hphi_model* m = L.m;
+  Workspace& ws = m->ws;
+  const int steps = L.steps, prec = L.prec;
+  const bool cplx = L.cplx;
+  hphi::Status s;
+  L.launches = 0;
+  HPHI_CUDA_TRY(cudaMemsetAsync(L.base, 0, sizeof(double) * L.nsc, st));
+  auto start = [&]() -> hphi::Status {
+    if (L.v0) return {};
+    ++L.launches;  // buffer A holds C_0 (regenerated bit-identically for the second pass)
+    return hphi::launch_random(ws.vecA.p, m->dim, cplx, prec == HPHI_FP64, L.seed, st);
   };
-  if (p->profile) {
-    ev.assign(2 * (size_t)steps, nullptr);
-    for (auto& e : ev) {
-      cudaError_t ce = cudaEventCreate(&e);
-      if (ce != cudaSuccess) {
-        destroy_events();
-        return {HPHI_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce)};
-      }
-    }
-  }
   auto run_pass = [&](bool with_x) -> hphi::Status {
     hphi::Status q;
-    launches += 2 + 4 * steps;
-    if ((q = hphi::launch_lz_init(prec, cplx, v0, ws.vecA.p, ws.vecB.p, n_real, partials, vgrid, st)).code) return q;
-    if ((q = hphi::launch_lz_init_fin(lz, partials, vgrid, st)).code) return q;
-    if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)n_real, st));
+    L.launches += 2 + 4 * steps;
+    if ((q = hphi::launch_lz_init(prec, cplx, L.v0, ws.vecA.p, ws.vecB.p, L.n_real, L.partials, L.vgrid, st)).code)
+      return q;
+    if ((q = hphi::launch_lz_init_fin(L.lz, L.partials, L.vgrid, st)).code) return q;
+    if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)L.n_real, st));
     void* C = ws.vecA.p;
     void* P = ws.vecB.p;
     for (int k = 0; k < steps; ++k) {
       hphi::FusedArgs fa;
       fa.out = P;
-      fa.scal = lz.s;
-      fa.partials = partials;
-      fa.done = lz.done;
-      const bool timed = p->profile && !with_x;
-      if (timed) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * k], st));
-      if ((q = hv_launch(m, prec, C, nullptr, 1, hphi::Epi::kLanczos1, fa, grid, scratch, st)).code) return q;
-      if (timed) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * k + 1], st));
-      if ((q = hphi::launch_lz_fin1(lz, k, partials, grid, st)).code) return q;
-      if ((q = hphi::launch_lz_pass2(prec, cplx, lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, n_real, partials,
-                                     vgrid, st)).code)
+      fa.scal = L.lz.s;
+      fa.partials = L.partials;
+      fa.done = L.lz.done;
+      const bool timed = L.profile && !with_x;
+      if (timed) HPHI_CUDA_TRY(cudaEventRecord(L.ev[2 * k], st));
+      if ((q = hv_launch(m, prec, C, nullptr, 1, hphi::Epi::kLanczos1, fa, L.grid, L.scratch, st)).code) return q;
+      if (timed) HPHI_CUDA_TRY(cudaEventRecord(L.ev[2 * k + 1], st));
+      if ((q = hphi::launch_lz_fin1(L.lz, k, L.partials, L.grid, st)).code) return q;
+      if ((q = hphi::launch_lz_pass2(prec, cplx, L.lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, L.n_real,
+                                     L.partials, L.vgrid, st)).code)
         return q;
-      if ((q = hphi::launch_lz_fin2(lz, k, brk, partials, vgrid, st)).code) return q;
+      if ((q = hphi::launch_lz_fin2(L.lz, k, L.brk, L.partials, L.vgrid, st)).code) return q;
       std::swap(C, P);
     }
     return {};
   };
+  if ((s = start()).code) return s;
+  if ((s = run_pass(false)).code) return s;
+  ++L.launches;
+  if ((s = hphi::launch_tridiag(L.lz, steps, L.n_eig, L.refine, st)).code) return s;
+  if (!L.refine) return {};
+  if ((s = start()).code) return s;
+  if ((s = run_pass(true)).code) return s;
+  L.launches += 4;
+  // fp64 H x into the (now free) buffer A, then E, variance and residual
+  double* hx = ws.vecA.as<double>();
+  hphi::FusedArgs fa;
+  fa.out = hx;
+  fa.partials = L.partials;
+  if ((s = hv_launch(m, HPHI_FP64, ws.x.p, nullptr, 1, hphi::Epi::kRefine, fa, L.rgrid, L.scratch, st)).code) return s;
+  if ((s = hphi::launch_refine_fin(L.lz, L.partials, L.rgrid, 0, st)).code) return s;
+  if ((s = hphi::launch_refine_resid(cplx, ws.x.as<double>(), hx, L.n_real, L.lz, L.partials, L.vgrid, st)).code)
+    return s;
+  return hphi::launch_refine_fin(L.lz, L.partials, L.vgrid, 1, st);
+}
 
-  Timer tm;
-  HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
-  HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
-  HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
-  // the loop is captured once into a CUDA graph and replayed on the caller's stream
-  cudaStream_t cap = nullptr;
-  HPHI_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  auto cleanup = [&]() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (cap) cudaStreamDestroy(cap);
-    exec = nullptr; graph = nullptr; cap = nullptr;
-  };
-  auto capture_run = [&](bool with_x) -> hphi::Status {
-    // profiled runs launch eagerly: CUDA events recorded inside a captured graph cannot
-    // be queried with cudaEventElapsedTime
-    if (p->profile) return run_pass(with_x);
-    cudaStream_t saved = st;
-    st = cap;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { st = saved; return {HPHI_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)}; }
-    hphi::Status q = run_pass(with_x);
-    e = cudaStreamEndCapture(cap, &graph);
-    st = saved;
-    if (q.code) return q;
-    if (e != cudaSuccess) return {HPHI_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e)};
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) return {HPHI_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)};
-    e = cudaGraphLaunch(exec, st);
-    if (e != cudaSuccess) return {HPHI_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)};
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    exec = nullptr;
-    graph = nullptr;
-    return {};
-  };
-  // When a random start is generated, buffer A already holds it; keep a copy for the
-  // second pass by regenerating it (same seed, bit-identical).
-  auto fail_out = [&](hphi::Status q) {
-    cleanup();
-    destroy_events();
-    return q;
-  };
-  s = capture_run(false);
-  if (s.code) return fail_out(s);
-  ++launches;
-  s = hphi::launch_tridiag(lz, steps, std::max(1, std::min(8, p->n_eig)), p->refine != 0, st);
-  if (s.code) return fail_out(s);
-  HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
-  if (p->refine) {
-    if (!v0) {
-      ++launches;
-      s = hphi::launch_random(ws.vecA.p, m->dim, cplx, prec == HPHI_FP64, p->seed, st);
-      if (s.code) return fail_out(s);
-    }
-    s = capture_run(true);
-    if (s.code) return fail_out(s);
-    launches += 4;
-    // fp64 H x into the (now free) Lanczos buffers, then E, variance and residual
-    double* hx = ws.vecA.as<double>();
-    hphi::FusedArgs fa;
-    fa.out = hx;
-    fa.partials = partials;
-    s = hv_launch(m, HPHI_FP64, ws.x.p, nullptr, 1, hphi::Epi::kRefine, fa, rgrid, scratch, st);
-    if (s.code) return fail_out(s);
-    s = hphi::launch_refine_fin(lz, partials, rgrid, 0, st);
-    if (s.code) return fail_out(s);
-    s = hphi::launch_refine_resid(cplx, ws.x.as<double>(), hx, n_real, lz, partials, vgrid, st);
-    if (s.code) return fail_out(s);
-    s = hphi::launch_refine_fin(lz, partials, vgrid, 1, st);
-    if (s.code) return fail_out(s);
-  }
-  cleanup();
-  // results to the host
-  std::vector<double> host(nsc);
-  HPHI_CUDA_TRY(cudaMemcpyAsync(host.data(), base, sizeof(double) * nsc, cudaMemcpyDeviceToHost, st));
+hphi::Status lz_collect(LzPlan& L, hphi_lanczos_result* r, cudaStream_t st) {
+  std::vector<double> host(L.nsc);
+  HPHI_CUDA_TRY(cudaMemcpyAsync(host.data(), L.base, sizeof(double) * L.nsc, cudaMemcpyDeviceToHost, st));
   HPHI_CUDA_TRY(cudaStreamSynchronize(st));
-  float ms = 0.f;
-  HPHI_CUDA_TRY(cudaEventElapsedTime(&ms, tm.a, tm.b));
-  const int* hf = reinterpret_cast<const int*>(host.data() + (reinterpret_cast<double*>(flags) - base));
+  const int* hf = reinterpret_cast<const int*>(host.data() + (reinterpret_cast<double*>(L.flags) - L.base));
   r->steps_done = hf[1];
-  if (r->alpha) memcpy(r->alpha, host.data() + (lz.alpha - base), sizeof(double) * steps);
-  if (r->beta) memcpy(r->beta, host.data() + (lz.beta - base), sizeof(double) * steps);
-  for (int k = 0; k < 8; ++k) r->eig[k] = (k < p->n_eig) ? host[(lz.tri - base) + k] : 0.0;
-  if (p->refine) {
-    r->e_refined = host[(lz.tri - base) + 8];
-    r->residual = host[(lz.tri - base) + 9];
-    r->variance = host[(lz.tri - base) + 10];
+  if (r->alpha) memcpy(r->alpha, host.data() + (L.lz.alpha - L.base), sizeof(double) * L.steps);
+  if (r->beta) memcpy(r->beta, host.data() + (L.lz.beta - L.base), sizeof(double) * L.steps);
+  for (int k = 0; k < 8; ++k) r->eig[k] = (k < L.n_eig) ? host[(L.lz.tri - L.base) + k] : 0.0;
+  if (L.refine) {
+    r->e_refined = host[(L.lz.tri - L.base) + 8];
+    r->residual = host[(L.lz.tri - L.base) + 9];
+    r->variance = host[(L.lz.tri - L.base) + 10];
   } else {
     r->e_refined = r->residual = r->variance = 0.0;
   }
-  r->device_ms = ms;
   r->hv_ms = 0.f;
   r->hv_launches = 0;
-  if (p->profile) {
-    for (int k = 0; k < steps; ++k) {
+  if (L.profile) {
+    for (int k = 0; k < L.steps && k < r->steps_done; ++k) {
       float t = 0.f;
-      if (k < r->steps_done) {
-        if (cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) r->hv_ms += t;
-        else cudaGetLastError();  // clear the error so later calls do not report it
-      }
+      if (cudaEventElapsedTime(&t, L.ev[2 * k], L.ev[2 * k + 1]) == cudaSuccess) r->hv_ms += t;
+      else cudaGetLastError();  // clear the error so later calls do not report it
     }
-    r->hv_launches = std::min(steps, r->steps_done + 0);
-    destroy_events();
+    r->hv_launches = std::min(L.steps, r->steps_done);
   }
-  r->kernel_launches = launches;
+  r->kernel_launches = L.launches;
+  return {};
+}
+
+// Runs `enqueue` captured into one CUDA graph (fork/join over `branches` streams if > 0) and
+// launches it on st between the events of tm.
+template <class F>
+hphi::Status run_graph(cudaStream_t st, Timer& tm, int branches, F enqueue) {
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> bs(std::max(0, branches), nullptr);
+  std::vector<cudaEvent_t> joins(bs.size(), nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  hphi::Status s;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : joins)
+      if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (auto b : bs)
+      if (b) cudaStreamDestroy(b);
+    if (cap) cudaStreamDestroy(cap);
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  for (size_t i = 0; e == cudaSuccess && i < bs.size(); ++i) {
+    e = cudaStreamCreateWithFlags(&bs[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cleanup();
+    return {HPHI_ERR_CUDA, std::string("graph setup: ") + cudaGetErrorString(e)};
+  }
+  if (bs.empty()) {
+    s = enqueue(0, cap);
+  } else {
+    e = cudaEventRecord(fork, cap);
+    for (size_t i = 0; e == cudaSuccess && i < bs.size() && !s.code; ++i) {
+      e = cudaStreamWaitEvent(bs[i], fork, 0);
+      if (e == cudaSuccess) s = enqueue((int)i, bs[i]);
+      if (e == cudaSuccess && !s.code) e = cudaEventRecord(joins[i], bs[i]);
+      if (e == cudaSuccess && !s.code) e = cudaStreamWaitEvent(cap, joins[i], 0);
+    }
+    if (e != cudaSuccess && !s.code) s = {HPHI_ERR_CUDA, std::string("graph fork/join: ") + cudaGetErrorString(e)};
+  }
+  e = cudaStreamEndCapture(cap, &graph);
+  if (!s.code && e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e)};
+  if (!s.code) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)};
+  }
+  if (!s.code) {
+    e = cudaEventRecord(tm.a, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(tm.b, st);
+    if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)};
+  }
+  cleanup();
+  return s;
+}
+
+hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_result* r, cudaStream_t st) {
+  LzPlan L;
+  hphi::Status s = lz_prepare(m, p, L);
+  if (s.code) return s;
+  Timer tm;
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
+  if (L.profile) {
+    // profiled runs launch eagerly: events recorded inside a captured graph cannot be
+    // queried with cudaEventElapsedTime
+    HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
+    if ((s = lz_enqueue(L, st)).code) return s;
+    HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
+  } else {
+    s = run_graph(st, tm, 0, [&](int, cudaStream_t cs) { return lz_enqueue(L, cs); });
+    if (s.code) return s;
+  }
+  if ((s = lz_collect(L, r, st)).code) return s;
+  float ms = 0.f;
+  HPHI_CUDA_TRY(cudaEventElapsedTime(&ms, tm.a, tm.b));
+  r->device_ms = ms;
+  return {};
+}
+
+// Sector sub-model (same terms, HPHI_BASIS_SZ with n_up up spins), built once per term set.
+hphi::Status sector_model(hphi_model* m, int n_up, cudaStream_t st, hphi_model** out) {
+  if (m->sub_gen != m->gen) {
+    m->sub.clear();
+    m->sub_gen = m->gen;
+  }
+  auto it = m->sub.find(n_up);
+  if (it == m->sub.end()) {
+    std::unique_ptr<hphi_model> sm(new (std::nothrow) hphi_model());
+    if (!sm) return {HPHI_ERR_OUT_OF_MEMORY, "host allocation failed"};
+    sm->kind = m->kind;
+    sm->n_sites = m->n_sites;
+    sm->coup = m->coup;
+    sm->field = m->field;
+    sm->basis = HPHI_BASIS_SZ;
+    sm->a = n_up;
+    hphi::Status s = build_sector_impl(sm.get(), st);
+    if (s.code) return s;
+    sm->built = true;
+    it = m->sub.emplace(n_up, std::move(sm)).first;
+  }
+  *out = it->second.get();
+  return {};
+}
+
+// All requested S^z sectors in one CUDA graph: each sector's Lanczos chain (fused steps,
+// eigensolve, optional refinement) is one branch, so small sectors run beside large ones.
+hphi::Status lanczos_sectors_impl(hphi_model* m, const int* n_up, int n_sec, const hphi_lanczos_params* p,
+                                  hphi_lanczos_result* res, cudaStream_t st) {
+  std::vector<hphi_model*> subs(n_sec, nullptr);
+  hphi::Status s;
+  for (int i = 0; i < n_sec; ++i)
+    if ((s = sector_model(m, n_up[i], st, &subs[i])).code) return s;
+  std::vector<std::unique_ptr<LzPlan>> plans;
+  for (int i = 0; i < n_sec; ++i) {
+    hphi_lanczos_params q = *p;
+    q.seed = p->seed + (uint64_t)n_up[i];
+    q.v0 = nullptr;
+    q.profile = 0;
+    plans.emplace_back(new LzPlan());
+    if ((s = lz_prepare(subs[i], &q, *plans.back())).code) return s;
+  }
+  Timer tm;
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
+  s = run_graph(st, tm, n_sec, [&](int i, cudaStream_t cs) { return lz_enqueue(*plans[i], cs); });
+  if (s.code) return s;
+  float ms = 0.f;
+  for (int i = 0; i < n_sec; ++i)
+    if ((s = lz_collect(*plans[i], &res[i], st)).code) return s;
+  HPHI_CUDA_TRY(cudaEventElapsedTime(&ms, tm.a, tm.b));
+  for (int i = 0; i < n_sec; ++i) res[i].device_ms = ms;
   return {};
 }
 
@@ -1095,6 +1209,25 @@ int hphi_lanczos_run(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_r
   if (p->steps < 1 || p->steps > 4096 || (p->prec != HPHI_FP64 && p->prec != HPHI_FP32) || p->n_eig < 1 || p->n_eig > 8)
     return fail(m, HPHI_ERR_INVALID_ARG, "lanczos: steps in 1..4096, prec FP64/FP32, n_eig in 1..8");
   hphi::Status s = lanczos_impl(m, p, r, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
+int hphi_lanczos_run_sectors(hphi_model* m, const int* n_up_list, int n_sectors, const hphi_lanczos_params* p,
+                             hphi_lanczos_result* results, void* stream) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (m->kind != HPHI_SPIN_HALF) return fail(m, HPHI_ERR_INVALID_ARG, "lanczos_run_sectors: spin models only");
+  if (!n_up_list || !p || !results || n_sectors < 1 || n_sectors > 64)
+    return fail(m, HPHI_ERR_INVALID_ARG, "lanczos_run_sectors: 1..64 sectors, non-NULL lists");
+  if (p->steps < 1 || p->steps > 4096 || (p->prec != HPHI_FP64 && p->prec != HPHI_FP32) || p->n_eig < 1 || p->n_eig > 8)
+    return fail(m, HPHI_ERR_INVALID_ARG, "lanczos_run_sectors: steps in 1..4096, prec FP64/FP32, n_eig in 1..8");
+  if (p->v0) return fail(m, HPHI_ERR_INVALID_ARG, "lanczos_run_sectors: start vectors are seeded per sector (v0 must be NULL)");
+  for (int i = 0; i < n_sectors; ++i) {
+    if (n_up_list[i] < 0 || n_up_list[i] > m->n_sites || m->n_sites > 40)
+      return fail(m, HPHI_ERR_INVALID_ARG, "lanczos_run_sectors: n_up out of range (or more than 40 sites)");
+    for (int j = 0; j < i; ++j)
+      if (n_up_list[j] == n_up_list[i]) return fail(m, HPHI_ERR_INVALID_ARG, "lanczos_run_sectors: repeated sector");
+  }
+  hphi::Status s = lanczos_sectors_impl(m, n_up_list, n_sectors, p, results, (cudaStream_t)stream);
   return s.code ? fail(m, s) : HPHI_OK;
 }
 

@@ -312,3 +312,57 @@ def test_tpq_64_starts_layout():
         one = m.tpq(1, 10, l=1.0, psi0=torch.as_tensor(np.ascontiguousarray(psi0[:, c:c + 1])))
         assert _rel(res["u"][:, c], one["u"][:, 0]) < 1e-12
     assert np.all(np.abs(res["u"][0]) < 0.2)  # infinite-temperature energy ~ Tr H / D = 0
+
+
+# ----------------------------------------------------------------------------- sector batches
+def test_lanczos_sectors_match_oracle_and_single_runs():
+    n = 12
+    spec = wl.j1j2_ring(n, 1.0, 0.5)
+    m = hp.Model.from_spec(spec)
+    sectors = list(range(n + 1))
+    res = m.lanczos_sectors(sectors, 60, seed=500, n_eig=2)
+    for r in res:
+        k = r["n_up"]
+        sspec = spec.with_basis(wl.BASIS_SZ, k)
+        D = oracle.dim(sspec)
+        v0 = oracle.gauss_at(500 + k, np.arange(D, dtype=np.uint64), False)
+        a, b = oracle.lanczos(sspec, v0, 60)
+        assert r["steps"] == len(a)
+        nn = min(12, len(a))
+        assert _rel(r["alpha"][:nn], a[:nn]) < 1e-12
+        e0 = oracle.ritz_values(a, b)[0]
+        assert abs(r["eig"][0] - e0) <= 1e-10 * max(1.0, abs(e0))
+        # identical to a standalone run of the same sector and seed
+        single = hp.Model.from_spec(sspec).lanczos(60, seed=500 + k, n_eig=2)
+        assert np.array_equal(single["alpha"], r["alpha"]) and np.array_equal(single["beta"], r["beta"])
+    assert abs(res[6]["eig"][0] - (-3 * n / 8)) < 1e-10  # Majumdar-Ghosh point
+
+
+def _mg_closed_forms(n, res):
+    by = {r["n_up"]: r["eig"][0] for r in res}
+    assert abs(by[n // 2] - (-3 * n / 8)) <= 1e-10 * 3 * n / 8
+    assert abs(by[0] - n * 1.5 / 4) < 1e-12 and abs(by[n] - n * 1.5 / 4) < 1e-12
+    k = 2 * np.pi * np.arange(n) / n
+    e1 = n * 1.5 / 4 + np.min((np.cos(k) - 1) + 0.5 * (np.cos(2 * k) - 1))
+    assert abs(by[n - 1] - e1) < 1e-10 and abs(by[1] - e1) < 1e-10
+    # S^z <-> -S^z partners share their spectrum; after a fixed step count the slowest
+    # mid-size sectors are converged to ~1e-9, so this checks the pairing at 1e-7
+    for up in range(n + 1):
+        assert abs(by[up] - by[n - up]) <= 1e-7 * max(1.0, abs(by[up]))
+
+
+def test_j1j2_ring28_all_sectors_fp64_closed_forms():
+    """The uneven-sector workload at full size (29 sectors, dims 1 .. 40,116,600, 150 steps)."""
+    W = wl.workload("j1j2_ring28_all_sectors")
+    m = hp.Model.from_spec(W["model"])
+    res = m.lanczos_sectors(W["sectors"], W["steps"], prec=hp.FP64)
+    _mg_closed_forms(28, res)
+
+
+def test_j1j2_ring28_all_sectors_fp32_refined():
+    W = wl.workload("j1j2_ring28_all_sectors")
+    m = hp.Model.from_spec(W["model"])
+    res = m.lanczos_sectors(W["sectors"], W["steps"], prec=hp.FP32, refine=True)
+    by = {r["n_up"]: r for r in res}
+    e = by[14]["e_refined"]
+    assert abs(e - (-10.5)) <= 1e-8 * 10.5 and e >= -10.5 - 1e-9
