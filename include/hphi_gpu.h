@@ -140,6 +140,25 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
  * held by every GPU that loads the library until the process exits. */
 int hphi_apply_H_noalloc(hphi_model* m, const void* v, void* w, void* stream);
 
+/* ---------------------------------------------------------------- autotuning */
+
+typedef struct {
+  int n_candidates;    /* launch configurations timed (0: nothing to tune for this model)      */
+  int best_dn_ept;     /* chosen columns per thread of the down-spin pass                       */
+  int best_up_k;       /* chosen rows per shared-memory tile of the up-spin pass                */
+  float best_ms;       /* H v time of the chosen configuration                                  */
+  float default_ms;    /* H v time of the built-in default                                      */
+  float worst_ms;      /* H v time of the slowest candidate                                     */
+} hphi_tune_result;
+
+/* Times the launch configurations of the model's H v at precision prec (HPHI_FP64 or
+ * HPHI_FP32) on a seeded vector and keeps the fastest for every later hphi_apply_H /
+ * hphi_lanczos_run / hphi_tpq_run on this model.  Today the two-pass Hubbard path is tuned
+ * (columns per thread of the down-spin pass x rows per tile of the up-spin pass); other
+ * models report n_candidates = 0.  Uses the model's workspace; synchronises the stream.
+ * *out may be NULL.  No counterpart in the paper (its CPU code has no launch shapes). */
+int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream);
+
 /* ---------------------------------------------------------------- start vectors */
 
 /* Fills v (device, [dim][nvec], precision prec) with standard-normal numbers from the
@@ -170,6 +189,10 @@ typedef struct {
                           quotient, residual |Hx - Ex| / |x| and variance (appendix A.3)   */
   double breakdown;    /* stop when beta_{k+1} <= breakdown * max(1, |alpha_k|); 0 -> 1e-13 */
   int profile;         /* 1: time every fused H v launch with CUDA events (hv_ms below)   */
+  int keep_basis;      /* refinement source: 1 keep all m Lanczos vectors in device memory
+                          and form x = V_m e~ in one streaming pass; -1 replay the recurrence
+                          (section 3.4's second pass); 0 keep them when they fit in 60% of
+                          the free device memory, else replay                            */
 } hphi_lanczos_params;
 
 typedef struct {

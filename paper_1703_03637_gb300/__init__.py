@@ -29,7 +29,7 @@ EXPORTS = [
     "hphi_add_hopping", "hphi_add_onsite_U", "hphi_add_density", "hphi_add_chemical_potential", "hphi_set_basis",
     "hphi_build_sector", "hphi_dim", "hphi_is_complex", "hphi_basis_states", "hphi_basis_ranks", "hphi_apply_H",
     "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run", "hphi_apply_H_noalloc",
-    "hphi_lanczos_run_sectors",
+    "hphi_lanczos_run_sectors", "hphi_autotune",
 ]
 
 
@@ -42,7 +42,7 @@ class LibraryError(RuntimeError):
 class LanczosParams(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("v0", ctypes.c_void_p),
                 ("n_eig", ctypes.c_int), ("refine", ctypes.c_int), ("breakdown", ctypes.c_double),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("keep_basis", ctypes.c_int)]
 
 
 class LanczosResult(ctypes.Structure):
@@ -50,6 +50,11 @@ class LanczosResult(ctypes.Structure):
                 ("eig", ctypes.c_double * 8), ("e_refined", ctypes.c_double), ("residual", ctypes.c_double),
                 ("variance", ctypes.c_double), ("device_ms", ctypes.c_float), ("hv_ms", ctypes.c_float),
                 ("hv_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int), ("best_dn_ept", ctypes.c_int), ("best_up_k", ctypes.c_int),
+                ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float), ("worst_ms", ctypes.c_float)]
 
 
 class TpqParams(ctypes.Structure):
@@ -105,6 +110,7 @@ def load(build_if_missing: bool = True):
         L.hphi_philox4x32_10.argtypes = [P, P, P, I64, P]
         L.hphi_lanczos_run.argtypes = [P, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         L.hphi_tpq_run.argtypes = [P, ctypes.POINTER(TpqParams), ctypes.POINTER(TpqResult), P]
+        L.hphi_autotune.argtypes = [P, I, ctypes.POINTER(TuneResult), P]
         L.hphi_lanczos_run_sectors.argtypes = [P, P, I, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         _lib = L
         return L
@@ -245,6 +251,14 @@ class Model:
         self._check(self._L.hphi_apply_H(self._h, _dptr(v), _dptr(w), nvec, prec, _stream()))
         return w
 
+    def autotune(self, prec=FP64) -> dict:
+        """Time the H v launch configurations and keep the fastest (see hphi_autotune)."""
+        _torch()
+        r = TuneResult()
+        self._check(self._L.hphi_autotune(self._h, prec, ctypes.byref(r), _stream()))
+        return dict(n_candidates=r.n_candidates, dn_ept=r.best_dn_ept, up_k=r.best_up_k, best_ms=r.best_ms,
+                    default_ms=r.default_ms, worst_ms=r.worst_ms)
+
     def apply_H_noalloc(self, v, w):
         """w = H v through the allocation-free entry point (fp64, one vector, real Hubbard
         models with one hopping value per species).  v and w are caller-owned CUDA tensors of
@@ -275,7 +289,7 @@ class Model:
         return out
 
     def lanczos(self, steps: int, prec=FP64, seed: int = 123432, v0=None, n_eig: int = 1, refine: bool = False,
-                breakdown: float = 0.0, profile: bool = False):
+                breakdown: float = 0.0, profile: bool = False, keep_basis: int = 0):
         """Section 3.4 Lanczos; returns dict(alpha, beta, steps, eig, e_refined, residual, variance, ms)."""
         torch = _torch()
         if v0 is not None:
@@ -283,7 +297,7 @@ class Model:
         a = np.zeros(steps)
         b = np.zeros(steps)
         p = LanczosParams(steps, prec, seed, _dptr(v0) if v0 is not None else None, n_eig, int(refine), breakdown,
-                          int(profile))
+                          int(profile), int(keep_basis))
         r = LanczosResult()
         r.alpha = a.ctypes.data
         r.beta = b.ctypes.data
@@ -294,7 +308,7 @@ class Model:
                     hv_launches=r.hv_launches, launches=r.kernel_launches)
 
     def lanczos_sectors(self, n_up_list, steps: int, prec=FP64, seed: int = 123432, n_eig: int = 1,
-                        refine: bool = False, breakdown: float = 0.0):
+                        refine: bool = False, breakdown: float = 0.0, keep_basis: int = 0):
         """Lanczos in several S^z sectors captured as one CUDA graph; one result dict per sector."""
         _torch()
         nu = np.ascontiguousarray(n_up_list, dtype=np.int32)
@@ -305,7 +319,7 @@ class Model:
         for i in range(ns):
             res[i].alpha = al[i].ctypes.data
             res[i].beta = be[i].ctypes.data
-        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0)
+        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0, int(keep_basis))
         self._check(self._L.hphi_lanczos_run_sectors(self._h, nu.ctypes.data, ns, ctypes.byref(p), res, _stream()))
         out = []
         for i in range(ns):

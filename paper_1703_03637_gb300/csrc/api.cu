@@ -93,7 +93,7 @@ cplx site_el(int a, int b, int* kb) {
 }
 
 struct Workspace {
-  DBuf vecA, vecB, x, partials, scal, work;
+  DBuf vecA, vecB, x, partials, scal, work, basis;
 };
 
 }  // namespace
@@ -749,6 +749,86 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
   return s.code ? fail(m, s) : HPHI_OK;
 }
 
+int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (prec != HPHI_FP64 && prec != HPHI_FP32) return fail(m, HPHI_ERR_INVALID_ARG, "autotune: prec FP64 or FP32");
+  hphi_tune_result res{};
+  if (!use_hub_fast(m, prec, 1, hphi::Epi::kStore)) {
+    if (out) *out = res;
+    return HPHI_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t esz = prec == HPHI_FP64 ? 8 : 4;
+  hphi::Status s;
+  if ((s = m->ws.vecA.ensure(esz * (size_t)m->dim)).code) return fail(m, s);
+  if ((s = m->ws.vecB.ensure(esz * (size_t)m->dim)).code) return fail(m, s);
+  const size_t need = hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kStore);
+  if (need && (s = m->ws.work.ensure(need)).code) return fail(m, s);
+  void* scratch = need ? m->ws.work.p : nullptr;
+  if ((s = hphi::launch_random(m->ws.vecA.p, m->dim, false, prec == HPHI_FP64, 7, st)).code) return fail(m, s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    cudaGetLastError();
+    return fail(m, HPHI_ERR_CUDA, "autotune: cudaEventCreate failed");
+  }
+  const int pi = prec == HPHI_FP64 ? 0 : 1;
+  const int saved_ept = m->hdev.tuned_ept[pi], saved_k = m->hdev.tuned_k[pi];
+  float best = 1e30f, worst = 0.f, dflt = 0.f;
+  int best_ept = 0, best_k = 0;
+  const int epts[] = {0, 1, 2, 4};
+  const int ks[] = {0, 1, 2, 4};
+  hphi::FusedArgs fa;
+  for (int ept : epts) {
+    for (int k : ks) {
+      if ((ept == 0) != (k == 0)) continue;  // (0, 0) is the built-in default
+      m->hdev.tuned_ept[pi] = ept;
+      m->hdev.tuned_k[pi] = k;
+      const int grid = hv_grid_for(m, 1, prec, hphi::Epi::kStore);
+      s = hv_launch(m, prec, m->ws.vecA.p, m->ws.vecB.p, 1, hphi::Epi::kStore, fa, grid, scratch, st);
+      if (s.code) break;
+      cudaEventRecord(a, st);
+      for (int rep = 0; rep < 3 && !s.code; ++rep)
+        s = hv_launch(m, prec, m->ws.vecA.p, m->ws.vecB.p, 1, hphi::Epi::kStore, fa, grid, scratch, st);
+      cudaEventRecord(b, st);
+      if (s.code) break;
+      if (cudaEventSynchronize(b) != cudaSuccess) {
+        s = {HPHI_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(cudaGetLastError())};
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      ms /= 3.f;
+      ++res.n_candidates;
+      if (ept == 0) dflt = ms;
+      worst = std::max(worst, ms);
+      if (ms < best) {
+        best = ms;
+        best_ept = ept;
+        best_k = k;
+      }
+    }
+    if (s.code) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (s.code) {
+    m->hdev.tuned_ept[pi] = saved_ept;
+    m->hdev.tuned_k[pi] = saved_k;
+    return fail(m, s);
+  }
+  m->hdev.tuned_ept[pi] = best_ept;
+  m->hdev.tuned_k[pi] = best_k;
+  res.best_dn_ept = best_ept;
+  res.best_up_k = best_k;
+  res.best_ms = best;
+  res.default_ms = dflt;
+  res.worst_ms = worst;
+  if (out) *out = res;
+  return HPHI_OK;
+}
+
 int hphi_apply_H_noalloc(hphi_model* m, const void* v, void* w, void* stream) {
   int rc = check_built(m);
   if (rc) return rc;
@@ -794,8 +874,9 @@ struct Timer {
 struct LzPlan {
   hphi_model* m = nullptr;
   int steps = 0, prec = 0, n_eig = 1;
-  bool cplx = false, refine = false, profile = false;
+  bool cplx = false, refine = false, profile = false, store = false;
   int64_t n_real = 0;
+  size_t vbytes = 0;
   int grid = 1, rgrid = 1, vgrid = 1;
   double* partials = nullptr;
   void* scratch = nullptr;
@@ -837,8 +918,23 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   hphi::Status s;
   // the refinement's fp64 H x reuses buffer A, which must then hold an fp64 vector
   const size_t need_a = L.refine ? std::max(vbytes, (size_t)8 * (size_t)L.n_real) : vbytes;
-  if ((s = ws.vecA.ensure(need_a)).code) return s;
-  if ((s = ws.vecB.ensure(vbytes)).code) return s;
+  L.vbytes = vbytes;
+  // keep the whole basis when asked, or when it fits comfortably (the refinement then needs
+  // one streaming pass over it instead of a second Lanczos run)
+  if (L.refine && p->keep_basis >= 0) {
+    const size_t need = (size_t)(steps + 1) * vbytes;
+    if (p->keep_basis == 1) {
+      L.store = true;
+    } else {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+      // a basis buffer kept from an earlier run counts as free (ensure() reuses or replaces it)
+      L.store = ws.basis.bytes >= need || need <= (size_t)(0.6 * (double)(free_b + ws.basis.bytes));
+    }
+    if (L.store && (s = ws.basis.ensure(need)).code) return s;
+  }
+  if ((s = ws.vecA.ensure(L.store ? (size_t)8 * (size_t)L.n_real : need_a)).code) return s;
+  if (!L.store && (s = ws.vecB.ensure(vbytes)).code) return s;
   if (L.refine && (s = ws.x.ensure(8 * (size_t)L.n_real)).code) return s;
   if (use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1)) {
     size_t need = hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kLanczos1);
@@ -881,22 +977,34 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   hphi::Status s;
   L.launches = 0;
   HPHI_CUDA_TRY(cudaMemsetAsync(L.base, 0, sizeof(double) * L.nsc, st));
+  // stored basis: V_k at slot k (C_k); otherwise two buffers A / B swapped every step
+  auto slot = [&](int k) -> void* {
+    return static_cast<char*>(ws.basis.p) + (size_t)k * L.vbytes;
+  };
+  void* c0 = L.store ? slot(0) : ws.vecA.p;
+  void* p0 = L.store ? slot(1) : ws.vecB.p;
   auto start = [&]() -> hphi::Status {
     if (L.v0) return {};
     ++L.launches;  // buffer A holds C_0 (regenerated bit-identically for the second pass)
-    return hphi::launch_random(ws.vecA.p, m->dim, cplx, prec == HPHI_FP64, L.seed, st);
+    return hphi::launch_random(c0, m->dim, cplx, prec == HPHI_FP64, L.seed, st);
   };
   auto run_pass = [&](bool with_x) -> hphi::Status {
     hphi::Status q;
     L.launches += 2 + 4 * steps;
-    if ((q = hphi::launch_lz_init(prec, cplx, L.v0, ws.vecA.p, ws.vecB.p, L.n_real, L.partials, L.vgrid, st)).code)
-      return q;
+    if ((q = hphi::launch_lz_init(prec, cplx, L.v0, c0, p0, L.n_real, L.partials, L.vgrid, st)).code) return q;
     if ((q = hphi::launch_lz_init_fin(L.lz, L.partials, L.vgrid, st)).code) return q;
     if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)L.n_real, st));
-    void* C = ws.vecA.p;
-    void* P = ws.vecB.p;
+    void* C = c0;
+    void* P = p0;
     for (int k = 0; k < steps; ++k) {
       hphi::FusedArgs fa;
+      if (L.store) {
+        // pass 1 reads v_{k-1} from its slot and writes u into slot k + 1 (slot 1 holds the
+        // zero vector at k = 0); pass 2 finishes slot k + 1 in place
+        C = slot(k);
+        P = slot(k + 1);
+        fa.in = (k == 0) ? slot(1) : slot(k - 1);
+      }
       fa.out = P;
       fa.scal = L.lz.s;
       fa.partials = L.partials;
@@ -910,7 +1018,7 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
                                      L.partials, L.vgrid, st)).code)
         return q;
       if ((q = hphi::launch_lz_fin2(L.lz, k, L.brk, L.partials, L.vgrid, st)).code) return q;
-      std::swap(C, P);
+      if (!L.store) std::swap(C, P);
     }
     return {};
   };
@@ -919,8 +1027,16 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   ++L.launches;
   if ((s = hphi::launch_tridiag(L.lz, steps, L.n_eig, L.refine, st)).code) return s;
   if (!L.refine) return {};
-  if ((s = start()).code) return s;
-  if ((s = run_pass(true)).code) return s;
+  if (L.store) {
+    // Ritz vector straight from the stored basis: one streaming pass
+    ++L.launches;
+    if ((s = hphi::launch_lz_combine(prec, L.lz, slot(0), L.n_real, (int64_t)(L.vbytes / (prec == HPHI_FP64 ? 8 : 4)),
+                                     ws.x.as<double>(), L.vgrid, st)).code)
+      return s;
+  } else {
+    if ((s = start()).code) return s;
+    if ((s = run_pass(true)).code) return s;
+  }
   L.launches += 4;
   // fp64 H x into the (now free) buffer A, then E, variance and residual
   double* hx = ws.vecA.as<double>();

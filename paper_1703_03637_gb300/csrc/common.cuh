@@ -100,6 +100,9 @@ struct HubDev {
   // two-pass path (real model, one hopping value per species): neighbour tables
   // nbr[k * maxdeg + q] = rank of the q-th hop target of species state k | sign << 31
   int fast;
+  int dn_ept;                // pass D columns per thread (0: default)
+  int up_k;                  // pass U rows per tile (0: largest that fits)
+  int tuned_ept[2], tuned_k[2];  // autotuner choices per precision (HPHI_FP64, HPHI_FP32)
   int maxdeg_up, maxdeg_dn;
   double c_up, c_dn;         // the hopping coefficient of each species
   const uint32_t* nbr_up;
@@ -160,6 +163,7 @@ struct FusedArgs {
   // TPQ: Xn <- inv[c] * (l * X - Y / Ns); partial sums <X, Y>, |Y|^2, |Xn|^2 per column.
   // Refine: stores Y and reduces <x, Y>, <x, x>.
   void* out = nullptr;             // P (Lanczos) / X_{k+1} (TPQ) / Hx (refine)
+  const void* in = nullptr;        // Lanczos: previous vector read by pass 1 (null: same as out)
   const double* scal = nullptr;    // device scalars read at kernel start
   double* partials = nullptr;      // [grid][nvec][kMaxRedQ]
   const int* done = nullptr;       // device flag: skip all work when set
@@ -206,6 +210,9 @@ Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* 
 Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, cudaStream_t st);
 Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, cudaStream_t st);
 Status launch_refine_fin(const LzDev& lz, const double* partials, int grid, int which, cudaStream_t st);
+// x = sum_k coef_k sigma_k V_k over the stored Lanczos vectors (k < steps_done)
+Status launch_lz_combine(int prec, const LzDev& lz, const void* V, int64_t n_real, int64_t stride_real, double* x,
+                         int grid, cudaStream_t st);
 Status launch_refine_resid(bool cplx, const double* x, const double* hx, int64_t n_real, const LzDev& lz,
                            double* partials, int grid, cudaStream_t st);
 

@@ -168,8 +168,9 @@ __device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>:
   } else if constexpr (E == Epi::kLanczos1) {
     // P <- sigma_k * (H C) - beta_k sigma_{k-1} * P ;  partial <C, H C>
     S* P = reinterpret_cast<S*>(fa.out);
+    const S* Pin = fa.in ? reinterpret_cast<const S*>(fa.in) : P;
     R pr, pi;
-    ld<S>(P, idx, pr, pi);
+    ld<S>(Pin, idx, pr, pi);
     const R c1 = (R)es.c1, c2 = (R)es.c2;
     st<S>(P, idx, c1 * hr - c2 * pr, c1 * hi - c2 * pi);
     red.add(0, sr, hr);

@@ -479,9 +479,32 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up_q(const HubDev md, const 
 template <class R>
 int pick_k(const HubDev& md) {
   const int64_t row = md.dim_up * (int64_t)sizeof(R);
-  if (4 * row <= kSmemBudget) return 4;
-  if (2 * row <= kSmemBudget) return 2;
-  return 1;
+  int k = 1;
+  if (4 * row <= kSmemBudget) k = 4;
+  else if (2 * row <= kSmemBudget) k = 2;
+  if (md.up_k > 0 && md.up_k < k) k = (md.up_k >= 2) ? 2 : 1;
+  return k;
+}
+
+int pick_kq(const HubDev& md) {
+  int k = (2 * md.dim_up * 8 <= kSmemBudget) ? 2 : 1;
+  if (md.up_k == 1) k = 1;
+  return k;
+}
+
+// pass D launch with the tuned (or default) columns per thread
+template <class R>
+Status launch_dn(const HubDev& md, const R* X, R* W, const int* done, cudaStream_t st) {
+  int ept = md.dn_ept > 0 ? md.dn_ept : (sizeof(R) == 8 ? HPHI_DN_EPT64 : HPHI_DN_EPT32);
+  if (ept != 1 && ept != 2 && ept != 4) ept = 1;
+  const int64_t sw = (int64_t)kThreads * ept;
+  const int64_t items = ((md.dim_up + sw - 1) / sw) * md.dim_dn;
+  const int gd = (int)std::min<int64_t>(items, (int64_t)num_sms() * 8);
+  if (ept == 4) k_hub_dn<R, 4><<<gd, kThreads, 0, st>>>(md, X, W, done);
+  else if (ept == 2) k_hub_dn<R, 2><<<gd, kThreads, 0, st>>>(md, X, W, done);
+  else k_hub_dn<R, 1><<<gd, kThreads, 0, st>>>(md, X, W, done);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
 }
 
 template <class R, int K, Epi E>
@@ -542,14 +565,10 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
   HPHI_CUDA_TRY(cudaGetLastError());
   k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done);
   HPHI_CUDA_TRY(cudaGetLastError());
-  constexpr int EPT = HPHI_DN_EPT64;
-  const int64_t sw = (int64_t)kThreads * EPT;
-  const int64_t items = ((md.dim_up + sw - 1) / sw) * md.dim_dn;
-  const int gd = (int)std::min<int64_t>(items, (int64_t)num_sms() * 8);
-  k_hub_dn<long long, EPT><<<gd, kThreads, 0, st>>>(md, Q, WQ, fa.done);
-  HPHI_CUDA_TRY(cudaGetLastError());
+  Status sd = launch_dn<long long>(md, Q, WQ, fa.done, st);
+  if (sd.code) return sd;
   double* out = reinterpret_cast<double*>(w);
-  const int K = (2 * md.dim_up * 8 <= kSmemBudget) ? 2 : 1;
+  const int K = pick_kq(md);
   const size_t smem = (size_t)K * md.dim_up * 8;
   if (K == 2) {
     HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up_q<2, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
@@ -563,7 +582,7 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
 }
 
 int upq_grid(const HubDev& md, Epi epi) {
-  const int K = (2 * md.dim_up * 8 <= kSmemBudget) ? 2 : 1;
+  const int K = pick_kq(md);
   int occ = 1;
 #define HPHI_OCCQ(KK)                                                          \
   switch (epi) {                                                               \
@@ -585,12 +604,8 @@ Status launch_r(const HubDev& md, const void* v, void* w, void* scratch, const F
   // kStore writes the down-spin sums into w and finishes them in place; the fused steps
   // use the scratch vector
   R* W = (E == Epi::kStore) ? reinterpret_cast<R*>(w) : reinterpret_cast<R*>(scratch);
-  constexpr int EPT = sizeof(R) == 8 ? HPHI_DN_EPT64 : HPHI_DN_EPT32;
-  const int64_t sw = (int64_t)kThreads * EPT;
-  const int64_t items = ((md.dim_up + sw - 1) / sw) * md.dim_dn;
-  const int gd = (int)std::min<int64_t>(items, (int64_t)num_sms() * 8);
-  k_hub_dn<R, EPT><<<gd, kThreads, 0, st>>>(md, X, W, fa.done);
-  HPHI_CUDA_TRY(cudaGetLastError());
+  Status sd = launch_dn<R>(md, X, W, fa.done, st);
+  if (sd.code) return sd;
   R* out = reinterpret_cast<R*>(w);
   switch (pick_k<R>(md)) {
     case 4: return launch_up<R, 4, E>(md, X, W, out, fa, grid_up, st);
@@ -641,9 +656,12 @@ Status noalloc_scratch(void** out) {
 
 }  // namespace
 
+HubDev with_shape(const HubDev& md, int prec);
+
 size_t noalloc_capacity_bytes() { return kNoAllocScratchBytes; }
 
-Status launch_hub_store_noalloc(const HubDev& md, const void* v, void* w, cudaStream_t st) {
+Status launch_hub_store_noalloc(const HubDev& md0, const void* v, void* w, cudaStream_t st) {
+  const HubDev md = with_shape(md0, HPHI_FP64);
   const size_t need = quant_scratch_bytes(md);
   if (need > kNoAllocScratchBytes)
     return {HPHI_ERR_INVALID_ARG, "hphi_apply_H_noalloc: the basis needs " + std::to_string(need) +
@@ -673,7 +691,17 @@ bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi) {
   return row <= kSmemBudget;
 }
 
-int hub_up_grid(const HubDev& md, int prec, Epi epi) {
+// the launch shape of one precision: the autotuner's choice, else the built-in default
+HubDev with_shape(const HubDev& md, int prec) {
+  HubDev t = md;
+  const int i = prec == HPHI_FP64 ? 0 : 1;
+  t.dn_ept = md.tuned_ept[i];
+  t.up_k = md.tuned_k[i];
+  return t;
+}
+
+int hub_up_grid(const HubDev& md0, int prec, Epi epi) {
+  const HubDev md = with_shape(md0, prec);
   return prec == HPHI_FP64 ? upq_grid(md, epi) : up_grid_r<float>(md, epi);
 }
 
@@ -682,8 +710,9 @@ size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi) {
   return epi == Epi::kStore ? 0 : (size_t)4 * md.dim;
 }
 
-Status launch_hub_fast(const HubDev& md, int prec, const void* v, void* w, void* scratch, Epi epi,
+Status launch_hub_fast(const HubDev& md0, int prec, const void* v, void* w, void* scratch, Epi epi,
                        const FusedArgs& fa, int grid_up, cudaStream_t st) {
+  const HubDev md = with_shape(md0, prec);
   if (prec == HPHI_FP64) {
     switch (epi) {
       case Epi::kStore: return launch_q<Epi::kStore>(md, v, w, scratch, fa, grid_up, st);

@@ -244,6 +244,23 @@ __global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double* __restrict_
   }
 }
 
+// ------------------------------------------------------------------ Ritz vector from a stored basis
+// x = sum_{k < n} coef_k sigma_k V_k, V_k the unnormalised Lanczos vectors kept in HBM
+// (stride_real reals apart); fp64 accumulation, one streaming read of the basis.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_lz_combine(LzDev lz, const R* __restrict__ V, int64_t n_real,
+                                                          int64_t stride_real, double* __restrict__ x) {
+  __shared__ double s_c[4096];
+  const int n = *lz.steps_done;
+  for (int k = threadIdx.x; k < n; k += kThreads) s_c[k] = lz.coef[k] * lz.sig[k];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += (int64_t)gridDim.x * kThreads) {
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(s_c[k], (double)V[(int64_t)k * stride_real + i], acc);
+    x[i] = acc;
+  }
+}
+
 // ------------------------------------------------------------------ refinement
 __global__ void k_refine_fin(LzDev lz, const double* __restrict__ partials, int grid, int which) {
   __shared__ double sm[kThreads];
@@ -395,6 +412,16 @@ Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials
 Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, cudaStream_t st) {
   (void)m_max;
   k_tridiag<<<1, 32 * 8, 0, st>>>(lz, n_eig, want_vec ? 1 : 0, lz.tri + 16);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_lz_combine(int prec, const LzDev& lz, const void* V, int64_t n_real, int64_t stride_real, double* x,
+                         int grid, cudaStream_t st) {
+  if (prec == HPHI_FP64)
+    k_lz_combine<double><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const double*>(V), n_real, stride_real, x);
+  else
+    k_lz_combine<float><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const float*>(V), n_real, stride_real, x);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }

@@ -252,6 +252,9 @@ def test_lanczos_hubbard_two_pass_fp32_refined():
     assert _rel(r64["alpha"][:12], a[:12]) < 1e-12 and _rel(r64["beta"][:12], b[:12]) < 1e-12
     r32 = m.lanczos(20, prec=hp.FP32, v0=torch.as_tensor(v0))
     assert _rel(r32["alpha"][:8], a[:8]) < 1e-5
+    # two-pass kernels reading the previous vector from a kept basis slot give the same run
+    r32k = m.lanczos(20, prec=hp.FP32, v0=torch.as_tensor(v0), refine=True, keep_basis=1)
+    assert np.array_equal(r32k["alpha"], r32["alpha"])
 
 
 def test_lanczos_mixed_with_fp64_refinement():
@@ -260,13 +263,19 @@ def test_lanczos_mixed_with_fp64_refinement():
     v0 = wl.gaussian_vector(41, m.dim)[:, 0]
     a, b = oracle.lanczos(spec, v0, 120)
     e0 = oracle.ritz_values(a, b)[0]
-    r = m.lanczos(120, prec=hp.FP32, v0=torch.as_tensor(v0), refine=True)
+    r = m.lanczos(120, prec=hp.FP32, v0=torch.as_tensor(v0), refine=True, keep_basis=-1)
     assert abs(r["e_refined"] - e0) <= 1e-8 * abs(e0)
     assert r["e_refined"] >= e0 - 1e-12 * abs(e0)  # variational
     assert r["residual"] < 1e-3
-    r64 = m.lanczos(120, prec=hp.FP64, v0=torch.as_tensor(v0), refine=True)
-    assert abs(r64["e_refined"] - e0) <= 1e-10 * abs(e0)
-    assert r64["residual"] < 1e-5
+    # the same Ritz vector built from the basis kept in device memory instead of a replay
+    rk = m.lanczos(120, prec=hp.FP32, v0=torch.as_tensor(v0), refine=True, keep_basis=1)
+    assert np.array_equal(rk["alpha"], r["alpha"])
+    assert abs(rk["e_refined"] - r["e_refined"]) <= 1e-12 * abs(e0)
+    assert abs(rk["residual"] - r["residual"]) <= 1e-6 * r["residual"] + 1e-12
+    for kb in (-1, 1):
+        r64 = m.lanczos(120, prec=hp.FP64, v0=torch.as_tensor(v0), refine=True, keep_basis=kb)
+        assert abs(r64["e_refined"] - e0) <= 1e-10 * abs(e0)
+        assert r64["residual"] < 1e-5
 
 
 # ----------------------------------------------------------------------------- TPQ
@@ -366,3 +375,66 @@ def test_j1j2_ring28_all_sectors_fp32_refined():
     by = {r["n_up"]: r for r in res}
     e = by[14]["e_refined"]
     assert abs(e - (-10.5)) <= 1e-8 * 10.5 and e >= -10.5 - 1e-9
+
+
+# ----------------------------------------------------------------------------- full-size workloads
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_heisenberg_6x6_sz0_full_size_sampled_rows(prec):
+    """The 9,075,135,300-row sector: one H v at full size, sampled rows (first, last and random)
+    recomputed by the oracle from the Philox definition of the input."""
+    W = wl.workload("heisenberg_6x6_sz0")
+    spec = W["model"]
+    m = hp.Model.from_spec(spec)
+    assert m.dim == 9075135300
+    p = hp.FP64 if prec == "fp64" else hp.FP32
+    seed = 911
+    v = m.random_vector(seed, prec=p)
+    w = m.apply_H(v)
+    rng = np.random.default_rng(12)
+    rows = np.unique(np.concatenate([[0, 1, m.dim - 1], rng.integers(0, m.dim, size=1000)])).astype(np.int64)
+    got = w[torch.as_tensor(rows, device="cuda"), 0].double().cpu().numpy()
+    ref = oracle.apply_H_rows_philox(spec, rows.astype(np.uint64), seed, False).real
+    assert _rel(got, ref) < (1e-12 if prec == "fp64" else 2e-6)
+    del v, w
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_kitaev_24_tpq64_full_size(prec):
+    """The 2^24-row Kitaev cluster with 64 interleaved starts: the first records of starts 0
+    and 63 against the oracle run on the same Philox starts, and the infinite-temperature
+    moments Tr H / D = 0 and Tr H^2 / D = 36 K^2/16 + 24*3 h^2/4 from the k = 0 record."""
+    W = wl.workload("kitaev_24_tpq64")
+    spec = W["model"]
+    m = hp.Model.from_spec(spec)
+    nv, K, seed = 64, 3, 4242
+    p = hp.FP64 if prec == "fp64" else hp.FP32
+    res = m.tpq(nv, K, l=1.0, prec=p, seed=seed)
+    Ns = spec.n_sites
+    h2_0 = res["h2"][0] * Ns * Ns
+    assert abs(np.mean(h2_0) - (36 / 16 + 24 * 3 * 0.05 ** 2 / 4)) < 2e-3
+    assert abs(np.mean(res["u"][0])) < 2e-3
+    D = m.dim
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    for c in (0, 63):
+        idx = np.arange(D, dtype=np.uint64) * nv + c
+        psi0 = oracle.gauss_at(seed, idx, True)
+        u, h2, nrm = oracle.tpq(spec, psi0, K, 1.0)
+        assert _rel(res["u"][:, c], u) < tol
+        assert _rel(res["h2"][:, c], h2) < tol
+        assert _rel(res["norm"][:, c], nrm) < tol
+    torch.cuda.empty_cache()
+
+
+# ----------------------------------------------------------------------------- autotuner
+def test_autotune_keeps_results_exact():
+    spec = wl.hubbard_square(4, 3, 1.0, 8.0).with_basis(wl.BASIS_NUMBER, 6, 6)
+    m = hp.Model.from_spec(spec)
+    v = wl.gaussian_vector(71, m.dim)[:, 0]
+    ref = oracle.apply_H(spec, v).real
+    for prec in (hp.FP64, hp.FP32):
+        t = m.autotune(prec)
+        assert t["n_candidates"] >= 4 and t["best_ms"] <= t["default_ms"] + 1e-6
+        w = m.apply_H(_to_dev(m, v[:, None], prec)).cpu().numpy()[:, 0]
+        assert _rel(w, ref) < (1e-12 if prec == hp.FP64 else 2e-5)
+    assert hp.Model.from_spec(wl.heisenberg_ring(8)).autotune()["n_candidates"] == 0
