@@ -114,7 +114,7 @@ struct hphi_model {
   int device = 0;
   // device data
   DBuf d_entries, d_cls, d_lin, d_pairs, d_pcoef, d_hi_off, d_lo_rank, d_lo_list, d_lo_off;
-  DBuf d_nbr_up, d_deg_up, d_nbr_dn, d_deg_dn;
+  DBuf d_nbr_up, d_deg_up, d_nbr_dn, d_deg_dn, d_npos_up, d_npos_dn;
   hphi::SpinDev sdev{};
   hphi::HubDev hdev{};
   Workspace ws;
@@ -462,12 +462,20 @@ hphi::Status build_hub_fast(hphi_model* m, cudaStream_t st) {
   if ((s = m->d_deg_up.ensure((size_t)d.dim_up)).code) return s;
   if ((s = m->d_nbr_dn.ensure((size_t)4 * d.dim_dn * d.maxdeg_dn)).code) return s;
   if ((s = m->d_deg_dn.ensure((size_t)d.dim_dn)).code) return s;
+  if ((s = m->d_npos_up.ensure((size_t)d.dim_up)).code) return s;
+  if ((s = m->d_npos_dn.ensure((size_t)d.dim_dn)).code) return s;
   d.nbr_up = m->d_nbr_up.as<uint32_t>();
   d.deg_up = m->d_deg_up.as<uint8_t>();
+  d.npos_up = m->d_npos_up.as<uint8_t>();
   d.nbr_dn = m->d_nbr_dn.as<uint32_t>();
   d.deg_dn = m->d_deg_dn.as<uint8_t>();
-  if ((s = hphi::build_hub_neighbours(d, 0, m->d_nbr_up.as<uint32_t>(), m->d_deg_up.as<uint8_t>(), st)).code) return s;
-  if ((s = hphi::build_hub_neighbours(d, 1, m->d_nbr_dn.as<uint32_t>(), m->d_deg_dn.as<uint8_t>(), st)).code) return s;
+  d.npos_dn = m->d_npos_dn.as<uint8_t>();
+  if ((s = hphi::build_hub_neighbours(d, 0, m->d_nbr_up.as<uint32_t>(), m->d_deg_up.as<uint8_t>(),
+                                      m->d_npos_up.as<uint8_t>(), st)).code)
+    return s;
+  if ((s = hphi::build_hub_neighbours(d, 1, m->d_nbr_dn.as<uint32_t>(), m->d_deg_dn.as<uint8_t>(),
+                                      m->d_npos_dn.as<uint8_t>(), st)).code)
+    return s;
   d.fast = 1;
   return {};
 }

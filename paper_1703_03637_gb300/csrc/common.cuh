@@ -107,8 +107,10 @@ struct HubDev {
   double c_up, c_dn;         // the hopping coefficient of each species
   const uint32_t* nbr_up;
   const uint8_t* deg_up;
+  const uint8_t* npos_up;    // entries [0, npos) carry sign +1, [npos, deg) sign -1
   const uint32_t* nbr_dn;
   const uint8_t* deg_dn;
+  const uint8_t* npos_dn;
 };
 
 // ------------------------------------------------------------------ scalar traits
@@ -177,7 +179,8 @@ int hv_grid(int nvec);  // upper bound of any H v grid (partials sizing)
 
 // Two-pass Hubbard path (k_hub.cu): neighbour tables, and H v = diag + up hops (row tiles
 // in shared memory) + down hops (stripe-major row combinations into the scratch vector W).
-Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, cudaStream_t st);
+Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, uint8_t* npos,
+                            cudaStream_t st);
 bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi);
 int hub_up_grid(const HubDev& md, int prec, Epi epi);
 size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi);  // scratch the launch needs

@@ -32,7 +32,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 namespace {
 
-constexpr int kUpThreads = 1024;
 // columns per thread in pass D (stripe = kThreads * EPT columns); the stripe of all rows is
 // the L2 working set of pass D
 #ifndef HPHI_DN_EPT32
@@ -79,26 +78,50 @@ constexpr int kSmemBudget = 208000;  // shared-memory bytes for the row tile (pl
 // neighbour table of one species, hop-slot major: nbr[q * n + k] is the q-th active hop
 // target of state k (rank | sign << 31), so threads of consecutive states read
 // consecutive words
-__global__ void k_hub_nbr(const HubDev md, int species, uint32_t* __restrict__ nbr, uint8_t* __restrict__ deg) {
+__global__ void k_hub_nbr(const HubDev md, int species, uint32_t* __restrict__ nbr, uint8_t* __restrict__ deg,
+                          uint8_t* __restrict__ npos) {
   const int64_t n = species ? md.dim_dn : md.dim_up;
   const int e0 = species ? md.n_up_hops : 0;
   const int ne = species ? md.n_dn_hops : md.n_up_hops;
   const uint32_t* list = species ? md.list_dn : md.list_up;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t b = md.sector ? list[k] : (uint32_t)k;
-    int cnt = 0;
-    for (int q = 0; q < ne; ++q) {
-      const HopEntry h = md.hops[e0 + q];
-      if (((b >> h.i) ^ (b >> h.j)) & 1u) {
-        const uint32_t b2 = b ^ h.mask;
-        const uint32_t r2 = md.sector ? md.rank[b2] : b2;
-        const uint32_t sg = (uint32_t)(__popc(b & h.between) & 1);
-        nbr[(int64_t)cnt * n + k] = r2 | (sg << 31);
-        ++cnt;
+    // positive-sign targets first, then negative ones (hop order within each group)
+    int cnt = 0, np = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = 0; q < ne; ++q) {
+        const HopEntry h = md.hops[e0 + q];
+        if (((b >> h.i) ^ (b >> h.j)) & 1u) {
+          const uint32_t sg = (uint32_t)(__popc(b & h.between) & 1);
+          if ((int)sg != pass) continue;
+          const uint32_t b2 = b ^ h.mask;
+          const uint32_t r2 = md.sector ? md.rank[b2] : b2;
+          nbr[(int64_t)cnt * n + k] = r2 | (sg << 31);
+          ++cnt;
+        }
       }
+      if (pass == 0) np = cnt;
     }
     deg[k] = (uint8_t)cnt;
+    npos[k] = (uint8_t)np;
   }
+}
+
+// difference of two accumulated sums (pass D keeps positive and negative terms apart)
+__device__ __forceinline__ IntAcc diff_acc(const IntAcc& p, const IntAcc& n) {
+  IntAcc r;
+  r.s = p.s - n.s;
+  return r;
+}
+__device__ __forceinline__ F32Acc diff_acc(const F32Acc& p, const F32Acc& n) {
+  F32Acc r;
+  r.s = p.s - n.s;
+  return r;
+}
+__device__ __forceinline__ FixAcc diff_acc(const FixAcc& p, const FixAcc& n) {
+  FixAcc r = p;  // fp64 values never take pass D (they are quantised first); kept for completeness
+  r.add(n.value(), true);
+  return r;
 }
 
 // pass D: W[d][u] = sum over down-spin neighbours d' of d of +-X[d'][u].  Items run
@@ -107,7 +130,8 @@ __global__ void k_hub_nbr(const HubDev md, int species, uint32_t* __restrict__ n
 // broadcasts it with shuffles, so the data loads of four neighbours issue back to back.
 template <class R, int EPT>
 __global__ void __launch_bounds__(kThreads) k_hub_dn(const HubDev md, const R* __restrict__ X, R* __restrict__ W,
-                                                     const int* __restrict__ done) {
+                                                     const int* __restrict__ done,
+                                                     unsigned long long* __restrict__ next_item) {
   using A = typename SumAcc<R>::T;
   if (done != nullptr && *done) return;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -116,27 +140,39 @@ __global__ void __launch_bounds__(kThreads) k_hub_dn(const HubDev md, const R* _
   const int n_str = (int)((dim_up + SW - 1) / SW);
   const int64_t n_items = (int64_t)n_str * dim_dn;
   const int last_full = (int)(dim_up / SW);  // stripes [0, last_full) need no bounds checks
-
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+  // items are handed out in order from a counter, so all CTAs stay on neighbouring rows of
+  // one stripe and the stripe of X they gather stays in L2 (static round-robin lets CTAs
+  // drift over several stripes)
+  __shared__ int64_t s_item;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = (int64_t)atomicAdd(next_item, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= n_items) break;
     const int s = (int)(item / dim_dn);
     const int64_t d = item - (int64_t)s * dim_dn;
     const int deg = md.deg_dn[d];
+    const int npos = md.npos_dn[d];
     const int u0 = s * SW + tid;
     const bool full = s < last_full;
-    A acc[EPT];
+    // the list is sign-sorted: entries [0, npos) add, [npos, deg) subtract; each group is
+    // summed without per-term sign handling and the two sums are subtracted once
+    A accp[EPT], accn[EPT];
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) acc[j].zero();
+    for (int j = 0; j < EPT; ++j) {
+      accp[j].zero();
+      accn[j].zero();
+    }
     for (int qb = 0; qb < deg; qb += 32) {
       const int nq = (deg - qb < 32) ? (deg - qb) : 32;
       const uint32_t mine = (lane < nq) ? __ldg(md.nbr_dn + (int64_t)(qb + lane) * dim_dn + d) : 0u;
       for (int q0 = 0; q0 < nq; q0 += 4) {
         R x[4][EPT];
-        bool ng[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const uint32_t e = __shfl_sync(0xffffffffu, mine, (q0 + t) & 31);
           const bool on = q0 + t < nq;
-          ng[t] = (e >> 31) != 0;
           const R* src = X + (int64_t)(e & 0x7fffffffu) * dim_up + u0;
 #pragma unroll
           for (int j = 0; j < EPT; ++j) {
@@ -144,12 +180,31 @@ __global__ void __launch_bounds__(kThreads) k_hub_dn(const HubDev md, const R* _
             if (on && (full || u0 + j * kThreads < dim_up)) x[t][j] = __ldg(src + j * kThreads);
           }
         }
+        const int qn = qb + q0;  // list position of t = 0
+        if (qn + 4 <= npos) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < 4; ++t)
 #pragma unroll
-          for (int j = 0; j < EPT; ++j) acc[j].add(x[t][j], ng[t]);
+            for (int j = 0; j < EPT; ++j) accp[j].add(x[t][j], false);
+        } else if (qn >= npos) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) accn[j].add(x[t][j], false);
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+              if (qn + t < npos) accp[j].add(x[t][j], false);
+              else accn[j].add(x[t][j], false);
+            }
+        }
       }
     }
+    A acc[EPT];
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) acc[j] = diff_acc(accp[j], accn[j]);
     R* dst = W + d * dim_up + u0;
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
@@ -159,8 +214,8 @@ __global__ void __launch_bounds__(kThreads) k_hub_dn(const HubDev md, const R* _
 }
 
 // pass U: up-spin hops on K rows staged in shared memory, diag, + c_dn W, fused epilogue
-template <class R, int K, Epi E>
-__global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R* __restrict__ X,
+template <class R, int K, Epi E, int NT>
+__global__ void __launch_bounds__(NT) k_hub_up(const HubDev md, const R* __restrict__ X,
                                                        const R* __restrict__ W, R* __restrict__ w, FusedArgs fa) {
   using A = typename SumAcc<R>::T;
   constexpr bool F64 = sizeof(R) == 8;
@@ -171,14 +226,14 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
   __shared__ PairEntry s_pair[kMaxPairs];
   __shared__ R s_uc[kMaxLin], s_mc[kMaxLin], s_pcoef[kMaxPairGroups];  // coefficients in R
   __shared__ double s_inv[1];
-  __shared__ double s_red[(kUpThreads / 32) * kMaxRedQ];
+  __shared__ double s_red[(NT / 32) * kMaxRedQ];
 
   if (fa.done != nullptr && *fa.done) return;
   const int tid = threadIdx.x;
-  for (int k = tid; k < md.n_ulin; k += kUpThreads) { s_ulin[k] = md.ulin[k]; s_uc[k] = (R)md.ulin[k].coef; }
-  for (int k = tid; k < md.n_mulin; k += kUpThreads) { s_mlin[k] = md.mulin[k]; s_mc[k] = (R)md.mulin[k].coef; }
-  for (int k = tid; k < md.n_pairs; k += kUpThreads) s_pair[k] = md.pairs[k];
-  for (int k = tid; k < md.n_pair_groups; k += kUpThreads) s_pcoef[k] = (R)md.pair_coef[k];
+  for (int k = tid; k < md.n_ulin; k += NT) { s_ulin[k] = md.ulin[k]; s_uc[k] = (R)md.ulin[k].coef; }
+  for (int k = tid; k < md.n_mulin; k += NT) { s_mlin[k] = md.mulin[k]; s_mc[k] = (R)md.mulin[k].coef; }
+  for (int k = tid; k < md.n_pairs; k += NT) s_pair[k] = md.pairs[k];
+  for (int k = tid; k < md.n_pair_groups; k += NT) s_pcoef[k] = (R)md.pair_coef[k];
   if constexpr (E == Epi::kTpq) {
     if (tid == 0) s_inv[0] = fa.scal[0];
   }
@@ -204,7 +259,7 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
     __syncthreads();
     // tile[u * K + m] = X[d0 + m][u]: the K rows interleaved, so one vector load per
     // neighbour fetches the value of all K rows
-    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+    for (int64_t u = tid; u < dim_up; u += NT) {
       R vals[K];
 #pragma unroll
       for (int m = 0; m < K; ++m) vals[m] = (m < nk) ? __ldg(X + (d0 + m) * dim_up + u) : (R)0;
@@ -214,7 +269,7 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
     uint32_t dn[K];
 #pragma unroll
     for (int m = 0; m < K; ++m) dn[m] = (m < nk) ? (md.sector ? __ldg(md.list_dn + d0 + m) : (uint32_t)(d0 + m)) : 0u;
-    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+    for (int64_t u = tid; u < dim_up; u += NT) {
       const uint32_t up = md.sector ? __ldg(md.list_up + u) : (uint32_t)u;
       const int deg = md.deg_up[u];
       const uint32_t* nb = md.nbr_up + u;
@@ -298,7 +353,7 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up(const HubDev md, const R*
     __syncthreads();
     if (tid < nq) {
       double x = 0.0;
-      for (int k = 0; k < kUpThreads / 32; ++k) x += s_red[k * kMaxRedQ + tid];
+      for (int k = 0; k < NT / 32; ++k) x += s_red[k * kMaxRedQ + tid];
       fa.partials[(size_t)blockIdx.x * kMaxRedQ + tid] = x;
     }
   }
@@ -345,8 +400,8 @@ __global__ void __launch_bounds__(kThreads) k_quant(const double* __restrict__ X
 
 // pass U on quantised rows: K int64 rows interleaved in shared memory; the fp64 value of
 // each element (for the diagonal and the reductions) is read from X itself
-template <int K, Epi E>
-__global__ void __launch_bounds__(kUpThreads) k_hub_up_q(const HubDev md, const double* __restrict__ X,
+template <int K, Epi E, int NT>
+__global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md, const double* __restrict__ X,
                                                          const long long* __restrict__ Q,
                                                          const long long* __restrict__ WQ, const int* __restrict__ Ep,
                                                          double* __restrict__ w, FusedArgs fa) {
@@ -357,14 +412,14 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up_q(const HubDev md, const 
   __shared__ PairEntry s_pair[kMaxPairs];
   __shared__ double s_pcoef[kMaxPairGroups];
   __shared__ double s_inv[1];
-  __shared__ double s_red[(kUpThreads / 32) * kMaxRedQ];
+  __shared__ double s_red[(NT / 32) * kMaxRedQ];
 
   if (fa.done != nullptr && *fa.done) return;
   const int tid = threadIdx.x;
-  for (int k = tid; k < md.n_ulin; k += kUpThreads) s_ulin[k] = md.ulin[k];
-  for (int k = tid; k < md.n_mulin; k += kUpThreads) s_mlin[k] = md.mulin[k];
-  for (int k = tid; k < md.n_pairs; k += kUpThreads) s_pair[k] = md.pairs[k];
-  for (int k = tid; k < md.n_pair_groups; k += kUpThreads) s_pcoef[k] = md.pair_coef[k];
+  for (int k = tid; k < md.n_ulin; k += NT) s_ulin[k] = md.ulin[k];
+  for (int k = tid; k < md.n_mulin; k += NT) s_mlin[k] = md.mulin[k];
+  for (int k = tid; k < md.n_pairs; k += NT) s_pair[k] = md.pairs[k];
+  for (int k = tid; k < md.n_pair_groups; k += NT) s_pcoef[k] = md.pair_coef[k];
   if constexpr (E == Epi::kTpq) {
     if (tid == 0) s_inv[0] = fa.scal[0];
   }
@@ -390,7 +445,7 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up_q(const HubDev md, const 
     const int64_t d0 = t * K;
     const int nk = (int)((dim_dn - d0 < K) ? (dim_dn - d0) : K);
     __syncthreads();
-    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+    for (int64_t u = tid; u < dim_up; u += NT) {
 #pragma unroll
       for (int m = 0; m < K; ++m) tile[u * K + m] = (m < nk) ? __ldg(Q + (d0 + m) * dim_up + u) : 0ll;
     }
@@ -398,7 +453,7 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up_q(const HubDev md, const 
     uint32_t dn[K];
 #pragma unroll
     for (int m = 0; m < K; ++m) dn[m] = (m < nk) ? (md.sector ? __ldg(md.list_dn + d0 + m) : (uint32_t)(d0 + m)) : 0u;
-    for (int64_t u = tid; u < dim_up; u += kUpThreads) {
+    for (int64_t u = tid; u < dim_up; u += NT) {
       const uint32_t up = md.sector ? __ldg(md.list_up + u) : (uint32_t)u;
       const int deg = md.deg_up[u];
       const uint32_t* nb = md.nbr_up + u;
@@ -470,7 +525,7 @@ __global__ void __launch_bounds__(kUpThreads) k_hub_up_q(const HubDev md, const 
     __syncthreads();
     if (tid < nq) {
       double x = 0.0;
-      for (int k = 0; k < kUpThreads / 32; ++k) x += s_red[k * kMaxRedQ + tid];
+      for (int k = 0; k < NT / 32; ++k) x += s_red[k * kMaxRedQ + tid];
       fa.partials[(size_t)blockIdx.x * kMaxRedQ + tid] = x;
     }
   }
@@ -494,59 +549,61 @@ int pick_kq(const HubDev& md) {
 
 // pass D launch with the tuned (or default) columns per thread
 template <class R>
-Status launch_dn(const HubDev& md, const R* X, R* W, const int* done, cudaStream_t st) {
+Status launch_dn(const HubDev& md, const R* X, R* W, const int* done, unsigned long long* counter, cudaStream_t st) {
   int ept = md.dn_ept > 0 ? md.dn_ept : (sizeof(R) == 8 ? HPHI_DN_EPT64 : HPHI_DN_EPT32);
   if (ept != 1 && ept != 2 && ept != 4) ept = 1;
   const int64_t sw = (int64_t)kThreads * ept;
   const int64_t items = ((md.dim_up + sw - 1) / sw) * md.dim_dn;
   const int gd = (int)std::min<int64_t>(items, (int64_t)num_sms() * 8);
-  if (ept == 4) k_hub_dn<R, 4><<<gd, kThreads, 0, st>>>(md, X, W, done);
-  else if (ept == 2) k_hub_dn<R, 2><<<gd, kThreads, 0, st>>>(md, X, W, done);
-  else k_hub_dn<R, 1><<<gd, kThreads, 0, st>>>(md, X, W, done);
+  HPHI_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+  if (ept == 4) k_hub_dn<R, 4><<<gd, kThreads, 0, st>>>(md, X, W, done, counter);
+  else if (ept == 2) k_hub_dn<R, 2><<<gd, kThreads, 0, st>>>(md, X, W, done, counter);
+  else k_hub_dn<R, 1><<<gd, kThreads, 0, st>>>(md, X, W, done, counter);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
 
-template <class R, int K, Epi E>
-int up_occupancy() {
-  static int b = 0;
-  if (b == 0) {
-    // the dynamic tile size varies per model; occupancy is computed for the budget
-    int n = 0;
-    cudaFuncSetAttribute(k_hub_up<R, K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hub_up<R, K, E>, kUpThreads, kSmemBudget) != cudaSuccess ||
-        n < 1) {
-      cudaGetLastError();
-      n = 1;
-    }
-    b = n;
+// pass U threads: 1024 (one CTA per SM) for tiles above ~110 KB, else 512 so two CTAs per
+// SM alternate between loading a tile and working on one
+inline int up_threads(size_t tile_bytes) { return tile_bytes > 110000 ? 1024 : 512; }
+
+template <class KernelT>
+int occupancy_for(KernelT kern, int nt, size_t smem) {
+  int n = 0;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, nt, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
   }
-  return b;
+  return n;
+}
+
+template <class R, int K, Epi E>
+int up_occupancy(const HubDev& md) {
+  const size_t smem = (size_t)K * md.dim_up * sizeof(R);
+  return up_threads(smem) == 1024 ? occupancy_for(k_hub_up<R, K, E, 1024>, 1024, smem)
+                                  : occupancy_for(k_hub_up<R, K, E, 512>, 512, smem);
 }
 
 template <class R, int K, Epi E>
 Status launch_up(const HubDev& md, const R* X, const R* W, R* w, const FusedArgs& fa, int grid, cudaStream_t st) {
   const size_t smem = (size_t)K * md.dim_up * sizeof(R);
-  HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up<R, K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
-  k_hub_up<R, K, E><<<grid, kUpThreads, smem, st>>>(md, X, W, w, fa);
+  if (up_threads(smem) == 1024) {
+    HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up<R, K, E, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    k_hub_up<R, K, E, 1024><<<grid, 1024, smem, st>>>(md, X, W, w, fa);
+  } else {
+    HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up<R, K, E, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
+    k_hub_up<R, K, E, 512><<<grid, 512, smem, st>>>(md, X, W, w, fa);
+  }
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
 
 template <int K, Epi E>
-int upq_occupancy() {
-  static int b = 0;
-  if (b == 0) {
-    int n = 0;
-    cudaFuncSetAttribute(k_hub_up_q<K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hub_up_q<K, E>, kUpThreads, kSmemBudget) != cudaSuccess ||
-        n < 1) {
-      cudaGetLastError();
-      n = 1;
-    }
-    b = n;
-  }
-  return b;
+int upq_occupancy(const HubDev& md) {
+  const size_t smem = (size_t)K * md.dim_up * 8;
+  return up_threads(smem) == 1024 ? occupancy_for(k_hub_up_q<K, E, 1024>, 1024, smem)
+                                  : occupancy_for(k_hub_up_q<K, E, 512>, 512, smem);
 }
 
 // scratch layout of the quantised fp64 path: [Q: dim int64][WQ: dim int64][E: int]
@@ -559,24 +616,28 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
   long long* Q = reinterpret_cast<long long*>(scratch);
   long long* WQ = Q + md.dim;
   int* Ep = reinterpret_cast<int*>(WQ + md.dim);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(WQ + md.dim) + 1;
   const int gv = (int)std::max<int64_t>(1, std::min<int64_t>((md.dim + kThreads - 1) / kThreads, (int64_t)num_sms() * 8));
   HPHI_CUDA_TRY(cudaMemsetAsync(Ep, 0, sizeof(int), st));
   k_maxexp<<<gv, kThreads, 0, st>>>(X, md.dim, Ep, fa.done);
   HPHI_CUDA_TRY(cudaGetLastError());
   k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done);
   HPHI_CUDA_TRY(cudaGetLastError());
-  Status sd = launch_dn<long long>(md, Q, WQ, fa.done, st);
+  Status sd = launch_dn<long long>(md, Q, WQ, fa.done, counter, st);
   if (sd.code) return sd;
   double* out = reinterpret_cast<double*>(w);
   const int K = pick_kq(md);
   const size_t smem = (size_t)K * md.dim_up * 8;
+  const bool big = up_threads(smem) == 1024;
+#define HPHI_UPQ(KK, NN)                                                                                          \
+  HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up_q<KK, E, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget)); \
+  k_hub_up_q<KK, E, NN><<<grid_up, NN, smem, st>>>(md, X, Q, WQ, Ep, out, fa);
   if (K == 2) {
-    HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up_q<2, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
-    k_hub_up_q<2, E><<<grid_up, kUpThreads, smem, st>>>(md, X, Q, WQ, Ep, out, fa);
+    if (big) { HPHI_UPQ(2, 1024) } else { HPHI_UPQ(2, 512) }
   } else {
-    HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up_q<1, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget));
-    k_hub_up_q<1, E><<<grid_up, kUpThreads, smem, st>>>(md, X, Q, WQ, Ep, out, fa);
+    if (big) { HPHI_UPQ(1, 1024) } else { HPHI_UPQ(1, 512) }
   }
+#undef HPHI_UPQ
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
@@ -586,10 +647,10 @@ int upq_grid(const HubDev& md, Epi epi) {
   int occ = 1;
 #define HPHI_OCCQ(KK)                                                          \
   switch (epi) {                                                               \
-    case Epi::kStore: occ = upq_occupancy<KK, Epi::kStore>(); break;           \
-    case Epi::kLanczos1: occ = upq_occupancy<KK, Epi::kLanczos1>(); break;     \
-    case Epi::kTpq: occ = upq_occupancy<KK, Epi::kTpq>(); break;               \
-    case Epi::kRefine: occ = upq_occupancy<KK, Epi::kRefine>(); break;         \
+    case Epi::kStore: occ = upq_occupancy<KK, Epi::kStore>(md); break;         \
+    case Epi::kLanczos1: occ = upq_occupancy<KK, Epi::kLanczos1>(md); break;   \
+    case Epi::kTpq: occ = upq_occupancy<KK, Epi::kTpq>(md); break;             \
+    case Epi::kRefine: occ = upq_occupancy<KK, Epi::kRefine>(md); break;       \
   }
   if (K == 2) { HPHI_OCCQ(2) } else { HPHI_OCCQ(1) }
 #undef HPHI_OCCQ
@@ -604,7 +665,11 @@ Status launch_r(const HubDev& md, const void* v, void* w, void* scratch, const F
   // kStore writes the down-spin sums into w and finishes them in place; the fused steps
   // use the scratch vector
   R* W = (E == Epi::kStore) ? reinterpret_cast<R*>(w) : reinterpret_cast<R*>(scratch);
-  Status sd = launch_dn<R>(md, X, W, fa.done, st);
+  // the item counter of pass D sits after the fp32 scratch vector (first bytes of scratch
+  // when the scratch holds no vector)
+  const size_t voff = (E == Epi::kStore) ? 0 : (((size_t)md.dim * sizeof(R) + 255) / 256) * 256;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + voff);
+  Status sd = launch_dn<R>(md, X, W, fa.done, counter, st);
   if (sd.code) return sd;
   R* out = reinterpret_cast<R*>(w);
   switch (pick_k<R>(md)) {
@@ -620,10 +685,10 @@ int up_grid_r(const HubDev& md, Epi epi) {
   const int k = pick_k<R>(md);
 #define HPHI_OCC(KK)                                                         \
   switch (epi) {                                                             \
-    case Epi::kStore: occ = up_occupancy<R, KK, Epi::kStore>(); break;       \
-    case Epi::kLanczos1: occ = up_occupancy<R, KK, Epi::kLanczos1>(); break; \
-    case Epi::kTpq: occ = up_occupancy<R, KK, Epi::kTpq>(); break;           \
-    case Epi::kRefine: occ = up_occupancy<R, KK, Epi::kRefine>(); break;     \
+    case Epi::kStore: occ = up_occupancy<R, KK, Epi::kStore>(md); break;       \
+    case Epi::kLanczos1: occ = up_occupancy<R, KK, Epi::kLanczos1>(md); break; \
+    case Epi::kTpq: occ = up_occupancy<R, KK, Epi::kTpq>(md); break;           \
+    case Epi::kRefine: occ = up_occupancy<R, KK, Epi::kRefine>(md); break;     \
   }
   if (k == 4) { HPHI_OCC(4) } else if (k == 2) { HPHI_OCC(2) } else { HPHI_OCC(1) }
 #undef HPHI_OCC
@@ -674,10 +739,11 @@ Status launch_hub_store_noalloc(const HubDev& md0, const void* v, void* w, cudaS
   return launch_q<Epi::kStore>(md, v, w, scratch, fa, upq_grid(md, Epi::kStore), st);
 }
 
-Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, cudaStream_t st) {
+Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, uint8_t* npos,
+                            cudaStream_t st) {
   const int64_t n = species ? md.dim_dn : md.dim_up;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)num_sms() * 8));
-  k_hub_nbr<<<g, kThreads, 0, st>>>(md, species, nbr, deg);
+  k_hub_nbr<<<g, kThreads, 0, st>>>(md, species, nbr, deg, npos);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
@@ -707,7 +773,7 @@ int hub_up_grid(const HubDev& md0, int prec, Epi epi) {
 
 size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi) {
   if (prec == HPHI_FP64) return quant_scratch_bytes(md);
-  return epi == Epi::kStore ? 0 : (size_t)4 * md.dim;
+  return (epi == Epi::kStore ? 0 : (((size_t)4 * md.dim + 255) / 256) * 256) + 256;
 }
 
 Status launch_hub_fast(const HubDev& md0, int prec, const void* v, void* w, void* scratch, Epi epi,
