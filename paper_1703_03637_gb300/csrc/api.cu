@@ -114,7 +114,7 @@ struct hphi_model {
   int device = 0;
   // device data
   DBuf d_entries, d_cls, d_lin, d_pairs, d_pcoef, d_hi_off, d_lo_rank, d_lo_list, d_lo_off;
-  DBuf d_nbr_up, d_deg_up, d_nbr_dn, d_deg_dn, d_npos_up, d_npos_dn;
+  DBuf d_nbr_up, d_deg_up, d_nbr_dn, d_deg_dn, d_npos_up, d_npos_dn, d_counter;
   hphi::SpinDev sdev{};
   hphi::HubDev hdev{};
   Workspace ws;
@@ -483,6 +483,7 @@ hphi::Status build_hub_fast(hphi_model* m, cudaStream_t st) {
 hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
   HPHI_CUDA_TRY(cudaGetDevice(&m->device));
   hphi::Status s;
+  if ((s = m->d_counter.ensure(256)).code) return s;
   const int N = m->n_sites;
   if (m->kind == HPHI_SPIN_HALF) {
     if ((s = compile_spin(m, st)).code) return s;
@@ -505,6 +506,7 @@ hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
       d.t.lo_list_off = m->d_lo_off.as<uint32_t>();
       d.dim = (int64_t)binom_host(N, m->a);
     }
+    d.counter = m->d_counter.as<unsigned long long>();
     m->dim = d.dim;
   } else {
     if ((s = compile_hub(m, st)).code) return s;
@@ -527,6 +529,7 @@ hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
       d.list_dn = m->d_lo_list.as<uint32_t>() + off[m->b];
     }
     d.dim = d.dim_up * d.dim_dn;
+    d.counter = m->d_counter.as<unsigned long long>();
     m->dim = d.dim;
     if ((s = build_hub_fast(m, st)).code) return s;
   }

@@ -77,6 +77,7 @@ struct SpinDev {
   const PairEntry* pairs;
   const double* pair_coef;   // [n_pair_groups]
   SectorTables t;
+  unsigned long long* counter;  // work-item counter of the H v kernels (reset before each launch)
 };
 
 struct HubDev {
@@ -97,6 +98,7 @@ struct HubDev {
   const uint32_t* rank;      // [2^N]
   const uint32_t* list_up;   // [dim_up]
   const uint32_t* list_dn;   // [dim_dn]
+  unsigned long long* counter;  // work-item counter of the generic kernel
   // two-pass path (real model, one hopping value per species): neighbour tables
   // nbr[k * maxdeg + q] = rank of the q-th hop target of species state k | sign << 31
   int fast;

@@ -63,11 +63,26 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
   Red<F64> red;
   red.zero();
   const int64_t total = md.dim * (int64_t)nvec;
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  __shared__ int64_t s_item;
   const uint64_t hmax = md.sector ? ((1ull << md.t.H) - 1ull) : 0ull;
   const int n_ent = md.n_entries;
 
-  for (int64_t base = (int64_t)blockIdx.x * kThreads; base < total; base += stride) {
+  // plain H v: chunks of kThreads elements are handed out in order from a counter, so
+  // resident CTAs stay on neighbouring rows and share the rows they gather through L2.
+  // Fused steps keep the static assignment (chunk = CTA + k * grid): each CTA's partial sums
+  // then cover the same elements in the same order every run (bit-reproducible reductions).
+  constexpr bool kDyn = (E == Epi::kStore);
+  int64_t next = blockIdx.x;
+  for (;;) {
+    if constexpr (kDyn) {
+      __syncthreads();
+      if (tid == 0) s_item = (int64_t)atomicAdd(md.counter, 1ull);
+      __syncthreads();
+      next = s_item;
+    }
+    const int64_t base = next * kThreads;
+    if constexpr (!kDyn) next += gridDim.x;
+    if (base >= total) break;
     const int64_t idx = base + tid;
     const bool act = idx < total;
     int64_t r;
@@ -227,7 +242,19 @@ __global__ void __launch_bounds__(kThreads) k_hv_hub(const HubDev md, const S* _
   const int64_t nchunk = (row_elems + kThreads - 1) / kThreads;
   const int64_t n_items = nchunk * md.dim_dn;
 
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+  __shared__ int64_t s_item;
+  constexpr bool kDyn = (E == Epi::kStore);  // see k_hv_spin: fused steps stay static
+  int64_t next = blockIdx.x;
+  for (;;) {
+    if constexpr (kDyn) {
+      __syncthreads();
+      if (tid == 0) s_item = (int64_t)atomicAdd(md.counter, 1ull);
+      __syncthreads();
+      next = s_item;
+    }
+    const int64_t item = next;
+    if constexpr (!kDyn) next += gridDim.x;
+    if (item >= n_items) break;
     const int64_t d = item / nchunk;
     const int64_t e = (item - d * nchunk) * kThreads + tid;
     const uint32_t dn = md.sector ? __ldg(md.list_dn + d) : (uint32_t)d;
@@ -434,6 +461,9 @@ Status launch_t(bool hub, const void* md, const void* v, void* w, int nvec, cons
     lg = 0;
     while ((1 << lg) < nvec) ++lg;
   }
+  unsigned long long* counter = hub ? reinterpret_cast<const HubDev*>(md)->counter
+                                   : reinterpret_cast<const SpinDev*>(md)->counter;
+  HPHI_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   if (hub) {
     k_hv_hub<S, E><<<grid, kThreads, 0, st>>>(*reinterpret_cast<const HubDev*>(md), reinterpret_cast<const S*>(v),
                                              reinterpret_cast<S*>(w), nvec, lg, fa);
