@@ -274,6 +274,11 @@ hphi::Status compile_spin(hphi_model* m, cudaStream_t st) {
   if ((int)ct.coefs.size() > hphi::kMaxClasses) return {HPHI_ERR_UNSUPPORTED, "too many distinct coupling values"};
   if ((int)ents.size() > hphi::kMaxSpinEntries) return {HPHI_ERR_UNSUPPORTED, "too many off-diagonal terms"};
   std::stable_sort(ents.begin(), ents.end(), [](const hphi::SpinEntry& x, const hphi::SpinEntry& y) { return x.cls < y.cls; });
+  int max_run = 0;
+  for (size_t k = 0, run = 0; k < ents.size(); ++k) {
+    run = (k > 0 && ents[k].cls == ents[k - 1].cls) ? run + 1 : 1;
+    max_run = std::max(max_run, (int)run);
+  }
   std::vector<double2> cls;
   for (const cplx& c : ct.coefs) cls.push_back(make_double2(c.real(), c.imag()));
   // linear groups by value
@@ -312,6 +317,7 @@ hphi::Status compile_spin(hphi_model* m, cudaStream_t st) {
   d.n_sites = N;
   d.sector = sector ? 1 : 0;
   d.n_entries = (int)ents.size();
+  d.max_run = max_run;
   d.n_classes = (int)cls.size();
   d.n_lin = (int)lg.size();
   d.n_pairs = (int)pe.size();
@@ -559,8 +565,18 @@ bool use_hub_fast(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
   return m->kind == HPHI_HUBBARD && hphi::hub_fast_ok(m->hdev, prec, m->cplx_model, nvec, epi);
 }
 
+bool use_batch(hphi_model* m, int nvec) { return m->kind == HPHI_SPIN_HALF && hphi::batch_applies(m->sdev, nvec); }
+
+// scratch an H v launch needs beyond its vectors (0: none)
+size_t hv_scratch_bytes(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
+  if (use_hub_fast(m, prec, nvec, epi)) return hphi::hub_scratch_bytes(m->hdev, prec, epi);
+  if (use_batch(m, nvec)) return hphi::batch_scratch_bytes(m->sdev, prec, m->cplx_model, nvec);
+  return 0;
+}
+
 int hv_grid_for(hphi_model* m, int nvec, int prec, hphi::Epi epi) {
   if (use_hub_fast(m, prec, nvec, epi)) return hphi::hub_up_grid(m->hdev, prec, epi);
+  if (use_batch(m, nvec)) return hphi::batch_grid(prec, m->cplx_model, nvec, epi, m->dim);
   const bool hub = m->kind == HPHI_HUBBARD;
   const int64_t cap = hphi::hv_resident_grid(hub, prec, m->cplx_model, epi);
   int64_t work;
@@ -570,11 +586,16 @@ int hv_grid_for(hphi_model* m, int nvec, int prec, hphi::Epi epi) {
 }
 
 // One H v (or fused step) launch: the two-pass Hubbard kernels when they apply (they need
-// a scratch vector for the fused steps), else the generic gather kernel.
+// a scratch vector for the fused steps), the batched-row kernel for many aligned vectors of
+// a full-basis spin model (fp64 needs scratch), else the generic gather kernel.  Every
+// kernel loops over its rows with any grid, so the grid of hv_grid_for suits each of them.
 hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec, hphi::Epi epi,
                        const hphi::FusedArgs& fa, int grid, void* scratch, cudaStream_t st) {
   if (use_hub_fast(m, prec, nvec, epi) && (hphi::hub_scratch_bytes(m->hdev, prec, epi) == 0 || scratch != nullptr))
     return hphi::launch_hub_fast(m->hdev, prec, v, w, scratch, epi, fa, grid, st);
+  if (use_batch(m, nvec) && hphi::batch_aligned(v, w) &&
+      (scratch != nullptr || hphi::batch_scratch_bytes(m->sdev, prec, m->cplx_model, nvec) == 0))
+    return hphi::launch_batch(m->sdev, prec, m->cplx_model, v, w, scratch, nvec, epi, fa, grid, st);
   return hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec, epi, fa, grid, st);
 }
 
@@ -747,13 +768,11 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
   if (v == w) return fail(m, HPHI_ERR_INVALID_ARG, "apply_H: v and w must not overlap");
   hphi::FusedArgs fa;
   void* scratch = nullptr;
-  if (use_hub_fast(m, prec, nvec, hphi::Epi::kStore)) {
-    const size_t need = hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kStore);
-    if (need) {
-      hphi::Status a = m->ws.work.ensure(need);
-      if (a.code) return fail(m, a);
-      scratch = m->ws.work.p;
-    }
+  const size_t need = hv_scratch_bytes(m, prec, nvec, hphi::Epi::kStore);
+  if (need) {
+    hphi::Status a = m->ws.work.ensure(need);
+    if (a.code) return fail(m, a);
+    scratch = m->ws.work.p;
   }
   hphi::Status s = hv_launch(m, prec, v, w, nvec, hphi::Epi::kStore, fa, hv_grid_for(m, nvec, prec, hphi::Epi::kStore),
                              scratch, (cudaStream_t)stream);
@@ -1245,9 +1264,9 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   if ((s = ws.vecA.ensure(vbytes)).code) return s;
   if ((s = ws.vecB.ensure(vbytes)).code) return s;
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * nvec * hphi::kMaxRedQ)).code) return s;
-  const bool tfast = use_hub_fast(m, prec, nvec, hphi::Epi::kTpq);
-  if (tfast && (s = ws.work.ensure(hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kTpq))).code) return s;
-  void* tscratch = tfast ? ws.work.p : nullptr;
+  const size_t tneed = hv_scratch_bytes(m, prec, nvec, hphi::Epi::kTpq);
+  if (tneed && (s = ws.work.ensure(tneed)).code) return s;
+  void* tscratch = tneed ? ws.work.p : nullptr;
   const size_t nsc = 2 * (size_t)nvec + 3 * (size_t)K * nvec;
   if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;
   hphi::TpqDev tq;

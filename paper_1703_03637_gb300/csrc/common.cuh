@@ -78,6 +78,7 @@ struct SpinDev {
   const double* pair_coef;   // [n_pair_groups]
   SectorTables t;
   unsigned long long* counter;  // work-item counter of the H v kernels (reset before each launch)
+  int max_run;                  // longest run of entries of one class
 };
 
 struct HubDev {
@@ -193,6 +194,15 @@ Status launch_hub_fast(const HubDev& md, int prec, const void* v, void* w, void*
                        const FusedArgs& fa, int grid_up, cudaStream_t st);
 // resident CTAs of the chosen kernel instance over the whole GPU (occupancy API)
 int hv_resident_grid(bool hubbard, int prec, bool cplx, Epi epi);
+
+// Batched-row H v (k_batch.cu): full-basis spin models on <= 32 sites, nvec in {32, 64,
+// 128, 256}, vectors 32-byte aligned.  fp64 needs batch_scratch_bytes() of scratch.
+bool batch_applies(const SpinDev& md, int nvec);
+bool batch_aligned(const void* v, const void* w);
+size_t batch_scratch_bytes(const SpinDev& md, int prec, bool cplx, int nvec);
+int batch_grid(int prec, bool cplx, int nvec, Epi epi, int64_t dim);
+Status launch_batch(const SpinDev& md, int prec, bool cplx, const void* v, void* w, void* scratch, int nvec, Epi epi,
+                    const FusedArgs& fa, int grid, cudaStream_t st);
 
 // Streaming vector kernels and finalisers (k_solver.cu) -------------------------------
 struct LzDev {           // device scalars of one Lanczos run

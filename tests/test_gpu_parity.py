@@ -323,6 +323,76 @@ def test_tpq_64_starts_layout():
     assert np.all(np.abs(res["u"][0]) < 0.2)  # infinite-temperature energy ~ Tr H / D = 0
 
 
+# ----------------------------------------------------------------------------- batched rows
+BATCH_MODELS = [
+    ("kitaev_3x2", lambda: wl.kitaev_honeycomb(3, 2)),
+    ("random_spin_9", lambda: wl.random_spin_model(9, 14, seed=2)),
+    ("heisenberg_ring12", lambda: wl.heisenberg_ring(12)),
+]
+
+
+@pytest.mark.parametrize("name,mk", BATCH_MODELS, ids=[c[0] for c in BATCH_MODELS])
+@pytest.mark.parametrize("nvec", [32, 64, 128, 256])
+def test_batched_rows_apply_H(name, mk, nvec):
+    """Many vectors per row (the batched-row kernel: several lanes per row, several columns
+    per lane; fp64 through the quantised gathers) against the oracle."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    v = wl.gaussian_vector(71 + nvec, m.dim, nvec, complex_=m.is_complex)
+    ref = oracle.apply_H(spec, v)
+    ref = ref if m.is_complex else ref.real
+    for prec, tol in ((hp.FP64, 1e-12), (hp.FP32, 2e-5)):
+        w = m.apply_H(_to_dev(m, v, prec)).cpu().numpy()
+        assert _rel(w, ref) < tol
+
+
+def test_batched_rows_unaligned_falls_back():
+    """Vectors that do not start on a 32-byte boundary take the generic kernel: same result."""
+    spec = wl.kitaev_honeycomb(3, 2)
+    m = hp.Model.from_spec(spec)
+    nv = 32
+    v = wl.gaussian_vector(77, m.dim, nv, complex_=True)
+    ref = oracle.apply_H(spec, v)
+    for prec, tol in ((hp.FP64, 1e-12), (hp.FP32, 2e-5)):
+        dt = m.dtype(prec)
+        buf_v = torch.empty(m.dim * nv + 1, dtype=dt, device="cuda")
+        buf_w = torch.empty(m.dim * nv + 1, dtype=dt, device="cuda")
+        vv = buf_v[1:].view(m.dim, nv)
+        vv.copy_(torch.as_tensor(v).to(dt))
+        ww = buf_w[1:].view(m.dim, nv)
+        assert vv.data_ptr() % 32 != 0
+        m.apply_H(vv, ww)
+        assert _rel(ww.cpu().numpy(), ref) < tol
+
+
+def test_batched_rows_long_class_run():
+    """All-to-all Heisenberg on 17 sites: 136 exchange terms share one coefficient, more than
+    the 127 terms an exact 64-bit integer class sum allows, so fp64 keeps per-term
+    fixed-point sums; both precisions still match the oracle."""
+    n = 17
+    spec = wl.heisenberg(n, [(i, j) for i in range(n) for j in range(i + 1, n)], 0.7, name="heisenberg_all_17")
+    m = hp.Model.from_spec(spec)
+    v = wl.gaussian_vector(75, m.dim, 32)
+    ref = oracle.apply_H(spec, v).real
+    for prec, tol in ((hp.FP64, 1e-12), (hp.FP32, 2e-5)):
+        w = m.apply_H(_to_dev(m, v, prec)).cpu().numpy()
+        assert _rel(w, ref) < tol
+
+
+@pytest.mark.parametrize("nv", [32, 128])
+def test_batched_rows_tpq(nv):
+    """mTPQ over 32 / 128 starts through the batched-row kernel against the oracle."""
+    spec = wl.kitaev_honeycomb(3, 2)
+    m = hp.Model.from_spec(spec)
+    psi0 = wl.gaussian_vector(93, m.dim, nv, complex_=True)
+    for prec, tol in ((hp.FP64, 1e-11), (hp.FP32, 2e-5)):
+        res = m.tpq(nv, 10, l=1.0, psi0=torch.as_tensor(psi0), prec=prec)
+        for c in (0, 13, nv - 1):
+            u, h2, nrm = oracle.tpq(spec, psi0[:, c], 10, 1.0)
+            assert _rel(res["u"][:, c], u) < tol and _rel(res["norm"][:, c], nrm) < tol
+            assert _rel(res["h2"][:, c], h2) < tol
+
+
 # ----------------------------------------------------------------------------- sector batches
 def test_lanczos_sectors_match_oracle_and_single_runs():
     n = 12
