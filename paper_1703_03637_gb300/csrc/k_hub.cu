@@ -398,10 +398,10 @@ __global__ void __launch_bounds__(kThreads) k_quant(const double* __restrict__ X
   }
 }
 
-// pass U on quantised rows: K int64 rows interleaved in shared memory; the fp64 value of
-// each element (for the diagonal and the reductions) is read from X itself
+// pass U on quantised rows: K int64 rows interleaved in shared memory; the diagonal term and
+// the reductions take each element's value from the same quantised tile
 template <int K, Epi E, int NT>
-__global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md, const double* __restrict__ X,
+__global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
                                                          const long long* __restrict__ Q,
                                                          const long long* __restrict__ WQ, const int* __restrict__ Ep,
                                                          double* __restrict__ w, FusedArgs fa) {
@@ -430,6 +430,13 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md, const double* 
   }
   const int eoff = *Ep - 1078;
   const bool same_c = md.c_up == md.c_dn;
+  // one hopping value of magnitude 2^k (t = 1 in particular): c * fix(a) = fix(+-a) 2^k,
+  // an exponent shift instead of an fp64 multiply per element
+  const long long cbits = __double_as_longlong(md.c_up);
+  const int cexp = (int)((cbits >> 52) & 0x7ff);
+  const bool c_p2 = same_c && (cbits & 0xfffffffffffffll) == 0 && cexp > 0 && cexp < 0x7ff;
+  const bool c_neg = cbits < 0;
+  const int c_l2 = cexp - 1023;
   // diagonal = c0 + U * popcount(up & dn & mask) in the common single-group case: table
   __shared__ double s_dtab[33];
   const bool dtab = md.n_ulin == 1 && md.n_mulin == 0 && md.n_pairs == 0;
@@ -477,7 +484,9 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md, const double* 
       for (int m = 0; m < K; ++m) {
         if (m >= nk) break;
         const int64_t idx = (d0 + m) * dim_up + u;
-        const double x = __ldg(X + idx);
+        // the row's own value from the quantised tile: H v is then H applied to the
+        // quantised vector (each element within 2^-57 max|x| of v, as in the gathers)
+        const double x = fix_to_double(tile[u * K + m], eoff);
         double dg;
         if (dtab) {
           dg = s_dtab[__popc(up & dn[m] & (uint32_t)s_ulin[0].mask)];
@@ -506,7 +515,8 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md, const double* 
         }
         const long long wq = __ldg(WQ + idx);
         double hv;
-        if (same_c) hv = fma(dg, x, md.c_up * fix_to_double(acc[m] + wq, eoff));
+        if (c_p2) hv = fma(dg, x, fix_to_double(c_neg ? -(acc[m] + wq) : acc[m] + wq, eoff + c_l2));
+        else if (same_c) hv = fma(dg, x, md.c_up * fix_to_double(acc[m] + wq, eoff));
         else hv = fma(dg, x, fma(md.c_up, fix_to_double(acc[m], eoff), md.c_dn * fix_to_double(wq, eoff)));
         epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, w, fa, es, s_inv, red);
       }
@@ -631,7 +641,7 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
   const bool big = up_threads(smem) == 1024;
 #define HPHI_UPQ(KK, NN)                                                                                          \
   HPHI_CUDA_TRY(cudaFuncSetAttribute(k_hub_up_q<KK, E, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget)); \
-  k_hub_up_q<KK, E, NN><<<grid_up, NN, smem, st>>>(md, X, Q, WQ, Ep, out, fa);
+  k_hub_up_q<KK, E, NN><<<grid_up, NN, smem, st>>>(md, Q, WQ, Ep, out, fa);
   if (K == 2) {
     if (big) { HPHI_UPQ(2, 1024) } else { HPHI_UPQ(2, 512) }
   } else {
