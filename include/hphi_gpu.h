@@ -119,7 +119,10 @@ int hphi_basis_ranks(hphi_model* m, const uint64_t* states, int64_t n, int64_t* 
 
 /* w = H v for nvec interleaved vectors.  v, w: device buffers [dim][nvec] of the model's
  * scalar type in precision prec (HPHI_FP64 or HPHI_FP32); v and w must not overlap.
- * Matrix-free: every element is generated on the fly from the bit strings. */
+ * Matrix-free: every element is generated on the fly from the bit strings.  Scratch the
+ * kernels need lives in the model's workspace, allocated on first use and kept: the two-pass
+ * Hubbard path one vector, fp64 with nvec in {32, 64, 128, 256} on a full-basis spin model
+ * (when v and w start on 32-byte boundaries) one vector of 64-bit integers. */
 int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void* stream);
 
 /* Allocation-free w = H v.  The paper has no counterpart: this is a service for callers
@@ -158,6 +161,19 @@ typedef struct {
  * models report n_candidates = 0.  Uses the model's workspace; synchronises the stream.
  * *out may be NULL.  No counterpart in the paper (its CPU code has no launch shapes). */
 int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream);
+
+/* Window passes of the many-vector H v (full-basis spin models, nvec in {32, 64, 128, 256}):
+ * section 4.3's continuous-memory-access idea on one GPU.  Each pass takes the terms whose
+ * flipped sites lie in one cyclic window of `bits` sites and visits the rows with that
+ * window's bits varying fastest, so a pass's gathers hit a block of rows small enough to
+ * stay in L2 instead of reaching across the whole vector in HBM.  bits = -1 (the default)
+ * runs one pass, 0 sizes the window so that a block of input rows fills about a quarter of
+ * L2, 1..32 forces a window size (a window covering all sites means one pass).  At most 8
+ * passes; a plan that needs more falls back to one pass.  The passes cut HBM traffic about
+ * threefold on the 2^24-row Kitaev cluster but add instructions, and one pass is already
+ * bound by instruction issue there, hence the default.  The Lanczos step (one vector) is not
+ * affected.  Results agree with one pass up to floating-point summation order. */
+int hphi_set_window_bits(hphi_model* m, int bits);
 
 /* ---------------------------------------------------------------- start vectors */
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "hphi_add_hopping", "hphi_add_onsite_U", "hphi_add_density", "hphi_add_chemical_potential", "hphi_set_basis",
     "hphi_build_sector", "hphi_dim", "hphi_is_complex", "hphi_basis_states", "hphi_basis_ranks", "hphi_apply_H",
     "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run", "hphi_apply_H_noalloc",
-    "hphi_lanczos_run_sectors", "hphi_autotune",
+    "hphi_lanczos_run_sectors", "hphi_autotune", "hphi_set_window_bits",
 ]
 
 
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         L.hphi_lanczos_run.argtypes = [P, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         L.hphi_tpq_run.argtypes = [P, ctypes.POINTER(TpqParams), ctypes.POINTER(TpqResult), P]
         L.hphi_autotune.argtypes = [P, I, ctypes.POINTER(TuneResult), P]
+        L.hphi_set_window_bits.argtypes = [P, I]
         L.hphi_lanczos_run_sectors.argtypes = [P, P, I, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         _lib = L
         return L
@@ -258,6 +259,10 @@ class Model:
         self._check(self._L.hphi_autotune(self._h, prec, ctypes.byref(r), _stream()))
         return dict(n_candidates=r.n_candidates, dn_ept=r.best_dn_ept, up_k=r.best_up_k, best_ms=r.best_ms,
                     default_ms=r.default_ms, worst_ms=r.worst_ms)
+
+    def set_window_bits(self, bits: int):
+        """Window passes of the many-vector H v: 0 automatic, -1 off, else the window's sites."""
+        self._check(self._L.hphi_set_window_bits(self._h, int(bits)))
 
     def apply_H_noalloc(self, v, w):
         """w = H v through the allocation-free entry point (fp64, one vector, real Hubbard

@@ -121,6 +121,15 @@ struct hphi_model {
   // sector sub-models of hphi_lanczos_run_sectors, rebuilt when the terms change
   uint64_t gen = 0, sub_gen = ~0ull;
   std::map<int, std::unique_ptr<hphi_model>> sub;
+  // window passes of the batched-row kernel: the compiled entries, the size setting
+  // (-1 off, 0 sized from L2, else the window's sites) and the plans built so far by size
+  std::vector<hphi::SpinEntry> host_entries;
+  int win_bits_opt = -1;
+  struct WinCache {
+    DBuf ents, dep;
+    hphi::BatchPlan plan;
+  };
+  std::map<int, std::unique_ptr<WinCache>> win;
 };
 
 namespace {
@@ -318,6 +327,8 @@ hphi::Status compile_spin(hphi_model* m, cudaStream_t st) {
   d.sector = sector ? 1 : 0;
   d.n_entries = (int)ents.size();
   d.max_run = max_run;
+  m->host_entries = ents;
+  m->win.clear();
   d.n_classes = (int)cls.size();
   d.n_lin = (int)lg.size();
   d.n_pairs = (int)pe.size();
@@ -567,10 +578,54 @@ bool use_hub_fast(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
 
 bool use_batch(hphi_model* m, int nvec) { return m->kind == HPHI_SPIN_HALF && hphi::batch_applies(m->sdev, nvec); }
 
+// Window plan of the batched-row kernel for nvec vectors in precision prec, or null for one
+// pass in natural row order (windows off, one window holds every term, or no plan found).
+// Built on first use for each window size and kept until the terms change.
+const hphi::BatchPlan* batch_plan(hphi_model* m, int prec, int nvec) {
+  if (!use_batch(m, nvec) || m->win_bits_opt < 0) return nullptr;
+  const int wbits = m->win_bits_opt > 0 ? m->win_bits_opt : hphi::batch_window_bits(prec, m->cplx_model, nvec);
+  if (wbits >= m->n_sites) return nullptr;
+  auto it = m->win.find(wbits);
+  if (it == m->win.end()) {
+    std::unique_ptr<hphi_model::WinCache> wc(new (std::nothrow) hphi_model::WinCache());
+    std::vector<hphi::SpinEntry> ordered;
+    std::vector<uint32_t> dep;
+    int off[hphi::kMaxPasses + 1] = {};
+    int np = 0, max_run = 0;
+    if (!wc || !hphi::batch_plan_windows(m->n_sites, wbits, m->host_entries, &ordered, &dep, off, &np, &max_run) ||
+        upload(wc->ents, ordered, nullptr).code || upload(wc->dep, dep, nullptr).code ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+      cudaGetLastError();
+      wc.reset();
+    } else {
+      wc->plan.n_pass = np;
+      wc->plan.ents = wc->ents.as<hphi::SpinEntry>();
+      wc->plan.dep = wc->dep.as<uint32_t>();
+      for (int k = 0; k <= np; ++k) wc->plan.ent_off[k] = off[k];
+      wc->plan.max_run = max_run;
+    }
+    it = m->win.emplace(wbits, std::move(wc)).first;
+  }
+  return it->second ? &it->second->plan : nullptr;
+}
+
+// kernels one hv_launch runs (for the launch counts the results report)
+int hv_kernels(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
+  if (use_hub_fast(m, prec, nvec, epi)) return prec == HPHI_FP64 ? 4 : 2;  // (max-exponent, quantise,) D, U
+  if (use_batch(m, nvec)) {
+    const hphi::BatchPlan* plan = epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec);
+    const int passes = plan ? plan->n_pass : 1;
+    return passes + (hphi::batch_scratch_bytes(m->sdev, plan, prec, m->cplx_model, nvec) ? 2 : 0);
+  }
+  return 1;
+}
+
 // scratch an H v launch needs beyond its vectors (0: none)
 size_t hv_scratch_bytes(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
   if (use_hub_fast(m, prec, nvec, epi)) return hphi::hub_scratch_bytes(m->hdev, prec, epi);
-  if (use_batch(m, nvec)) return hphi::batch_scratch_bytes(m->sdev, prec, m->cplx_model, nvec);
+  if (use_batch(m, nvec))
+    return hphi::batch_scratch_bytes(m->sdev, epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec), prec,
+                                     m->cplx_model, nvec);
   return 0;
 }
 
@@ -593,9 +648,11 @@ hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec
                        const hphi::FusedArgs& fa, int grid, void* scratch, cudaStream_t st) {
   if (use_hub_fast(m, prec, nvec, epi) && (hphi::hub_scratch_bytes(m->hdev, prec, epi) == 0 || scratch != nullptr))
     return hphi::launch_hub_fast(m->hdev, prec, v, w, scratch, epi, fa, grid, st);
-  if (use_batch(m, nvec) && hphi::batch_aligned(v, w) &&
-      (scratch != nullptr || hphi::batch_scratch_bytes(m->sdev, prec, m->cplx_model, nvec) == 0))
-    return hphi::launch_batch(m->sdev, prec, m->cplx_model, v, w, scratch, nvec, epi, fa, grid, st);
+  if (use_batch(m, nvec) && hphi::batch_aligned(v, w)) {
+    const hphi::BatchPlan* plan = epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec);
+    if (scratch != nullptr || hphi::batch_scratch_bytes(m->sdev, plan, prec, m->cplx_model, nvec) == 0)
+      return hphi::launch_batch(m->sdev, plan, prec, m->cplx_model, v, w, scratch, nvec, epi, fa, grid, st);
+  }
   return hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec, epi, fa, grid, st);
 }
 
@@ -777,6 +834,13 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
   hphi::Status s = hv_launch(m, prec, v, w, nvec, hphi::Epi::kStore, fa, hv_grid_for(m, nvec, prec, hphi::Epi::kStore),
                              scratch, (cudaStream_t)stream);
   return s.code ? fail(m, s) : HPHI_OK;
+}
+
+int hphi_set_window_bits(hphi_model* m, int bits) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  if (bits < -1 || bits > 32) return fail(m, HPHI_ERR_INVALID_ARG, "window bits: -1, 0 or 1..32");
+  m->win_bits_opt = bits;
+  return HPHI_OK;
 }
 
 int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream) {
@@ -1020,7 +1084,7 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   };
   auto run_pass = [&](bool with_x) -> hphi::Status {
     hphi::Status q;
-    L.launches += 2 + 4 * steps;
+    L.launches += 2 + (3 + hv_kernels(m, prec, 1, hphi::Epi::kLanczos1)) * steps;
     if ((q = hphi::launch_lz_init(prec, cplx, L.v0, c0, p0, L.n_real, L.partials, L.vgrid, st)).code) return q;
     if ((q = hphi::launch_lz_init_fin(L.lz, L.partials, L.vgrid, st)).code) return q;
     if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)L.n_real, st));
@@ -1067,7 +1131,7 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
     if ((s = start()).code) return s;
     if ((s = run_pass(true)).code) return s;
   }
-  L.launches += 4;
+  L.launches += 3 + hv_kernels(m, HPHI_FP64, 1, hphi::Epi::kRefine);
   // fp64 H x into the (now free) buffer A, then E, variance and residual
   double* hx = ws.vecA.as<double>();
   hphi::FusedArgs fa;
@@ -1340,7 +1404,7 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   if (r->h2) memcpy(r->h2, host.data() + kn, sizeof(double) * kn);
   if (r->norm) memcpy(r->norm, host.data() + 2 * kn, sizeof(double) * kn);
   r->device_ms = ms;
-  r->kernel_launches = (p->psi0 ? 0 : 1) + 2 + 2 * K;
+  r->kernel_launches = (p->psi0 ? 0 : 1) + 2 + (1 + hv_kernels(m, prec, nvec, hphi::Epi::kTpq)) * K;
   return {};
 }
 

@@ -197,12 +197,29 @@ int hv_resident_grid(bool hubbard, int prec, bool cplx, Epi epi);
 
 // Batched-row H v (k_batch.cu): full-basis spin models on <= 32 sites, nvec in {32, 64,
 // 128, 256}, vectors 32-byte aligned.  fp64 needs batch_scratch_bytes() of scratch.
+// With a window plan the terms run in passes over bit windows (the rows of each pass are
+// visited with the window's bits varying fastest, so the pass's gathers stay in L2).
+constexpr int kMaxPasses = 8;
+struct BatchPlan {
+  int n_pass = 0;
+  const SpinEntry* ents = nullptr;  // entries pass by pass, class-sorted within a pass
+  const uint32_t* dep = nullptr;    // [n_pass][4][256]: byte b of the visit index -> row bits
+  int ent_off[kMaxPasses + 1] = {};
+  int max_run = 0;                  // longest class run within a pass
+};
+// Greedy cyclic windows of wbits sites covering every entry's flip mask; false when more
+// than kMaxPasses windows would be needed.
+bool batch_plan_windows(int n_sites, int wbits, const std::vector<SpinEntry>& ents,
+                        std::vector<SpinEntry>* ordered, std::vector<uint32_t>* dep, int* ent_off, int* n_pass,
+                        int* max_run);
+// window size whose block of rows (input rows only) fills about a quarter of L2
+int batch_window_bits(int prec, bool cplx, int nvec);
 bool batch_applies(const SpinDev& md, int nvec);
 bool batch_aligned(const void* v, const void* w);
-size_t batch_scratch_bytes(const SpinDev& md, int prec, bool cplx, int nvec);
+size_t batch_scratch_bytes(const SpinDev& md, const BatchPlan* plan, int prec, bool cplx, int nvec);
 int batch_grid(int prec, bool cplx, int nvec, Epi epi, int64_t dim);
-Status launch_batch(const SpinDev& md, int prec, bool cplx, const void* v, void* w, void* scratch, int nvec, Epi epi,
-                    const FusedArgs& fa, int grid, cudaStream_t st);
+Status launch_batch(const SpinDev& md, const BatchPlan* plan, int prec, bool cplx, const void* v, void* w,
+                    void* scratch, int nvec, Epi epi, const FusedArgs& fa, int grid, cudaStream_t st);
 
 // Streaming vector kernels and finalisers (k_solver.cu) -------------------------------
 struct LzDev {           // device scalars of one Lanczos run

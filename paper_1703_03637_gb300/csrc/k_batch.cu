@@ -3,8 +3,8 @@
 //
 // The vectors are stored [row][column], so the nvec entries a term gathers from row s ^ mask
 // are contiguous.  A row is handled by nvec / CPL lanes, lane l owning CPL consecutive
-// columns (32 bytes, two 16-byte loads per neighbour); a warp takes 32 / (nvec / CPL) rows at
-// once.  The per-term work (entry, phase code, neighbour row) is paid once per lane for CPL
+// columns (32 or 64 bytes: two or four 16-byte loads per neighbour); a warp takes
+// 32 / (nvec / CPL) rows at once.  The per-term work (entry, phase code, neighbour row) is paid once per lane for CPL
 // columns instead of once per column as in the generic kernel, and the loads are 16 bytes wide.
 //
 // fp64 runs the gathers on a copy of the input quantised to 64-bit integers with one scale
@@ -18,16 +18,25 @@
 #include "epilogue.cuh"
 #include "reduce.cuh"
 
-#ifndef HPHI_BATCH_MINB
-#define HPHI_BATCH_MINB 2  // resident CTAs per SM the register budget is cut for
-#endif
 
 namespace hphi {
 
 namespace {
 
-template <class S> struct BatchCpl {
-  static constexpr int kMin = (int)(32 / sizeof(S));  // columns per lane giving 32-byte loads
+// Launch shape per scalar type and epilogue, from a sweep on the 2^24-row, 64-vector Kitaev
+// workload: kRegs = 32-bit registers of gathered values in flight per thread, kMinB =
+// resident CTAs per SM the register budget is cut for, kLaneBytes = bytes of a row one lane
+// gathers per term (at least).  The plain fp32 product keeps the most loads in flight; the
+// fused steps and fp64 trade them for occupancy; fp64 lanes take 64 bytes (four columns).
+template <class S, Epi E> struct BatchTune {
+  static constexpr bool kF64 = Traits<S>::kF64;
+  static constexpr int kRegs = (!kF64 && E == Epi::kStore) ? 64 : 32;
+  static constexpr int kMinB = 2;
+  static constexpr int kLaneBytes = kF64 ? 64 : 32;
+};
+
+template <class S, Epi E> struct BatchCpl {
+  static constexpr int kMin = (int)(BatchTune<S, E>::kLaneBytes / sizeof(S));  // columns per lane
 };
 
 template <class T, int N> struct Regs {
@@ -35,7 +44,8 @@ template <class T, int N> struct Regs {
 };
 
 // CPL consecutive elements of type S as (re, im) scalars of type T; p is 32-byte aligned
-template <class S, int CPL, class T>
+// (kStream: evict-first, for the pass accumulator, which is read once per pass)
+template <class S, int CPL, bool kStream = false, class T>
 __device__ __forceinline__ void vload(const T* __restrict__ p, Regs<T, CPL>& o) {
   constexpr bool C = Traits<S>::kCplx;
   constexpr int nT = CPL * (C ? 2 : 1);
@@ -45,7 +55,8 @@ __device__ __forceinline__ void vload(const T* __restrict__ p, Regs<T, CPL>& o) 
     T t[nT];
   } b;
 #pragma unroll
-  for (int k = 0; k < n16; ++k) b.u[k] = __ldg(reinterpret_cast<const uint4*>(p) + k);
+  for (int k = 0; k < n16; ++k)
+    b.u[k] = kStream ? __ldcs(reinterpret_cast<const uint4*>(p) + k) : __ldg(reinterpret_cast<const uint4*>(p) + k);
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
     o.re[c] = C ? b.t[2 * c] : b.t[c];
@@ -53,7 +64,7 @@ __device__ __forceinline__ void vload(const T* __restrict__ p, Regs<T, CPL>& o) 
   }
 }
 
-template <class S, int CPL, class T>
+template <class S, int CPL, bool kStream = false, class T>
 __device__ __forceinline__ void vstore(T* __restrict__ p, const Regs<T, CPL>& o) {
   constexpr bool C = Traits<S>::kCplx;
   constexpr int nT = CPL * (C ? 2 : 1);
@@ -72,8 +83,20 @@ __device__ __forceinline__ void vstore(T* __restrict__ p, const Regs<T, CPL>& o)
     }
   }
 #pragma unroll
-  for (int k = 0; k < n16; ++k) reinterpret_cast<uint4*>(p)[k] = b.u[k];
+  for (int k = 0; k < n16; ++k) {
+    if (kStream) __stcs(reinterpret_cast<uint4*>(p) + k, b.u[k]);
+    else reinterpret_cast<uint4*>(p)[k] = b.u[k];
+  }
 }
+
+// one pass over the rows: its entries, its visit order and its place in the sequence
+struct PassArgs {
+  const SpinEntry* ents;  // entries [e0, e1) of this pass
+  int e0, e1;
+  const uint32_t* dep;    // [4][256] visit-index byte -> row bits; null: natural order
+  int first, last;        // the first pass adds the diagonal, the last runs the epilogue
+  void* acc;              // row-owned accumulator between passes (null for one pass)
+};
 
 // column exponents: E[c] = the largest exponent field over the rows (real and imaginary
 // parts) of column c; the [row][column] vector is read once, coalesced
@@ -120,22 +143,21 @@ __global__ void __launch_bounds__(kThreads) k_quant_cols(const double* __restric
   }
 }
 
-// phase codes 0 (none), 1 (+1), 2 (+i), 3 (-1), 4 (-i) as (re, im)
-__constant__ float c_phase_f[5][2] = {{0.f, 0.f}, {1.f, 0.f}, {0.f, 1.f}, {-1.f, 0.f}, {0.f, -1.f}};
-
 // QT (fp64 only): gathers read the quantised copy Q; class sums are exact int64 sums.
 // Without QT, fp64 class sums are exact fixed-point sums of the fp64 terms (class runs
 // longer than 127 terms) and fp32 sums are plain fp32.
 template <class S, Epi E, int CPL, bool QT>
-__global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
-    k_hv_batch(const SpinDev md, const S* __restrict__ v, S* __restrict__ w, int nvec, FusedArgs fa,
-               const long long* __restrict__ Q, const int* __restrict__ Ec) {
+__global__ void __launch_bounds__(kThreads, BatchTune<S, E>::kMinB)
+    k_hv_batch(const SpinDev md, const PassArgs pa, const S* __restrict__ v, S* __restrict__ w, int nvec,
+               FusedArgs fa, const long long* __restrict__ Q, const int* __restrict__ Ec) {
   using R = typename Traits<S>::R;
   constexpr bool C = Traits<S>::kCplx;
   constexpr bool F64 = Traits<S>::kF64;
   static_assert(!QT || F64, "quantised gathers are an fp64 path");
   constexpr int kWarps = kThreads / 32;
-  constexpr int kB = (CPL * (C ? 2 : 1) * (QT ? 8 : (int)sizeof(R)) <= 32) ? 8 : 4;  // terms in flight
+  // terms in flight: kBatchRegs 32-bit registers of gathered values
+  constexpr int kRegsPerTerm = CPL * (C ? 2 : 1) * (QT ? 2 : (int)sizeof(R) / 4);
+  constexpr int kB = BatchTune<S, E>::kRegs / kRegsPerTerm > 1 ? BatchTune<S, E>::kRegs / kRegsPerTerm : 1;
   using T = std::conditional_t<QT, long long, R>;  // gathered scalar
   using A = std::conditional_t<QT, IntAcc, typename SumAcc<R>::T>;
   __shared__ SpinEntry s_ent[kMaxSpinEntries];
@@ -145,11 +167,17 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
   __shared__ double s_pcoef[kMaxPairGroups];
   __shared__ double s_inv[kMaxNvec];
   __shared__ double s_red[(E == Epi::kStore) ? 1 : kThreads * CPL];
+  __shared__ uint32_t s_dep[4 * 256];
+  __shared__ float2 s_phase[8];  // phase codes 0 (none), 1 (+1), 2 (+i), 3 (-1), 4 (-i) as (re, im)
 
   if (fa.done != nullptr && *fa.done) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ne = md.n_entries;
-  for (int k = tid; k < ne; k += kThreads) s_ent[k] = md.entries[k];
+  const int ne = pa.e1 - pa.e0;
+  for (int k = tid; k < ne; k += kThreads) s_ent[k] = pa.ents[pa.e0 + k];
+  if (tid < 8) s_phase[tid] = make_float2(tid == 1 ? 1.f : tid == 3 ? -1.f : 0.f, tid == 2 ? 1.f : tid == 4 ? -1.f : 0.f);
+  const bool deposit = pa.dep != nullptr;
+  if (deposit)
+    for (int k = tid; k < 4 * 256; k += kThreads) s_dep[k] = pa.dep[k];
   for (int k = tid; k < md.n_classes; k += kThreads) {
     const double2 cc = md.cls_coef[k];
     s_cr[k] = (R)cc.x;
@@ -180,9 +208,18 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
 #pragma unroll
   for (int q = 0; q < CPL; ++q) eoff[q] = QT ? Ec[c0 + q] - 1078 : 0;
   const int64_t step = (int64_t)gridDim.x * kWarps * rpw;
+  const bool first = pa.first != 0, last = pa.last != 0;
+  S* acc = reinterpret_cast<S*>(pa.acc);
   for (int64_t row = ((int64_t)blockIdx.x * kWarps + warp) * rpw + slot; row < md.dim; row += step) {
-    const uint32_t s = (uint32_t)row;
-    const int64_t off = row * nvec + c0;
+    const uint32_t t = (uint32_t)row;  // visit index
+    const uint32_t s = deposit ? (s_dep[t & 255u] | s_dep[256 + ((t >> 8) & 255u)] |
+                                  s_dep[512 + ((t >> 16) & 255u)] | s_dep[768 + (t >> 24)])
+                               : t;
+    const int64_t off = (int64_t)s * nvec + c0;
+    Regs<R, CPL> h;
+    if (!first) {
+      vload<S, CPL, true>(reinterpret_cast<const R*>(acc + off), h);
+    } else {
     // diagonal
     R d = (R)md.c0;
     for (int g = 0; g < md.n_lin; ++g) d += (R)s_lin[g].coef * (R)__popc(s & (uint32_t)s_lin[g].mask);
@@ -199,7 +236,6 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
       }
       d += (R)s_pcoef[grp] * (R)cnt;
     }
-    Regs<R, CPL> h;
     {
       Regs<R, CPL> x0;
       vload<S, CPL>(reinterpret_cast<const R*>(v + off), x0);
@@ -208,6 +244,7 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
         h.re[q] = d * x0.re[q];
         h.im[q] = d * x0.im[q];
       }
+    }
     }
     A ar[CPL], ai[CPL];
 #pragma unroll
@@ -289,14 +326,14 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
               }
             }
           } else {
-            const R pr = c_phase_f[code[j]][0], pi = c_phase_f[code[j]][1];
+            const float2 ph = s_phase[code[j]];
 #pragma unroll
             for (int q = 0; q < CPL; ++q) {
               if constexpr (C) {
-                ar[q].s += pr * x[j].re[q] - pi * x[j].im[q];
-                ai[q].s += pr * x[j].im[q] + pi * x[j].re[q];
+                ar[q].s = fmaf(ph.x, x[j].re[q], fmaf(-ph.y, x[j].im[q], ar[q].s));
+                ai[q].s = fmaf(ph.x, x[j].im[q], fmaf(ph.y, x[j].re[q], ai[q].s));
               } else {
-                ar[q].s += pr * x[j].re[q];
+                ar[q].s = fmaf(ph.x, x[j].re[q], ar[q].s);
               }
             }
           }
@@ -304,7 +341,9 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
       }
     }
     if (ne) flush(cur);
-    if constexpr (E == Epi::kStore) {
+    if (!last) {
+      vstore<S, CPL, true>(reinterpret_cast<R*>(acc + off), h);
+    } else if constexpr (E == Epi::kStore) {
       vstore<S, CPL>(reinterpret_cast<R*>(w + off), h);
     } else {
       Regs<R, CPL> x0;  // read again (from L1 / L2) rather than held across the term loop
@@ -315,6 +354,7 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
     }
   }
   if constexpr (E != Epi::kStore) {
+    if (!last) return;  // the same for the whole grid
     // per-column sums, one quantity at a time; the (warp, row slot) pairs are summed in a
     // fixed order, so the result does not depend on timing
     constexpr int nq = n_red<E>();
@@ -333,11 +373,12 @@ __global__ void __launch_bounds__(kThreads, HPHI_BATCH_MINB)
   }
 }
 
-bool quantised(const SpinDev& md, int prec) { return prec == HPHI_FP64 && md.max_run <= 127; }
+int max_run_of(const SpinDev& md, const BatchPlan* plan) { return plan ? plan->max_run : md.max_run; }
+bool quantised(int max_run, int prec) { return prec == HPHI_FP64 && max_run <= 127; }
 
 template <class S, Epi E, int CPL, bool QT>
-Status launch_q(const SpinDev& md, const void* v, void* w, void* scratch, int nvec, const FusedArgs& fa, int grid,
-                cudaStream_t st) {
+Status launch_q(const SpinDev& md, const BatchPlan* plan, const void* v, void* w, void* scratch, int nvec,
+                const FusedArgs& fa, int grid, cudaStream_t st) {
   constexpr int ncomp = Traits<S>::kCplx ? 2 : 1;
   const long long* Q = nullptr;
   const int* Ec = nullptr;
@@ -360,55 +401,69 @@ Status launch_q(const SpinDev& md, const void* v, void* w, void* scratch, int nv
     Q = q;
     Ec = e;
   }
-  k_hv_batch<S, E, CPL, QT><<<grid, kThreads, 0, st>>>(md, reinterpret_cast<const S*>(v), reinterpret_cast<S*>(w), nvec,
-                                                       fa, Q, Ec);
-  HPHI_CUDA_TRY(cudaGetLastError());
+  const int np = plan ? plan->n_pass : 1;
+  for (int p = 0; p < np; ++p) {
+    PassArgs pa;
+    pa.ents = plan ? plan->ents : md.entries;
+    pa.e0 = plan ? plan->ent_off[p] : 0;
+    pa.e1 = plan ? plan->ent_off[p + 1] : md.n_entries;
+    pa.dep = plan ? plan->dep + (size_t)p * 1024 : nullptr;
+    pa.first = p == 0;
+    pa.last = p == np - 1;
+    // the accumulator is the buffer the last pass writes row by row: w, or the epilogue's
+    // output (the last pass reads a row's partial sum before it overwrites the row)
+    pa.acc = np > 1 ? (E == Epi::kStore ? w : fa.out) : nullptr;
+    k_hv_batch<S, E, CPL, QT><<<grid, kThreads, 0, st>>>(md, pa, reinterpret_cast<const S*>(v),
+                                                         reinterpret_cast<S*>(w), nvec, fa, Q, Ec);
+    HPHI_CUDA_TRY(cudaGetLastError());
+  }
   return {};
 }
 
-// columns per lane for nvec vectors: 32-byte loads, at most 32 lanes per row
-template <class S>
+// columns per lane for nvec vectors: the tuned load width, at most 32 lanes per row
+template <class S, Epi E>
 int cpl_for(int nvec) {
-  return std::max(BatchCpl<S>::kMin, nvec / 32);
+  return std::max(BatchCpl<S, E>::kMin, nvec / 32);
 }
 
 template <class S, Epi E, int CPL>
-Status launch_c(const SpinDev& md, int prec, const void* v, void* w, void* scratch, int nvec, const FusedArgs& fa,
-                int grid, cudaStream_t st) {
-  if constexpr (CPL < BatchCpl<S>::kMin) {
+Status launch_c(const SpinDev& md, const BatchPlan* plan, int prec, const void* v, void* w, void* scratch, int nvec,
+                const FusedArgs& fa, int grid, cudaStream_t st) {
+  if constexpr (CPL < BatchCpl<S, E>::kMin) {
     return {HPHI_ERR_INVALID_ARG, "batched rows: columns per lane below the load width"};
   } else {
     if constexpr (Traits<S>::kF64) {
-      if (quantised(md, prec)) return launch_q<S, E, CPL, true>(md, v, w, scratch, nvec, fa, grid, st);
+      if (quantised(max_run_of(md, plan), prec))
+        return launch_q<S, E, CPL, true>(md, plan, v, w, scratch, nvec, fa, grid, st);
     }
-    return launch_q<S, E, CPL, false>(md, v, w, scratch, nvec, fa, grid, st);
+    return launch_q<S, E, CPL, false>(md, plan, v, w, scratch, nvec, fa, grid, st);
   }
 }
 
 template <class S, Epi E>
-Status launch_t(const SpinDev& md, int prec, const void* v, void* w, void* scratch, int nvec, const FusedArgs& fa,
-                int grid, cudaStream_t st) {
-  switch (cpl_for<S>(nvec)) {
-    case 2: return launch_c<S, E, 2>(md, prec, v, w, scratch, nvec, fa, grid, st);
-    case 4: return launch_c<S, E, 4>(md, prec, v, w, scratch, nvec, fa, grid, st);
-    case 8: return launch_c<S, E, 8>(md, prec, v, w, scratch, nvec, fa, grid, st);
+Status launch_t(const SpinDev& md, const BatchPlan* plan, int prec, const void* v, void* w, void* scratch, int nvec,
+                const FusedArgs& fa, int grid, cudaStream_t st) {
+  switch (cpl_for<S, E>(nvec)) {
+    case 2: return launch_c<S, E, 2>(md, plan, prec, v, w, scratch, nvec, fa, grid, st);
+    case 4: return launch_c<S, E, 4>(md, plan, prec, v, w, scratch, nvec, fa, grid, st);
+    case 8: return launch_c<S, E, 8>(md, plan, prec, v, w, scratch, nvec, fa, grid, st);
     default: return {HPHI_ERR_INVALID_ARG, "batched rows: unsupported nvec"};
   }
 }
 
 template <Epi E>
-Status launch_e(const SpinDev& md, int prec, bool cplx, const void* v, void* w, void* scratch, int nvec,
-                const FusedArgs& fa, int grid, cudaStream_t st) {
+Status launch_e(const SpinDev& md, const BatchPlan* plan, int prec, bool cplx, const void* v, void* w, void* scratch,
+                int nvec, const FusedArgs& fa, int grid, cudaStream_t st) {
   if (prec == HPHI_FP64)
-    return cplx ? launch_t<double2, E>(md, prec, v, w, scratch, nvec, fa, grid, st)
-                : launch_t<double, E>(md, prec, v, w, scratch, nvec, fa, grid, st);
-  return cplx ? launch_t<float2, E>(md, prec, v, w, scratch, nvec, fa, grid, st)
-              : launch_t<float, E>(md, prec, v, w, scratch, nvec, fa, grid, st);
+    return cplx ? launch_t<double2, E>(md, plan, prec, v, w, scratch, nvec, fa, grid, st)
+                : launch_t<double, E>(md, plan, prec, v, w, scratch, nvec, fa, grid, st);
+  return cplx ? launch_t<float2, E>(md, plan, prec, v, w, scratch, nvec, fa, grid, st)
+              : launch_t<float, E>(md, plan, prec, v, w, scratch, nvec, fa, grid, st);
 }
 
 template <class S, Epi E, int CPL>
 int occupancy_c() {
-  if constexpr (CPL < BatchCpl<S>::kMin) {
+  if constexpr (CPL < BatchCpl<S, E>::kMin) {
     return 1;
   } else {
     int n = 0;
@@ -424,7 +479,7 @@ int occupancy_c() {
 template <class S, Epi E>
 int occupancy_t(int nvec) {
   static int cache[4] = {0, 0, 0, 0};  // by columns per lane 2, 4, 8
-  const int cpl = cpl_for<S>(nvec);
+  const int cpl = cpl_for<S, E>(nvec);
   int& b = cache[cpl == 2 ? 1 : cpl == 4 ? 2 : 3];
   if (b == 0) b = cpl == 2 ? occupancy_c<S, E, 2>() : cpl == 4 ? occupancy_c<S, E, 4>() : occupancy_c<S, E, 8>();
   return b;
@@ -438,14 +493,94 @@ int occupancy_e(int prec, bool cplx, int nvec) {
 
 }  // namespace
 
+int batch_window_bits(int prec, bool cplx, int nvec) {
+  const double row = (double)nvec * (prec == HPHI_FP64 ? 8 : 4) * (cplx ? 2 : 1);
+  int w = 0;
+  while ((double)(1ll << (w + 1)) * row <= 32.0 * 1024 * 1024) ++w;
+  return w;
+}
+
+bool batch_plan_windows(int n_sites, int wbits, const std::vector<SpinEntry>& ents,
+                        std::vector<SpinEntry>* ordered, std::vector<uint32_t>* dep, int* ent_off, int* n_pass,
+                        int* max_run) {
+  *n_pass = 0;
+  if (n_sites > 32 || wbits < 1 || wbits >= n_sites) return false;
+  auto window = [&](int a) {
+    uint64_t m = 0;
+    for (int b = 0; b < wbits; ++b) m |= 1ull << ((a + b) % n_sites);
+    return m;
+  };
+  // greedy: the cyclic window holding the most unassigned flip masks, until all are held
+  std::vector<int> pass_of(ents.size(), -1);
+  std::vector<uint64_t> chosen;
+  size_t left = ents.size();
+  while (left > 0) {
+    if ((int)chosen.size() >= kMaxPasses) return false;
+    int best_a = -1;
+    size_t best_n = 0;
+    for (int a = 0; a < n_sites; ++a) {
+      const uint64_t m = window(a);
+      size_t n = 0;
+      for (size_t k = 0; k < ents.size(); ++k)
+        if (pass_of[k] < 0 && (ents[k].mask & ~m) == 0) ++n;
+      if (n > best_n) {
+        best_n = n;
+        best_a = a;
+      }
+    }
+    if (best_a < 0) return false;  // a mask wider than the window
+    const uint64_t m = window(best_a);
+    for (size_t k = 0; k < ents.size(); ++k)
+      if (pass_of[k] < 0 && (ents[k].mask & ~m) == 0) {
+        pass_of[k] = (int)chosen.size();
+        --left;
+      }
+    chosen.push_back(m);
+  }
+  if (chosen.size() < 2) return false;  // one window holds every term: the plain order does
+  ordered->clear();
+  dep->assign(chosen.size() * 1024, 0u);
+  *max_run = 0;
+  for (size_t p = 0; p < chosen.size(); ++p) {
+    ent_off[p] = (int)ordered->size();
+    for (size_t k = 0; k < ents.size(); ++k)  // input is class-sorted; keep that order
+      if (pass_of[k] == (int)p) ordered->push_back(ents[k]);
+    // visit index bit t -> row bit pos[t]: the window's bits first (fastest), then the rest
+    int pos[32], n = 0;
+    for (int b = 0; b < n_sites; ++b)
+      if ((chosen[p] >> b) & 1ull) pos[n++] = b;
+    for (int b = 0; b < n_sites; ++b)
+      if (!((chosen[p] >> b) & 1ull)) pos[n++] = b;
+    for (int byte = 0; byte < 4; ++byte)
+      for (int val = 0; val < 256; ++val) {
+        uint32_t r = 0;
+        for (int t = 0; t < 8; ++t) {
+          const int src = byte * 8 + t;
+          if (((val >> t) & 1) && src < n_sites) r |= 1u << pos[src];
+        }
+        (*dep)[p * 1024 + byte * 256 + val] = r;
+      }
+  }
+  ent_off[chosen.size()] = (int)ordered->size();
+  for (size_t p = 0; p < chosen.size(); ++p) {
+    int run = 0;
+    for (int k = ent_off[p]; k < ent_off[p + 1]; ++k) {
+      run = (k > ent_off[p] && (*ordered)[k].cls == (*ordered)[k - 1].cls) ? run + 1 : 1;
+      *max_run = std::max(*max_run, run);
+    }
+  }
+  *n_pass = (int)chosen.size();
+  return true;
+}
+
 bool batch_applies(const SpinDev& md, int nvec) {
   return md.sector == 0 && md.n_sites <= 32 && (nvec == 32 || nvec == 64 || nvec == 128 || nvec == 256);
 }
 
 bool batch_aligned(const void* v, const void* w) { return (((uintptr_t)v | (uintptr_t)w) & 31u) == 0; }
 
-size_t batch_scratch_bytes(const SpinDev& md, int prec, bool cplx, int nvec) {
-  if (!quantised(md, prec)) return 0;
+size_t batch_scratch_bytes(const SpinDev& md, const BatchPlan* plan, int prec, bool cplx, int nvec) {
+  if (!quantised(max_run_of(md, plan), prec)) return 0;
   return (size_t)md.dim * nvec * 8 * (cplx ? 2 : 1) + sizeof(int) * (size_t)nvec;
 }
 
@@ -463,19 +598,22 @@ int batch_grid(int prec, bool cplx, int nvec, Epi epi, int64_t dim) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
 }
 
-Status launch_batch(const SpinDev& md, int prec, bool cplx, const void* v, void* w, void* scratch, int nvec, Epi epi,
-                    const FusedArgs& fa, int grid, cudaStream_t st) {
+Status launch_batch(const SpinDev& md, const BatchPlan* plan, int prec, bool cplx, const void* v, void* w,
+                    void* scratch, int nvec, Epi epi, const FusedArgs& fa, int grid, cudaStream_t st) {
   if (!batch_applies(md, nvec) || !batch_aligned(v, w))
     return {HPHI_ERR_INVALID_ARG, "batched rows: model, nvec or alignment not supported"};
-  if (batch_scratch_bytes(md, prec, cplx, nvec) != 0 && scratch == nullptr)
+  // several passes keep their partial sums in the buffer the last pass writes: not possible
+  // for the Lanczos epilogue, which reads that buffer's previous contents
+  if (plan && (plan->n_pass < 2 || epi == Epi::kLanczos1)) plan = nullptr;
+  if (batch_scratch_bytes(md, plan, prec, cplx, nvec) != 0 && scratch == nullptr)
     return {HPHI_ERR_INVALID_ARG, "batched rows: fp64 needs a scratch buffer"};
   switch (epi) {
-    case Epi::kStore: return launch_e<Epi::kStore>(md, prec, cplx, v, w, scratch, nvec, fa, grid, st);
-    case Epi::kLanczos1: return launch_e<Epi::kLanczos1>(md, prec, cplx, v, w, scratch, nvec, fa, grid, st);
-    case Epi::kTpq: return launch_e<Epi::kTpq>(md, prec, cplx, v, w, scratch, nvec, fa, grid, st);
+    case Epi::kStore: return launch_e<Epi::kStore>(md, plan, prec, cplx, v, w, scratch, nvec, fa, grid, st);
+    case Epi::kLanczos1: return launch_e<Epi::kLanczos1>(md, plan, prec, cplx, v, w, scratch, nvec, fa, grid, st);
+    case Epi::kTpq: return launch_e<Epi::kTpq>(md, plan, prec, cplx, v, w, scratch, nvec, fa, grid, st);
     case Epi::kRefine:
       if (prec != HPHI_FP64) break;
-      return launch_e<Epi::kRefine>(md, prec, cplx, v, w, scratch, nvec, fa, grid, st);
+      return launch_e<Epi::kRefine>(md, plan, prec, cplx, v, w, scratch, nvec, fa, grid, st);
   }
   return {HPHI_ERR_INVALID_ARG, "batched rows: unsupported precision / epilogue"};
 }

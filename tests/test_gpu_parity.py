@@ -393,6 +393,48 @@ def test_batched_rows_tpq(nv):
             assert _rel(res["h2"][:, c], h2) < tol
 
 
+@pytest.mark.parametrize("name,mk,bits", [
+    ("kitaev_3x2_w6", lambda: wl.kitaev_honeycomb(3, 2), 6),
+    ("kitaev_3x2_w8", lambda: wl.kitaev_honeycomb(3, 2), 8),
+    ("random_spin_9_w4", lambda: wl.random_spin_model(9, 14, seed=1), 4),
+    ("heisenberg_ring12_w5", lambda: wl.heisenberg_ring(12), 5),
+])
+@pytest.mark.parametrize("nvec", [32, 64])
+def test_window_passes_apply_H(name, mk, bits, nvec):
+    """Terms split over bit windows (several passes, rows visited window-bits-fastest)."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    m.set_window_bits(bits)
+    v = wl.gaussian_vector(81 + nvec, m.dim, nvec, complex_=m.is_complex)
+    ref = oracle.apply_H(spec, v)
+    ref = ref if m.is_complex else ref.real
+    for prec, tol in ((hp.FP64, 1e-12), (hp.FP32, 2e-5)):
+        w = m.apply_H(_to_dev(m, v, prec)).cpu().numpy()
+        assert _rel(w, ref) < tol
+
+
+def test_window_passes_tpq():
+    """mTPQ over 32 starts with window passes: the records match the oracle, and the passes
+    really ran (more kernel launches than with one pass)."""
+    spec = wl.kitaev_honeycomb(3, 2)
+    m = hp.Model.from_spec(spec)
+    psi0 = wl.gaussian_vector(94, m.dim, 32, complex_=True)
+    launches = {}
+    for bits in (-1, 6):
+        m.set_window_bits(bits)
+        for prec, tol in ((hp.FP64, 1e-11), (hp.FP32, 2e-5)):
+            res = m.tpq(32, 8, l=1.0, psi0=torch.as_tensor(psi0), prec=prec)
+            launches[(bits, prec)] = res["launches"]
+            for c in (0, 31):
+                u, h2, nrm = oracle.tpq(spec, psi0[:, c], 8, 1.0)
+                assert _rel(res["u"][:, c], u) < tol and _rel(res["norm"][:, c], nrm) < tol
+                assert _rel(res["h2"][:, c], h2) < tol
+    assert launches[(6, hp.FP64)] > launches[(-1, hp.FP64)]
+    assert launches[(6, hp.FP32)] > launches[(-1, hp.FP32)]
+    with pytest.raises(hp.LibraryError):
+        m.set_window_bits(40)
+
+
 # ----------------------------------------------------------------------------- sector batches
 def test_lanczos_sectors_match_oracle_and_single_runs():
     n = 12
