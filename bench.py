@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -33,6 +34,9 @@ import workloads as wl  # noqa: E402
 
 METRIC = "H·v Gelem/s & %HBM peak; Lanczos/mTPQ steps/s, FP64 vs mixed+batched at ΔE"
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per fused H v launch group from one ncu capture of the current
+# kernels (profiles/hubbard_4x4_8u8d_hv_group_dram.md); None where no capture exists
+MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): 11_850_000_000}
 FP64_PEAK_TINST = 0.625   # nominal GB300 fp64 rate, 1.25 TFLOP/s = 0.625 T FMA/s
 
 
@@ -124,6 +128,25 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds / 1e9
 
 
+def l2_note(vector_bytes: int) -> str:
+    if vector_bytes > 129e6:
+        return f"vectors ({vector_bytes / 1e9:.2f} GB) exceed the 129 MB L2; no flush"
+    return f"vectors ({vector_bytes / 1e6:.2f} MB) fit in L2: on-chip workload, no flush"
+
+
+def hv_group_name(spec, m, prec, nvec, what):
+    """The kernels of one fused H v launch group, as the library picks them."""
+    import paper_1703_03637_gb300 as hp
+    kind = "spin" if spec.kind == wl.SPIN else "hubbard"
+    if kind == "hubbard" and not m.is_complex:
+        ks = "k_maxexp + k_quant + k_hub_dn + k_hub_up_q" if prec == hp.FP64 else "k_hub_dn + k_hub_up"
+    elif kind == "spin" and spec.basis == wl.BASIS_FULL and nvec in (32, 64, 128, 256):
+        ks = "k_maxexp_cols + k_quant_cols + k_hv_batch" if prec == hp.FP64 else "k_hv_batch"
+    else:
+        ks = "k_hv_hub" if kind == "hubbard" else "k_hv_spin"
+    return f"{ks} ({what})"
+
+
 # ----------------------------------------------------------------------------- CPU oracle timing
 def oracle_rows_per_s(spec, target_s: float = 12.0, max_rows: int = 4_000_000):
     """Oracle H v over a slice of rows of the workload, all host cores; rows per second."""
@@ -133,7 +156,8 @@ def oracle_rows_per_s(spec, target_s: float = 12.0, max_rows: int = 4_000_000):
     v = np.empty(D, dtype=np.complex128)
     v.real = rng.standard_normal(D)
     v.imag = 0.0
-    n = 20000
+    n = min(20000, D)
+    max_rows = min(max_rows, D)
     t0 = time.perf_counter()
     oracle.apply_H_slice(spec, v, 0, n)
     dt = time.perf_counter() - t0
@@ -147,6 +171,27 @@ def oracle_rows_per_s(spec, target_s: float = 12.0, max_rows: int = 4_000_000):
 
 
 # ----------------------------------------------------------------------------- main
+def run_e2e_lanczos(m, D, seed, steps, prec, args, world):
+    """The same Lanczos run through the public API with the start vector copied from pinned
+    host memory every step and the energies read back; rows x steps per second."""
+    import torch
+    v0_host = torch.from_numpy(wl.gaussian_vector(seed, D)[:, 0]).pin_memory()
+    if m.is_complex:
+        v0_host = v0_host.to(torch.complex128).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        v0_dev = v0_host.to("cuda", non_blocking=True)
+        m.lanczos(steps, prec=prec, v0=v0_dev)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    return {"value": whole_job_rate(D * steps * e2e_steps, world, e2e_s), "unit": "Gelem/s",
+            "h2d_bytes_per_step": int(v0_host.numel() * v0_host.element_size()),
+            "d2h_bytes_per_step": int(8 * (2 * steps + 8 + 4))}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_1703_03637_gb300 as hp
@@ -156,6 +201,7 @@ def run_ours(args, world, rank, local):
     spec, steps = W["model"], (args.lanczos_steps or W["steps"])
     prec = hp.FP64 if args.prec == "fp64" else hp.FP32
     m = hp.Model.from_spec(spec)
+    esz = (8 if prec == hp.FP64 else 4) * (2 if m.is_complex else 1)
     D = m.dim
     seed = wl.START_SEED + rank
     tune = m.autotune(prec) if args.autotune else None  # untimed set-up: picks the launch shape
@@ -185,19 +231,10 @@ def run_ours(args, world, rank, local):
     value = whole_job_rate(rows_per_step * args.steps, world, ms / 1e3)
 
     # end to end: host (pinned) start vector -> device each step, energies back to the host
-    v0_host = torch.from_numpy(wl.gaussian_vector(seed, D)[:, 0]).pin_memory()
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
-    for _ in range(e2e_steps):
-        v0_dev = v0_host.to("cuda", non_blocking=True)
-        r2 = m.lanczos(steps, prec=prec, v0=v0_dev)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": whole_job_rate(rows_per_step * e2e_steps, world, e2e_s), "unit": "Gelem/s",
-           "h2d_bytes_per_step": int(v0_host.numel() * v0_host.element_size()),
-           "d2h_bytes_per_step": int(8 * (2 * steps + 8 + 4))}
+    # (skipped above 16 GB of host vector: the 6x6 sector's would be 73 GB)
+    e2e = None
+    if D * 8 <= 16e9:
+        e2e = run_e2e_lanczos(m, D, seed, steps, prec, args, world)
 
     # mixed precision (fp32 vectors, fp64 reductions) + fp64 Rayleigh-quotient refinement on the
     # same workload, timed the same way, with its energy error against the fp64 run
@@ -224,21 +261,22 @@ def run_ours(args, world, rank, local):
     if rank != 0:
         return None
     hbm, src = peaks()
-    esz = 8 if prec == hp.FP64 else 4
     bytes_row = 3 * esz   # fused H v + Lanczos pass 1: gather-read C once, read P, write P
     hv_avg_ms = hv_ms / max(hv_n, 1)
     achieved = D * bytes_row / (hv_avg_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-            "kernel": "k_hv_hub<fused Lanczos pass 1>", "kernel_avg_ms": round(hv_avg_ms, 4),
+            "frac": round(achieved / hbm, 4), "traffic": MEASURED_TRAFFIC.get((args.workload, args.prec)),
+            "peak_source": src,
+            "kernel": hv_group_name(spec, m, prec, 1, "Lanczos pass 1"), "kernel_avg_ms": round(hv_avg_ms, 4),
             "algorithmic_bytes_per_launch": D * bytes_row}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == hp.FP64 else "f32+f64acc", "data": "synthetic",
-        "config": {"workload": args.workload, "dim": D, "lanczos_steps": steps, "model": "hubbard_4x4_U8_t1",
-                   "sector": "N_up=N_dn=8", "start": "philox gaussian, seed 123432+rank",
-                   "l2": "vectors (1.33 GB) exceed L2; no flush", "parallelism": f"replicas{world}"},
+        "config": {"workload": args.workload, "dim": D, "lanczos_steps": steps, "model": spec.name,
+                   "sector": {0: "full", 1: f"S^z: n_up={spec.n_a}", 2: f"N_up={spec.n_a}, N_dn={spec.n_b}"}[spec.basis],
+                   "start": "philox gaussian, seed 123432+rank", "l2": l2_note(D * esz),
+                   "parallelism": f"replicas{world}"},
         "lanczos_steps_per_s": round(steps / (ms_step / 1e3), 2),
         "e0": res["eig"][0], "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
@@ -246,11 +284,160 @@ def run_ours(args, world, rank, local):
         out["mixed"] = mixed
     if tune is not None:
         out["autotune"] = tune
-    if args.cpu_baseline:
+    if args.cpu_baseline and D * 16 <= 16e9:
         rps, n, dt, cores = oracle_rows_per_s(spec)
         out["cpu_baseline"] = {"value": round(rps / 1e9, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
                                "sample": f"oracle H v on {n} contiguous rows of the same sector ({dt:.1f} s, "
                                          f"OpenMP over {cores} host threads); a Lanczos step is one such H v per row"}
+    elif args.cpu_baseline:
+        out["cpu_baseline"] = None
+        out["cpu_baseline_note"] = "not run: the oracle needs the whole input vector in host memory (16 B per row)"
+    return out
+
+
+def run_tpq(args, world, rank, local):
+    """mTPQ on the 64-start Kitaev cluster: one benchmark step is one hphi_tpq_run of `iters`
+    multiplications by (l - H/N_s) for all starts (a bounded slice of the 1000-step run: every
+    multiplication costs the same)."""
+    import torch
+    import paper_1703_03637_gb300 as hp
+
+    torch.cuda.set_device(local)
+    W = wl.workload(args.workload)
+    spec, K, nv = W["model"], (args.lanczos_steps or 20), W["n_starts"]
+    prec = hp.FP64 if args.prec == "fp64" else hp.FP32
+    m = hp.Model.from_spec(spec)
+    D = m.dim
+    esz = (8 if prec == hp.FP64 else 4) * (2 if m.is_complex else 1)
+    seed = wl.START_SEED + 1000 * rank
+    for _ in range(args.warmup):
+        m.tpq(nv, K, l=W["l"], prec=prec, seed=seed, profile=True)
+    stream = torch.cuda.current_stream()
+    clk = Clocks(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hv_ms, hv_n, launches, res = 0.0, 0, 0, None
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = m.tpq(nv, K, l=W["l"], prec=prec, seed=seed, profile=True)
+        hv_ms += res["hv_ms"]
+        hv_n += res["hv_launches"]
+        launches += res["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop() if clk else None
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    units = D * nv * K  # row x start elements multiplied per benchmark step
+    value = whole_job_rate(units * args.steps, world, ms / 1e3)
+
+    # end to end: the fp64 start block from pinned host memory, records back to the host
+    psi_host = torch.from_numpy(wl.gaussian_vector(seed, D, nv, complex_=m.is_complex)).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(1):
+        psi_dev = psi_host.to("cuda", non_blocking=True)
+        m.tpq(nv, K, l=W["l"], prec=prec, psi0=psi_dev)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": whole_job_rate(units, world, e2e_s), "unit": "Gelem/s",
+           "h2d_bytes_per_step": int(psi_host.numel() * psi_host.element_size()),
+           "d2h_bytes_per_step": int(3 * 8 * K * nv)}
+    del psi_host
+    if rank != 0:
+        return None
+    hbm, src = peaks()
+    bytes_elem = 2 * esz  # fused H v + TPQ update: gather-read X once, write X_{k+1}
+    hv_avg_ms = hv_ms / max(hv_n, 1)
+    achieved = D * nv * bytes_elem / (hv_avg_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
+            "kernel": hv_group_name(spec, m, prec, nv, "mTPQ step"), "kernel_avg_ms": round(hv_avg_ms, 4),
+            "algorithmic_bytes_per_launch": D * nv * bytes_elem}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": ("c128" if prec == hp.FP64 else "c64+f64acc") if m.is_complex else
+        ("f64" if prec == hp.FP64 else "f32+f64acc"), "data": "synthetic",
+        "config": {"workload": args.workload, "dim": D, "n_starts": nv, "tpq_steps_per_run": K, "l": W["l"],
+                   "model": spec.name, "start": "philox gaussian, seed 123432+1000*rank",
+                   "l2": l2_note(D * nv * esz), "parallelism": f"replicas{world}"},
+        "tpq_steps_per_s": round(K * args.steps / (ms / 1e3), 3),
+        "u_last_mean": float(np.mean(res["u"][-1])), "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if args.cpu_baseline:
+        rps, n, dt, cores = oracle_rows_per_s(spec)
+        out["cpu_baseline"] = {"value": round(rps / 1e9, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+                               "sample": f"oracle H v on {n} contiguous rows, one start ({dt:.1f} s, OpenMP over "
+                                         f"{cores} host threads); an mTPQ step is one such H v per row and start"}
+    return out
+
+
+def run_sectors(args, world, rank, local):
+    """Lanczos in every S^z sector of the 28-site J1-J2 ring, all sectors as parallel branches
+    of one CUDA graph; one benchmark step is one hphi_lanczos_run_sectors call."""
+    import torch
+    import paper_1703_03637_gb300 as hp
+
+    torch.cuda.set_device(local)
+    W = wl.workload(args.workload)
+    spec, steps, sectors = W["model"], (args.lanczos_steps or W["steps"]), W["sectors"]
+    prec = hp.FP64 if args.prec == "fp64" else hp.FP32
+    refine = prec == hp.FP32
+    m = hp.Model.from_spec(spec)
+    seed = wl.START_SEED + rank
+    for _ in range(args.warmup):
+        m.lanczos_sectors(sectors, steps, prec=prec, seed=seed, refine=refine)
+    stream = torch.cuda.current_stream()
+    clk = Clocks(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches, rs = 0, None
+    e0.record(stream)
+    for _ in range(args.steps):
+        rs = m.lanczos_sectors(sectors, steps, prec=prec, seed=seed, refine=refine)
+        launches += sum(r["launches"] for r in rs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop() if clk else None
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    # rows x steps actually taken (tiny sectors stop at breakdown)
+    dims = [math.comb(spec.n_sites, n) for n in sectors]
+    units = sum(d * r["steps"] for d, r in zip(dims, rs))
+    value = whole_job_rate(units * args.steps, world, ms / 1e3)
+    if rank != 0:
+        return None
+    e = [(r["e_refined"] if refine else r["eig"][0]) for r in rs]
+    # the sector runs are parallel branches of one graph, so no single kernel can be timed:
+    # the achieved rate is the whole call's (a lower bound for the fused H v kernels)
+    hbm, src = peaks()
+    esz = 8 if prec == hp.FP64 else 4
+    alg = 3 * esz * units  # fused H v + Lanczos pass 1 traffic of all sectors and steps
+    achieved = alg * args.steps / (ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
+            "kernel": "whole sector graph (k_hv_spin Lanczos pass 1 + pass 2 + solvers); lower bound",
+            "algorithmic_bytes_per_launch": alg}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == hp.FP64 else "f32+f64acc+f64 refine", "data": "synthetic",
+        "config": {"workload": args.workload, "dim_total": sum(dims), "sectors": len(sectors), "lanczos_steps": steps,
+                   "model": spec.name, "start": "philox gaussian, seed 123432+rank",
+                   "l2": l2_note(max(dims) * (8 if prec == hp.FP64 else 4)), "parallelism": f"replicas{world}"},
+        "e0_min": min(e), "roofline": roof, "gpu_launches": launches, "clocks": clocks,
+    }
+    if args.cpu_baseline:
+        sub = spec.with_basis(wl.BASIS_SZ, spec.n_sites // 2)
+        rps, n, dt, cores = oracle_rows_per_s(sub)
+        out["cpu_baseline"] = {"value": round(rps / 1e9, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+                               "sample": f"oracle H v on {n} contiguous rows of the S^z=0 sector ({dt:.1f} s, OpenMP "
+                                         f"over {cores} host threads)"}
     return out
 
 
@@ -262,16 +449,19 @@ def run_reference(args, world, rank):
     W = wl.workload(args.workload)
     spec = W["model"]
     D = oracle.dim(spec)
+    if D * 16 > 16e9:
+        return {"impl": "reference", "unavailable": "the oracle needs the whole input vector in host memory "
+                                                    f"({D * 16 / 1e9:.0f} GB for this workload)"}
     rng = np.random.default_rng(0)
     v = np.empty(D, dtype=np.complex128)
     v.real = rng.standard_normal(D)
     v.imag = 0.0
-    n = 300_000
+    n = min(300_000, D)
     for _ in range(args.warmup):
         oracle.apply_H_slice(spec, v, 0, n // 10)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle.apply_H_slice(spec, v, (k * n) % (D - n), n)
+        oracle.apply_H_slice(spec, v, (k * n) % max(D - n, 1), n)
     dt = time.perf_counter() - t0
     cores = os.cpu_count() or 1
     val = n * args.steps / dt / 1e9
@@ -290,9 +480,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hubbard_4x4_8u8d")
+    ap.add_argument("--workload", default="hubbard_4x4_8u8d", choices=wl.WORKLOADS)
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--lanczos-steps", type=int, default=0, help="override the workload's Lanczos step count")
+    ap.add_argument("--lanczos-steps", "--iters", dest="lanczos_steps", type=int, default=0,
+                    help="Lanczos steps (or mTPQ multiplications) per benchmark step; 0: the workload's "
+                         "(mTPQ: 20 of the 1000)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", help="skip the fp32 + fp64-refinement run")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", help="use the built-in launch shape")
@@ -308,7 +500,12 @@ def main():
             print(json.dumps(out), flush=True)
         return
     world, rank, local = dist_setup(args.gpus)
-    out = run_ours(args, world, rank, local)
+    if args.workload in ("kitaev_24_tpq64", "kitaev_18_tpq64"):
+        out = run_tpq(args, world, rank, local)
+    elif args.workload == "j1j2_ring28_all_sectors":
+        out = run_sectors(args, world, rank, local)
+    else:
+        out = run_ours(args, world, rank, local)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -255,6 +255,8 @@ typedef struct {
   const void* psi0;    /* optional device [dim][n_starts] fp64 start block (complex128 for
                           complex models); normalised internally per start               */
   int prec;            /* HPHI_FP64 or HPHI_FP32 (fp32 storage, fp64 norms and energies)   */
+  int profile;         /* 1: launch the steps one by one (no graph) and time every fused H v
+                          launch group with CUDA events (hv_ms below)                      */
 } hphi_tpq_params;
 
 typedef struct {
@@ -263,6 +265,8 @@ typedef struct {
   double* norm;        /* host [steps][n_starts]: |(l - H/N_s) psi_k|                     */
   float device_ms;     /* device time of the TPQ loop                                      */
   int kernel_launches; /* CUDA kernels this call launched                                   */
+  float hv_ms;         /* profile = 1: summed device time of the fused H v launch groups   */
+  int hv_launches;     /* number of fused H v launch groups timed in hv_ms                  */
 } hphi_tpq_result;
 
 /* Microcanonical TPQ (section 3.5): psi_{k+1} = (l - H/N_s) psi_k / |(l - H/N_s) psi_k| for

@@ -59,12 +59,13 @@ class TuneResult(ctypes.Structure):
 
 class TpqParams(ctypes.Structure):
     _fields_ = [("n_starts", ctypes.c_int), ("steps", ctypes.c_int), ("l", ctypes.c_double), ("n_s", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("psi0", ctypes.c_void_p), ("prec", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("psi0", ctypes.c_void_p), ("prec", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class TpqResult(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("h2", ctypes.c_void_p), ("norm", ctypes.c_void_p), ("device_ms", ctypes.c_float),
-                ("kernel_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("hv_ms", ctypes.c_float), ("hv_launches", ctypes.c_int)]
 
 
 _lib = None
@@ -335,7 +336,7 @@ class Model:
         return out
 
     def tpq(self, n_starts: int, steps: int, l: float = 1.0, n_s: float = 0.0, prec=FP64, seed: int = 123432,
-            psi0=None):
+            psi0=None, profile: bool = False):
         """Section 3.5 mTPQ for n_starts interleaved starts; returns dict(u, h2, norm, ms), arrays [steps, n_starts]."""
         torch = _torch()
         if psi0 is not None:
@@ -343,10 +344,11 @@ class Model:
         u = np.zeros((steps, n_starts))
         h2 = np.zeros((steps, n_starts))
         nr = np.zeros((steps, n_starts))
-        p = TpqParams(n_starts, steps, l, n_s, seed, _dptr(psi0) if psi0 is not None else None, prec)
-        r = TpqResult(u.ctypes.data, h2.ctypes.data, nr.ctypes.data, 0.0, 0)
+        p = TpqParams(n_starts, steps, l, n_s, seed, _dptr(psi0) if psi0 is not None else None, prec, int(profile))
+        r = TpqResult(u.ctypes.data, h2.ctypes.data, nr.ctypes.data, 0.0, 0, 0.0, 0)
         self._check(self._L.hphi_tpq_run(self._h, ctypes.byref(p), ctypes.byref(r), _stream()))
-        return dict(u=u, h2=h2, norm=nr, ms=r.device_ms, launches=r.kernel_launches)
+        return dict(u=u, h2=h2, norm=nr, ms=r.device_ms, launches=r.kernel_launches, hv_ms=r.hv_ms,
+                    hv_launches=r.hv_launches)
 
 
 def philox4x32_10(ctr, key):

@@ -1350,14 +1350,31 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
     if ((s = hphi::launch_random(ws.vecA.p, m->dim * nvec, cplx, prec == HPHI_FP64, p->seed, st)).code) return s;
   }
   HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
+  // profiled runs launch eagerly on st with an event pair around every H v launch group
+  // (events recorded inside a captured graph cannot be timed)
+  const bool prof = p->profile != 0;
+  std::vector<cudaEvent_t> ev(prof ? 2 * (size_t)K : 0, nullptr);
+  struct EvGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EvGuard() {
+      for (cudaEvent_t x : v)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev_guard{ev};
+  for (auto& x : ev) HPHI_CUDA_TRY(cudaEventCreate(&x));
   cudaStream_t cap = nullptr;
-  HPHI_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaStreamDestroy(cap);
-    return {HPHI_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)};
+  cudaError_t e = cudaSuccess;
+  if (prof) {
+    cap = st;
+  } else {
+    HPHI_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return {HPHI_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)};
+    }
   }
   auto body = [&]() -> hphi::Status {
     hphi::Status q;
@@ -1372,26 +1389,30 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
       fa.partials = partials;
       fa.l = p->l;
       fa.inv_ns = inv_ns;
+      if (prof) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * (size_t)k], cap));
       if ((q = hv_launch(m, prec, X, nullptr, nvec, hphi::Epi::kTpq, fa, grid, tscratch, cap)).code) return q;
+      if (prof) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * (size_t)k + 1], cap));
       if ((q = hphi::launch_tpq_fin(tq, k, nvec, inv_ns, partials, grid, cap)).code) return q;
       std::swap(X, Xn);
     }
     return {};
   };
   s = body();
-  e = cudaStreamEndCapture(cap, &graph);
-  if (s.code == 0 && e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e)};
-  if (s.code == 0) {
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)};
+  if (!prof) {
+    e = cudaStreamEndCapture(cap, &graph);
+    if (s.code == 0 && e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e)};
+    if (s.code == 0) {
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)};
+    }
+    if (s.code == 0) {
+      e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)};
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
   }
-  if (s.code == 0) {
-    e = cudaGraphLaunch(exec, st);
-    if (e != cudaSuccess) s = {HPHI_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)};
-  }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  cudaStreamDestroy(cap);
   if (s.code) return s;
   HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
   std::vector<double> host(3 * (size_t)K * nvec);
@@ -1405,6 +1426,13 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   if (r->norm) memcpy(r->norm, host.data() + 2 * kn, sizeof(double) * kn);
   r->device_ms = ms;
   r->kernel_launches = (p->psi0 ? 0 : 1) + 2 + (1 + hv_kernels(m, prec, nvec, hphi::Epi::kTpq)) * K;
+  r->hv_ms = 0.f;
+  r->hv_launches = prof ? K : 0;
+  for (int k = 0; prof && k < K; ++k) {
+    float t = 0.f;
+    HPHI_CUDA_TRY(cudaEventElapsedTime(&t, ev[2 * (size_t)k], ev[2 * (size_t)k + 1]));
+    r->hv_ms += t;
+  }
   return {};
 }
 

@@ -53,3 +53,30 @@ def test_no_cpu_fallback_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(hp.LibraryError):
         hp.Model(hp.SPIN_HALF, 4).build()
+
+
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/hphi_gpu.h, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "hphi_gpu.h")).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    body = m.group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        field = re.search(r"([A-Za-z_][A-Za-z0-9_]*)\s*(\[[^\]]*\])?$", decl).group(1)
+        out.append(field)
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [
+    ("hphi_lanczos_params", "LanczosParams"), ("hphi_lanczos_result", "LanczosResult"),
+    ("hphi_tpq_params", "TpqParams"), ("hphi_tpq_result", "TpqResult"), ("hphi_tune_result", "TuneResult"),
+])
+def test_binding_structs_follow_header(cname, pyname):
+    """The ctypes structures list the header's fields in the header's order."""
+    import paper_1703_03637_gb300 as hp
+    py = [f[0] for f in getattr(hp, pyname)._fields_]
+    assert py == _header_struct_fields(cname)

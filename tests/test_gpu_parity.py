@@ -379,6 +379,18 @@ def test_batched_rows_long_class_run():
         assert _rel(w, ref) < tol
 
 
+def test_tpq_profile_mode_matches_graph():
+    """Profiled mTPQ (eager launches, an event pair per H v group) gives the records of the
+    graph run bit for bit and times every step."""
+    spec = wl.kitaev_honeycomb(3, 2)
+    m = hp.Model.from_spec(spec)
+    for nv, prec in ((64, hp.FP32), (64, hp.FP64), (2, hp.FP64)):
+        a = m.tpq(nv, 6, l=1.0, prec=prec, seed=11)
+        b = m.tpq(nv, 6, l=1.0, prec=prec, seed=11, profile=True)
+        assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["norm"], b["norm"])
+        assert b["hv_launches"] == 6 and b["hv_ms"] > 0 and a["hv_launches"] == 0
+
+
 @pytest.mark.parametrize("nv", [32, 128])
 def test_batched_rows_tpq(nv):
     """mTPQ over 32 / 128 starts through the batched-row kernel against the oracle."""

@@ -253,6 +253,11 @@ def workload(name: str) -> dict:
     if name == "kitaev_24_tpq64":
         m = kitaev_honeycomb(4, 3, -1.0, 0.05)
         return dict(model=m, steps=1000, n_starts=64, l=1.0, dim=1 << 24)
+    if name == "kitaev_18_tpq64":
+        # the same cluster family at 3x3 cells (2^18 rows): small enough for kernel profiling,
+        # its 64-start blocks (134 MB c64, 268 MB c128) still exceed L2
+        m = kitaev_honeycomb(3, 3, -1.0, 0.05)
+        return dict(model=m, steps=1000, n_starts=64, l=1.0, dim=1 << 18)
     if name == "j1j2_ring28_all_sectors":
         m = j1j2_ring(28, 1.0, 0.5)
         return dict(model=m, steps=150, sectors=list(range(29)), dim=1 << 28)
@@ -263,4 +268,4 @@ def workload(name: str) -> dict:
 
 
 WORKLOADS = ["heisenberg_ring12_full", "hubbard_4x4_8u8d", "kitaev_24_tpq64", "j1j2_ring28_all_sectors",
-             "heisenberg_6x6_sz0"]
+             "heisenberg_6x6_sz0", "kitaev_18_tpq64"]
