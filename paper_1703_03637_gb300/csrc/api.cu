@@ -1111,7 +1111,7 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
       if ((q = hphi::launch_lz_pass2(prec, cplx, L.lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, L.n_real,
                                      L.partials, L.vgrid, st)).code)
         return q;
-      if ((q = hphi::launch_lz_fin2(L.lz, k, L.brk, L.partials, L.vgrid, st)).code) return q;
+      if ((q = hphi::launch_lz_fin2(L.lz, k, L.brk, L.partials, L.vgrid, with_x, st)).code) return q;
       if (!L.store) std::swap(C, P);
     }
     return {};
@@ -1119,7 +1119,10 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   if ((s = start()).code) return s;
   if ((s = run_pass(false)).code) return s;
   ++L.launches;
-  if ((s = hphi::launch_tridiag(L.lz, steps, L.n_eig, L.refine, st)).code) return s;
+  // the replayed pass may skip steps whose Ritz coefficients change the unit Ritz vector by
+  // less than the storage precision's rounding (fp64: 1e-15, fp32: 1e-8)
+  const double tail_tol = prec == HPHI_FP64 ? 1e-30 : 1e-16;
+  if ((s = hphi::launch_tridiag(L.lz, steps, L.n_eig, L.refine, tail_tol, st)).code) return s;
   if (!L.refine) return {};
   if (L.store) {
     // Ritz vector straight from the stored basis: one streaming pass

@@ -227,7 +227,7 @@ struct LzDev {           // device scalars of one Lanczos run
   double* beta;          // [m]   beta[k] = beta_{k+1}
   double* sig;           // [m+1] sigma_k = 1 / |C_k|
   double* coef;          // [m]   Ritz coefficients (refinement pass)
-  double* s;             // [16]  scratch scalars for the next kernel (c1, c2, gamma, xcoef)
+  double* s;             // [16]  scratch scalars (c1, c2, gamma, xcoef, last replay step)
   int* done;             // [1]   breakdown flag
   int* steps_done;       // [1]
   double* tri;           // [8 + 3]  eigenvalues and refinement results
@@ -239,8 +239,12 @@ Status launch_lz_init_fin(const LzDev& lz, const double* partials, int grid, cud
 Status launch_lz_fin1(const LzDev& lz, int k, const double* partials, int grid, cudaStream_t st);
 Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* C, void* P, double* x,
                        int64_t n_real, double* partials, int grid, cudaStream_t st);
-Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, cudaStream_t st);
-Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, cudaStream_t st);
+// replay: the refinement's second pass (stops after the last step with a significant Ritz
+// coefficient, keeps the first pass's step count)
+Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, bool replay,
+                      cudaStream_t st);
+// tail_tol: Ritz-coefficient weight below which the replayed second pass may stop
+Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, double tail_tol, cudaStream_t st);
 Status launch_refine_fin(const LzDev& lz, const double* partials, int grid, int which, cudaStream_t st);
 // x = sum_k coef_k sigma_k V_k over the stored Lanczos vectors (k < steps_done)
 Status launch_lz_combine(int prec, const LzDev& lz, const void* V, int64_t n_real, int64_t stride_real, double* x,

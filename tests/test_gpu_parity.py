@@ -271,7 +271,10 @@ def test_lanczos_mixed_with_fp64_refinement():
     rk = m.lanczos(120, prec=hp.FP32, v0=torch.as_tensor(v0), refine=True, keep_basis=1)
     assert np.array_equal(rk["alpha"], r["alpha"])
     assert abs(rk["e_refined"] - r["e_refined"]) <= 1e-12 * abs(e0)
-    assert abs(rk["residual"] - r["residual"]) <= 1e-6 * r["residual"] + 1e-12
+    # the replayed pass may stop at the last step whose Ritz coefficient matters at fp32
+    # storage precision, so its unit Ritz vector differs from the stored-basis one by < 1e-8
+    # and the residual |Hx - Ex| by < 1e-8 |H - E|
+    assert abs(rk["residual"] - r["residual"]) <= 1e-2 * r["residual"] + 1e-8 * (abs(e0) + 1.0)
     for kb in (-1, 1):
         r64 = m.lanczos(120, prec=hp.FP64, v0=torch.as_tensor(v0), refine=True, keep_basis=kb)
         assert abs(r64["e_refined"] - e0) <= 1e-10 * abs(e0)
