@@ -118,11 +118,6 @@ __device__ __forceinline__ F32Acc diff_acc(const F32Acc& p, const F32Acc& n) {
   r.s = p.s - n.s;
   return r;
 }
-__device__ __forceinline__ FixAcc diff_acc(const FixAcc& p, const FixAcc& n) {
-  FixAcc r = p;  // fp64 values never take pass D (they are quantised first); kept for completeness
-  r.add(n.value(), true);
-  return r;
-}
 
 // pass D: W[d][u] = sum over down-spin neighbours d' of d of +-X[d'][u].  Items run
 // stripe-major (stripe = kThreads * EPT columns) so one stripe of all rows is the L2
