@@ -271,7 +271,9 @@ typedef struct {
 
 /* Microcanonical TPQ (section 3.5): psi_{k+1} = (l - H/N_s) psi_k / |(l - H/N_s) psi_k| for
  * all starts at once, one fused pass per step (H psi, the update, and the fp64 per-start
- * reductions <psi|H psi>, |H psi|^2 and |psi_{k+1}|^2).  Record k describes psi_k, the state
+ * reductions <psi|H psi> and |H psi|^2); the norm |(l - H/N_s) psi_k|^2 = l^2 - 2 l u_k +
+ * <H^2>_k follows from them, so l must lie above the spectrum per site (the method's
+ * condition), which keeps that difference free of cancellation.  Record k describes psi_k, the state
  * the (k+1)-th multiplication acts on, for k = 0 .. steps-1; the inverse temperature is
  * beta_k = (2k / N_s) / (l - u_k). */
 int hphi_tpq_run(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* r, void* stream);

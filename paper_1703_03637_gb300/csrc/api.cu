@@ -1395,7 +1395,7 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
       if (prof) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * (size_t)k], cap));
       if ((q = hv_launch(m, prec, X, nullptr, nvec, hphi::Epi::kTpq, fa, grid, tscratch, cap)).code) return q;
       if (prof) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * (size_t)k + 1], cap));
-      if ((q = hphi::launch_tpq_fin(tq, k, nvec, inv_ns, partials, grid, cap)).code) return q;
+      if ((q = hphi::launch_tpq_fin(tq, k, nvec, inv_ns, p->l, partials, grid, cap)).code) return q;
       std::swap(X, Xn);
     }
     return {};

@@ -165,7 +165,7 @@ enum class Epi { kStore = 0, kLanczos1 = 1, kTpq = 2, kRefine = 3 };
 
 struct FusedArgs {
   // Lanczos pass 1: P <- c1 * Y - c2 * P; partial sum of self * Y.
-  // TPQ: Xn <- inv[c] * (l * X - Y / Ns); partial sums <X, Y>, |Y|^2, |Xn|^2 per column.
+  // TPQ: Xn <- inv[c] * (l * X - Y / Ns); partial sums <X, Y>, |Y|^2 per column.
   // Refine: stores Y and reduces <x, Y>, <x, x>.
   void* out = nullptr;             // P (Lanczos) / X_{k+1} (TPQ) / Hx (refine)
   const void* in = nullptr;        // Lanczos: previous vector read by pass 1 (null: same as out)
@@ -262,7 +262,7 @@ struct TpqDev {
 Status launch_tpq_init(int prec, bool cplx, const void* psi0_f64, void* X, int64_t n_rows, int nvec,
                        double* partials, int grid, cudaStream_t st);
 Status launch_tpq_init_fin(const TpqDev& tq, int nvec, const double* partials, int grid, cudaStream_t st);
-Status launch_tpq_fin(const TpqDev& tq, int k, int nvec, double inv_ns, const double* partials, int grid,
+Status launch_tpq_fin(const TpqDev& tq, int k, int nvec, double inv_ns, double l, const double* partials, int grid,
                       cudaStream_t st);
 
 }  // namespace hphi

@@ -140,11 +140,11 @@ struct EpiScalars {
   double c1, c2;  // Lanczos pass 1
 };
 
-template <class S, Epi E>
+template <class S, Epi E, int NQ = kMaxRedQ>
 __device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>::R sr, typename Traits<S>::R si,
                                          typename Traits<S>::R hr, typename Traits<S>::R hi, S* __restrict__ w,
                                          const FusedArgs& fa, const EpiScalars& es, const double* s_inv,
-                                         Red<Traits<S>::kF64>& red) {
+                                         Red<Traits<S>::kF64, NQ>& red) {
   using R = typename Traits<S>::R;
   constexpr bool C = Traits<S>::kCplx;
   if constexpr (E == Epi::kStore) {
@@ -161,7 +161,8 @@ __device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>:
     if constexpr (C) red.add(0, si, hi);
     red.tick();
   } else if constexpr (E == Epi::kTpq) {
-    // X_{k+1} = (l X_k - H X_k / N_s) / |X_k| ; partials <X, HX>, |HX|^2, |X_{k+1}|^2
+    // X_{k+1} = (l X_k - H X_k / N_s) / |X_k| ; partials <X, HX>, |HX|^2.  |X_{k+1}|^2 follows
+    // from them (section 3.5's norm, deferred): l^2 - 2 l u_k + <H^2>_k.
     S* Xn = reinterpret_cast<S*>(fa.out);
     const R inv = (R)s_inv[c], l = (R)fa.l, ins = (R)fa.inv_ns;
     const R nr = inv * (l * sr - hr * ins);
@@ -169,11 +170,9 @@ __device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>:
     st<S>(Xn, idx, nr, ni);
     red.add(0, sr, hr);
     red.add(1, hr, hr);
-    red.add(2, nr, nr);
     if constexpr (C) {
       red.add(0, si, hi);
       red.add(1, hi, hi);
-      red.add(2, ni, ni);
     }
     red.tick();
   } else {  // kRefine: Hx stored; partials <x, Hx>, <x, x>, <Hx, Hx>
@@ -191,7 +190,7 @@ __device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>:
 }
 
 template <Epi E> __host__ __device__ constexpr int n_red() {
-  return E == Epi::kStore ? 0 : (E == Epi::kLanczos1 ? 1 : 3);
+  return E == Epi::kStore ? 0 : (E == Epi::kLanczos1 ? 1 : (E == Epi::kTpq ? 2 : 3));
 }
 
 }  // namespace hphi

@@ -26,11 +26,12 @@ namespace {
 // Launch shape per scalar type and epilogue, from a sweep on the 2^24-row, 64-vector Kitaev
 // workload: kRegs = 32-bit registers of gathered values in flight per thread, kMinB =
 // resident CTAs per SM the register budget is cut for, kLaneBytes = bytes of a row one lane
-// gathers per term (at least).  The plain fp32 product keeps the most loads in flight; the
-// fused steps and fp64 trade them for occupancy; fp64 lanes take 64 bytes (four columns).
+// gathers per term (at least).  The plain fp32 product keeps the most loads in flight, the
+// fp32 mTPQ step a few less (its sums need registers), fp64 fewer still; fp64 lanes take
+// 64 bytes (four columns).
 template <class S, Epi E> struct BatchTune {
   static constexpr bool kF64 = Traits<S>::kF64;
-  static constexpr int kRegs = (!kF64 && E == Epi::kStore) ? 64 : 32;
+  static constexpr int kRegs = kF64 ? 32 : (E == Epi::kStore ? 64 : (E == Epi::kTpq ? 48 : 32));
   static constexpr int kMinB = 2;
   static constexpr int kLaneBytes = kF64 ? 64 : 32;
 };
@@ -196,7 +197,8 @@ __global__ void __launch_bounds__(kThreads, BatchTune<S, E>::kMinB)
   }
   __syncthreads();
 
-  Red<F64> red[CPL];
+  constexpr int kNQ = n_red<E>() > 0 ? n_red<E>() : 1;
+  Red<F64, kNQ> red[CPL];
 #pragma unroll
   for (int q = 0; q < CPL; ++q) red[q].zero();
   const int lpr = nvec / CPL;  // lanes per row: a power of two <= 32
@@ -348,9 +350,42 @@ __global__ void __launch_bounds__(kThreads, BatchTune<S, E>::kMinB)
     } else {
       Regs<R, CPL> x0;  // read again (from L1 / L2) rather than held across the term loop
       vload<S, CPL>(reinterpret_cast<const R*>(v + off), x0);
+      if constexpr (E == Epi::kTpq || E == Epi::kRefine) {
+        // the same updates and sums as the shared epilogue, with the row's columns written
+        // as 16-byte stores
+        Regs<R, CPL> o;
 #pragma unroll
-      for (int q = 0; q < CPL; ++q)
-        epilogue<S, E>(off + q, c0 + q, x0.re[q], x0.im[q], h.re[q], h.im[q], w, fa, es, s_inv, red[q]);
+        for (int q = 0; q < CPL; ++q) {
+          if constexpr (E == Epi::kTpq) {
+            const R inv = (R)s_inv[c0 + q], l = (R)fa.l, ins = (R)fa.inv_ns;
+            o.re[q] = inv * (l * x0.re[q] - h.re[q] * ins);
+            o.im[q] = inv * (l * x0.im[q] - h.im[q] * ins);
+            red[q].add(0, x0.re[q], h.re[q]);
+            red[q].add(1, h.re[q], h.re[q]);
+            if constexpr (C) {
+              red[q].add(0, x0.im[q], h.im[q]);
+              red[q].add(1, h.im[q], h.im[q]);
+            }
+          } else {
+            o.re[q] = h.re[q];
+            o.im[q] = h.im[q];
+            red[q].add(0, x0.re[q], h.re[q]);
+            red[q].add(1, x0.re[q], x0.re[q]);
+            red[q].add(2, h.re[q], h.re[q]);
+            if constexpr (C) {
+              red[q].add(0, x0.im[q], h.im[q]);
+              red[q].add(1, x0.im[q], x0.im[q]);
+              red[q].add(2, h.im[q], h.im[q]);
+            }
+          }
+          red[q].tick();
+        }
+        vstore<S, CPL>(reinterpret_cast<R*>(reinterpret_cast<S*>(fa.out) + off), o);
+      } else {
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+          epilogue<S, E, kNQ>(off + q, c0 + q, x0.re[q], x0.im[q], h.re[q], h.im[q], w, fa, es, s_inv, red[q]);
+      }
     }
   }
   if constexpr (E != Epi::kStore) {

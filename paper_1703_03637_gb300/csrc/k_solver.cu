@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_tpq_init(const double* __restrict_
 }
 
 // one CTA per column; mode 0: initial norms; mode 1: records of step k
-__global__ void __launch_bounds__(kThreads) k_tpq_fin(TpqDev tq, int mode, int k, int nvec, double inv_ns,
+__global__ void __launch_bounds__(kThreads) k_tpq_fin(TpqDev tq, int mode, int k, int nvec, double inv_ns, double l,
                                                        const double* __restrict__ partials, int grid) {
   __shared__ double sm[kThreads];
   const int c = blockIdx.x;
@@ -356,12 +356,14 @@ __global__ void __launch_bounds__(kThreads) k_tpq_fin(TpqDev tq, int mode, int k
   }
   const double xy = sum_partials(partials, grid, nvec, c, 0, sm);
   const double yy = sum_partials(partials, grid, nvec, c, 1, sm);
-  const double nn = sum_partials(partials, grid, nvec, c, 2, sm);
   if (threadIdx.x == 0) {
     const double n2 = tq.n2[c];
     const size_t o = (size_t)k * nvec + c;
-    tq.u[o] = xy * inv_ns / n2;
-    tq.h2[o] = yy * inv_ns * inv_ns / n2;
+    const double u = xy * inv_ns / n2, h2 = yy * inv_ns * inv_ns / n2;
+    // |(l - H/N_s) psi_k|^2 for the unit psi_k; positive for l above the spectrum per site
+    const double nn = fmax(l * l - 2.0 * l * u + h2, 2.2250738585072014e-308);
+    tq.u[o] = u;
+    tq.h2[o] = h2;
     tq.nrm[o] = sqrt(nn);
     tq.n2[c] = nn;
     tq.inv[c] = 1.0 / sqrt(nn);
@@ -472,14 +474,14 @@ Status launch_tpq_init(int prec, bool cplx, const void* psi0_f64, void* X, int64
 }
 
 Status launch_tpq_init_fin(const TpqDev& tq, int nvec, const double* partials, int grid, cudaStream_t st) {
-  k_tpq_fin<<<nvec, kThreads, 0, st>>>(tq, 0, 0, nvec, 0.0, partials, grid);
+  k_tpq_fin<<<nvec, kThreads, 0, st>>>(tq, 0, 0, nvec, 0.0, 0.0, partials, grid);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
 
-Status launch_tpq_fin(const TpqDev& tq, int k, int nvec, double inv_ns, const double* partials, int grid,
+Status launch_tpq_fin(const TpqDev& tq, int k, int nvec, double inv_ns, double l, const double* partials, int grid,
                       cudaStream_t st) {
-  k_tpq_fin<<<nvec, kThreads, 0, st>>>(tq, 1, k, nvec, inv_ns, partials, grid);
+  k_tpq_fin<<<nvec, kThreads, 0, st>>>(tq, 1, k, nvec, inv_ns, l, partials, grid);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }

@@ -11,13 +11,14 @@
 
 namespace hphi {
 
-template <bool F64> struct Red;
+// NQ: number of reduced quantities (kernels that know theirs keep fewer registers)
+template <bool F64, int NQ = kMaxRedQ> struct Red;
 
-template <> struct Red<true> {
-  double s[kMaxRedQ];
+template <int NQ> struct Red<true, NQ> {
+  double s[NQ];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int q = 0; q < kMaxRedQ; ++q) s[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) s[q] = 0.0;
   }
   __device__ __forceinline__ void add(int q, double a, double b) { s[q] = fma(a, b, s[q]); }
   __device__ __forceinline__ void tick() {}
@@ -26,13 +27,13 @@ template <> struct Red<true> {
 
 // fp32 products accumulated without loss in (hi, lo) pairs: TwoProduct by FMA and TwoSum
 // (Knuth); every 16 elements the pair is added to an fp64 total.
-template <> struct Red<false> {
-  double tot[kMaxRedQ];
-  float hi[kMaxRedQ], lo[kMaxRedQ];
+template <int NQ> struct Red<false, NQ> {
+  double tot[NQ];
+  float hi[NQ], lo[NQ];
   int n;
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int q = 0; q < kMaxRedQ; ++q) { tot[q] = 0.0; hi[q] = 0.f; lo[q] = 0.f; }
+    for (int q = 0; q < NQ; ++q) { tot[q] = 0.0; hi[q] = 0.f; lo[q] = 0.f; }
     n = 0;
   }
   __device__ __forceinline__ void add(int q, float a, float b) {
@@ -46,7 +47,7 @@ template <> struct Red<false> {
   }
   __device__ __forceinline__ void flush() {
 #pragma unroll
-    for (int q = 0; q < kMaxRedQ; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       tot[q] += (double)hi[q] + (double)lo[q];
       hi[q] = 0.f;
       lo[q] = 0.f;
