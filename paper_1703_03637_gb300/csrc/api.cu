@@ -626,7 +626,19 @@ size_t hv_scratch_bytes(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
   if (use_batch(m, nvec))
     return hphi::batch_scratch_bytes(m->sdev, epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec), prec,
                                      m->cplx_model, nvec);
+  if (m->kind == HPHI_SPIN_HALF) return hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, nvec);
   return 0;
+}
+
+// Scratch that only speeds a launch up (the quantised copy of the generic spin path): the
+// workspace buffer if it can hold `need` bytes, else null (the launch then runs without it).
+void* optional_scratch(hphi_model* m, size_t need) {
+  if (need == 0) return nullptr;
+  if (m->ws.work.ensure(need).code) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return m->ws.work.p;
 }
 
 int hv_grid_for(hphi_model* m, int nvec, int prec, hphi::Epi epi) {
@@ -653,7 +665,16 @@ hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec
     if (scratch != nullptr || hphi::batch_scratch_bytes(m->sdev, plan, prec, m->cplx_model, nvec) == 0)
       return hphi::launch_batch(m->sdev, plan, prec, m->cplx_model, v, w, scratch, nvec, epi, fa, grid, st);
   }
-  return hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec, epi, fa, grid, st);
+  // spin models: scratch, when given, is at least spin_scratch_bytes (the caller sized it
+  // with hv_scratch_bytes, whose batched-row figure has the same quantised-copy layout)
+  void* sp = (m->kind == HPHI_SPIN_HALF && scratch != nullptr &&
+              hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, nvec) != 0 &&
+              m->ws.work.bytes >= hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, nvec) &&
+              scratch == m->ws.work.p)
+                 ? scratch
+                 : nullptr;
+  return hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec, epi, fa, grid, sp,
+                         st);
 }
 
 }  // namespace
@@ -826,7 +847,9 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
   hphi::FusedArgs fa;
   void* scratch = nullptr;
   const size_t need = hv_scratch_bytes(m, prec, nvec, hphi::Epi::kStore);
-  if (need) {
+  if (need && m->kind == HPHI_SPIN_HALF && !use_batch(m, nvec)) {
+    scratch = optional_scratch(m, need);
+  } else if (need) {
     hphi::Status a = m->ws.work.ensure(need);
     if (a.code) return fail(m, a);
     scratch = m->ws.work.p;
@@ -1035,6 +1058,12 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
     if (L.refine) need = std::max(need, hphi::hub_scratch_bytes(m->hdev, HPHI_FP64, hphi::Epi::kRefine));
     if ((s = ws.work.ensure(need)).code) return s;
     L.scratch = ws.work.p;
+  } else if (m->kind == HPHI_SPIN_HALF) {
+    // fp64 spin H v gathers from a quantised copy (one more vector); without the memory the
+    // per-term fixed-point sums run instead
+    size_t need = hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, 1);
+    if (L.refine) need = std::max(need, hphi::spin_scratch_bytes(m->sdev, HPHI_FP64, m->cplx_model, 1));
+    L.scratch = optional_scratch(m, need);
   }
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * hphi::kMaxRedQ)).code) return s;
   L.partials = ws.partials.as<double>();

@@ -175,9 +175,12 @@ struct FusedArgs {
   double l = 0.0, inv_ns = 0.0;
 };
 
-// Launches w = H v (or a fused step) over all rows; grid chosen by the library.
+// Launches w = H v (or a fused step) over all rows; grid chosen by the library.  Spin models
+// in fp64 gather from a quantised copy of v when scratch (spin_scratch_bytes) is given.
 Status launch_hv(bool hubbard, const void* md, int prec, bool cplx, const void* v, void* w, int nvec, Epi epi,
-                 const FusedArgs& fa, int grid, cudaStream_t st);
+                 const FusedArgs& fa, int grid, void* scratch, cudaStream_t st);
+bool spin_quantised(const SpinDev& md, int prec, int nvec);
+size_t spin_scratch_bytes(const SpinDev& md, int prec, bool cplx, int nvec);
 int hv_grid(int nvec);  // upper bound of any H v grid (partials sizing)
 
 // Two-pass Hubbard path (k_hub.cu): neighbour tables, and H v = diag + up hops (row tiles
@@ -215,6 +218,9 @@ bool batch_plan_windows(int n_sites, int wbits, const std::vector<SpinEntry>& en
 // window size whose block of rows (input rows only) fills about a quarter of L2
 int batch_window_bits(int prec, bool cplx, int nvec);
 bool batch_applies(const SpinDev& md, int nvec);
+// Q = the [rows][nvec] (x ncomp) fp64 block quantised to 64-bit integers, one scale per
+// column: q = round(x 2^(1078 - E_c)), E_c the column's largest exponent field (into E)
+Status launch_quant_cols(const double* v, int64_t rows, int nvec, int ncomp, long long* Q, int* E, cudaStream_t st);
 bool batch_aligned(const void* v, const void* w);
 size_t batch_scratch_bytes(const SpinDev& md, const BatchPlan* plan, int prec, bool cplx, int nvec);
 int batch_grid(int prec, bool cplx, int nvec, Epi epi, int64_t dim);

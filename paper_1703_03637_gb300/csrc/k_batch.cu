@@ -422,17 +422,8 @@ Status launch_q(const SpinDev& md, const BatchPlan* plan, const void* v, void* w
     const size_t vb = (size_t)md.dim * nvec * sizeof(S);
     long long* q = reinterpret_cast<long long*>(scratch);
     int* e = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(scratch) + vb);
-    const int rowlen = nvec * ncomp;
-    int lg_row = 0;
-    while ((1 << lg_row) < rowlen) ++lg_row;
-    HPHI_CUDA_TRY(cudaMemsetAsync(e, 0, sizeof(int) * nvec, st));
-    const int gv =
-        (int)std::min<int64_t>(((int64_t)md.dim * rowlen + kThreads - 1) / kThreads, (int64_t)num_sms() * 8);
-    k_maxexp_cols<<<gv, kThreads, 0, st>>>(reinterpret_cast<const double*>(v), md.dim, rowlen, ncomp, e);
-    HPHI_CUDA_TRY(cudaGetLastError());
-    k_quant_cols<<<gv, kThreads, 0, st>>>(reinterpret_cast<const double*>(v), q, (int64_t)md.dim * rowlen, lg_row,
-                                          ncomp == 2 ? 1 : 0, e);
-    HPHI_CUDA_TRY(cudaGetLastError());
+    Status qs = launch_quant_cols(reinterpret_cast<const double*>(v), md.dim, nvec, ncomp, q, e, st);
+    if (qs.code) return qs;
     Q = q;
     Ec = e;
   }
@@ -606,6 +597,22 @@ bool batch_plan_windows(int n_sites, int wbits, const std::vector<SpinEntry>& en
   }
   *n_pass = (int)chosen.size();
   return true;
+}
+
+Status launch_quant_cols(const double* v, int64_t rows, int nvec, int ncomp, long long* Q, int* E, cudaStream_t st) {
+  const int rowlen = nvec * ncomp;
+  if ((rowlen & (rowlen - 1)) != 0 || nvec > kMaxNvec)
+    return {HPHI_ERR_INVALID_ARG, "quantised copy: nvec must be a power of two up to 256"};
+  int lg_row = 0;
+  while ((1 << lg_row) < rowlen) ++lg_row;
+  HPHI_CUDA_TRY(cudaMemsetAsync(E, 0, sizeof(int) * nvec, st));
+  const int gv = (int)std::max<int64_t>(
+      1, std::min<int64_t>((rows * rowlen + kThreads - 1) / kThreads, (int64_t)num_sms() * 8));
+  k_maxexp_cols<<<gv, kThreads, 0, st>>>(v, rows, rowlen, ncomp, E);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  k_quant_cols<<<gv, kThreads, 0, st>>>(v, Q, rows * rowlen, lg_row, ncomp == 2 ? 1 : 0, E);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
 }
 
 bool batch_applies(const SpinDev& md, int nvec) {

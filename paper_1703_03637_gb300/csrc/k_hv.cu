@@ -10,6 +10,8 @@
 // the two hopping sites.  Reductions for the fused steps are per-thread partial sums
 // (fp64, or error-free fp32 TwoSum chunks flushed to fp64) reduced per CTA in a fixed
 // order and written to a partials array, so results are bit-reproducible run to run.
+#include <type_traits>
+
 #include "basis.cuh"
 #include "common.cuh"
 #include "reduce.cuh"
@@ -27,11 +29,19 @@ namespace {
 // thread (patterns are sorted by class), so class flushes never diverge.
 constexpr int kBatch = 8;
 
-template <class S, Epi E>
+//
+// QT (fp64): the gathers read the input quantised to 64-bit integers, one scale per vector
+// column (q = round(x 2^(1078 - E_c)), |q| < 2^56), so every class sum of at most 127 terms
+// is an exact integer sum (two integer instructions a term instead of the per-term
+// alignment of the fixed-point accumulator), converted to fp64 once per class.
+template <class S, Epi E, bool QT = false>
 __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S* __restrict__ v, S* __restrict__ w,
-                                                      int nvec, int lg_nvec, FusedArgs fa) {
+                                                      int nvec, int lg_nvec, FusedArgs fa,
+                                                      const long long* __restrict__ Q, const int* __restrict__ Ec) {
   using R = typename Traits<S>::R;
-  using A = typename SumAcc<R>::T;
+  static_assert(!QT || Traits<S>::kF64, "quantised gathers are an fp64 path");
+  using A = std::conditional_t<QT, IntAcc, typename SumAcc<R>::T>;
+  using T = std::conditional_t<QT, long long, R>;  // gathered scalar
   constexpr bool C = Traits<S>::kCplx;
   constexpr bool F64 = Traits<S>::kF64;
   __shared__ SpinEntry s_ent[kMaxSpinEntries];
@@ -126,13 +136,14 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
     R sr, si;
     ld<S>(v, idx, sr, si);
     R hr = d * sr, hi = d * si;
+    const int eoff = QT ? Ec[c] - 1078 : 0;
 
     A ar, ai;
     ar.zero();
     ai.zero();
     int cur = n_ent ? s_ent[0].cls : 0;
     for (int e0 = 0; e0 < n_ent; e0 += kBatch) {
-      R xr[kBatch], xi[kBatch];
+      T xr[kBatch], xi[kBatch];
       int code[kBatch];
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
@@ -147,7 +158,18 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
           if (code[j]) {
             const uint64_t s2 = s ^ en.mask;
             const uint64_t r2 = md.sector ? sector_rank(md.t, s2) : s2;
-            ld<S>(v, (int64_t)r2 * nvec + c, xr[j], xi[j]);
+            if constexpr (QT) {
+              const int64_t o = (int64_t)r2 * nvec + c;
+              if constexpr (C) {
+                const longlong2 t = __ldg(reinterpret_cast<const longlong2*>(Q) + o);
+                xr[j] = t.x;
+                xi[j] = t.y;
+              } else {
+                xr[j] = __ldg(Q + o);
+              }
+            } else {
+              ld<S>(v, (int64_t)r2 * nvec + c, xr[j], xi[j]);
+            }
           }
         }
       }
@@ -158,7 +180,14 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
           const int cls = s_ent[k].cls;
           if (cls != cur) {
             const double2 cc = s_cls[cur];
-            const R vr = (R)ar.value(), vi = (R)ai.value();
+            R vr, vi;
+            if constexpr (QT) {
+              vr = fix_to_double(ar.value(), eoff);
+              vi = C ? fix_to_double(ai.value(), eoff) : 0.0;
+            } else {
+              vr = (R)ar.value();
+              vi = (R)ai.value();
+            }
             if constexpr (C) {
               hr += (R)cc.x * vr - (R)cc.y * vi;
               hi += (R)cc.x * vi + (R)cc.y * vr;
@@ -170,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
             cur = cls;
           }
           if (code[j]) {
-            if constexpr (C) acc_phase<A, R>(code[j], xr[j], xi[j], ar, ai);
+            if constexpr (C) acc_phase<A, T>(code[j], xr[j], xi[j], ar, ai);
             else ar.add(xr[j], code[j] != 1);
           }
         }
@@ -178,7 +207,14 @@ __global__ void __launch_bounds__(kThreads) k_hv_spin(const SpinDev md, const S*
     }
     if (n_ent) {
       const double2 cc = s_cls[cur];
-      const R vr = (R)ar.value(), vi = (R)ai.value();
+      R vr, vi;
+      if constexpr (QT) {
+        vr = fix_to_double(ar.value(), eoff);
+        vi = C ? fix_to_double(ai.value(), eoff) : 0.0;
+      } else {
+        vr = (R)ar.value();
+        vi = (R)ai.value();
+      }
       if constexpr (C) {
         hr += (R)cc.x * vr - (R)cc.y * vi;
         hi += (R)cc.x * vi + (R)cc.y * vr;
@@ -455,7 +491,7 @@ int occupancy_e(bool hub, int prec, bool cplx) {
 
 template <class S, Epi E>
 Status launch_t(bool hub, const void* md, const void* v, void* w, int nvec, const FusedArgs& fa, int grid,
-                cudaStream_t st) {
+                void* scratch, cudaStream_t st) {
   int lg = -1;
   if ((nvec & (nvec - 1)) == 0) {
     lg = 0;
@@ -468,8 +504,23 @@ Status launch_t(bool hub, const void* md, const void* v, void* w, int nvec, cons
     k_hv_hub<S, E><<<grid, kThreads, 0, st>>>(*reinterpret_cast<const HubDev*>(md), reinterpret_cast<const S*>(v),
                                              reinterpret_cast<S*>(w), nvec, lg, fa);
   } else {
-    k_hv_spin<S, E><<<grid, kThreads, 0, st>>>(*reinterpret_cast<const SpinDev*>(md), reinterpret_cast<const S*>(v),
-                                              reinterpret_cast<S*>(w), nvec, lg, fa);
+    const SpinDev& sd = *reinterpret_cast<const SpinDev*>(md);
+    bool qt = false;
+    if constexpr (Traits<S>::kF64) {
+      if (spin_quantised(sd, HPHI_FP64, nvec) && scratch != nullptr) {
+        constexpr int ncomp = Traits<S>::kCplx ? 2 : 1;
+        long long* q = reinterpret_cast<long long*>(scratch);
+        int* e = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(scratch) + (size_t)sd.dim * nvec * sizeof(S));
+        Status qs = launch_quant_cols(reinterpret_cast<const double*>(v), sd.dim, nvec, ncomp, q, e, st);
+        if (qs.code) return qs;
+        k_hv_spin<S, E, true><<<grid, kThreads, 0, st>>>(sd, reinterpret_cast<const S*>(v), reinterpret_cast<S*>(w),
+                                                         nvec, lg, fa, q, e);
+        qt = true;
+      }
+    }
+    if (!qt)
+      k_hv_spin<S, E><<<grid, kThreads, 0, st>>>(sd, reinterpret_cast<const S*>(v), reinterpret_cast<S*>(w), nvec, lg,
+                                                fa, nullptr, nullptr);
   }
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
@@ -477,13 +528,13 @@ Status launch_t(bool hub, const void* md, const void* v, void* w, int nvec, cons
 
 template <Epi E>
 Status launch_e(bool hub, const void* md, int prec, bool cplx, const void* v, void* w, int nvec, const FusedArgs& fa,
-                int grid, cudaStream_t st) {
+                int grid, void* scratch, cudaStream_t st) {
   if (prec == HPHI_FP64) {
-    return cplx ? launch_t<double2, E>(hub, md, v, w, nvec, fa, grid, st)
-                : launch_t<double, E>(hub, md, v, w, nvec, fa, grid, st);
+    return cplx ? launch_t<double2, E>(hub, md, v, w, nvec, fa, grid, scratch, st)
+                : launch_t<double, E>(hub, md, v, w, nvec, fa, grid, scratch, st);
   }
-  return cplx ? launch_t<float2, E>(hub, md, v, w, nvec, fa, grid, st)
-              : launch_t<float, E>(hub, md, v, w, nvec, fa, grid, st);
+  return cplx ? launch_t<float2, E>(hub, md, v, w, nvec, fa, grid, scratch, st)
+              : launch_t<float, E>(hub, md, v, w, nvec, fa, grid, scratch, st);
 }
 
 }  // namespace
@@ -504,15 +555,25 @@ int hv_resident_grid(bool hubbard, int prec, bool cplx, Epi epi) {
   return num_sms() * b;
 }
 
+bool spin_quantised(const SpinDev& md, int prec, int nvec) {
+  return prec == HPHI_FP64 && md.max_run <= 127 && nvec >= 1 && nvec <= kMaxNvec && (nvec & (nvec - 1)) == 0;
+}
+
+size_t spin_scratch_bytes(const SpinDev& md, int prec, bool cplx, int nvec) {
+  if (!spin_quantised(md, prec, nvec)) return 0;
+  return (size_t)md.dim * nvec * 8 * (cplx ? 2 : 1) + sizeof(int) * (size_t)nvec;
+}
+
 Status launch_hv(bool hubbard, const void* md, int prec, bool cplx, const void* v, void* w, int nvec, Epi epi,
-                 const FusedArgs& fa, int grid, cudaStream_t st) {
+                 const FusedArgs& fa, int grid, void* scratch, cudaStream_t st) {
   switch (epi) {
-    case Epi::kStore: return launch_e<Epi::kStore>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, st);
-    case Epi::kLanczos1: return launch_e<Epi::kLanczos1>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, st);
-    case Epi::kTpq: return launch_e<Epi::kTpq>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, st);
+    case Epi::kStore: return launch_e<Epi::kStore>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, scratch, st);
+    case Epi::kLanczos1:
+      return launch_e<Epi::kLanczos1>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, scratch, st);
+    case Epi::kTpq: return launch_e<Epi::kTpq>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, scratch, st);
     case Epi::kRefine:
       if (prec != HPHI_FP64) return {HPHI_ERR_INVALID_ARG, "refinement runs in fp64"};
-      return launch_e<Epi::kRefine>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, st);
+      return launch_e<Epi::kRefine>(hubbard, md, prec, cplx, v, w, nvec, fa, grid, scratch, st);
   }
   return {HPHI_ERR_INVALID_ARG, "unknown epilogue"};
 }
