@@ -207,8 +207,9 @@ typedef struct {
   int profile;         /* 1: time every fused H v launch with CUDA events (hv_ms below)   */
   int keep_basis;      /* refinement source: 1 keep all m Lanczos vectors in device memory
                           and form x = V_m e~ in one streaming pass; -1 replay the recurrence
-                          (section 3.4's second pass); 0 keep them when they fit in 60% of
-                          the free device memory, else replay                            */
+                          (section 3.4's second pass), stopping after the last step whose
+                          Ritz coefficient still matters at the storage precision; 0 keep
+                          them when they fit in 60% of the free device memory, else replay */
 } hphi_lanczos_params;
 
 typedef struct {
