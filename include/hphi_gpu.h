@@ -268,6 +268,8 @@ typedef struct {
   int kernel_launches; /* CUDA kernels this call launched                                   */
   float hv_ms;         /* profile = 1: summed device time of the fused H v launch groups   */
   int hv_launches;     /* number of fused H v launch groups timed in hv_ms                  */
+  double* beta;        /* host [steps][n_starts] or NULL: inverse temperature of record k,
+                          beta_k = (2k / N_s) / (l - u_k) (section 3.5)                     */
 } hphi_tpq_result;
 
 /* Microcanonical TPQ (section 3.5): psi_{k+1} = (l - H/N_s) psi_k / |(l - H/N_s) psi_k| for

@@ -65,7 +65,8 @@ class TpqParams(ctypes.Structure):
 
 class TpqResult(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("h2", ctypes.c_void_p), ("norm", ctypes.c_void_p), ("device_ms", ctypes.c_float),
-                ("kernel_launches", ctypes.c_int), ("hv_ms", ctypes.c_float), ("hv_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("hv_ms", ctypes.c_float), ("hv_launches", ctypes.c_int),
+                ("beta", ctypes.c_void_p)]
 
 
 _lib = None
@@ -337,17 +338,19 @@ class Model:
 
     def tpq(self, n_starts: int, steps: int, l: float = 1.0, n_s: float = 0.0, prec=FP64, seed: int = 123432,
             psi0=None, profile: bool = False):
-        """Section 3.5 mTPQ for n_starts interleaved starts; returns dict(u, h2, norm, ms), arrays [steps, n_starts]."""
+        """Section 3.5 mTPQ for n_starts interleaved starts; returns dict(u, h2, norm, beta, ms, ...), arrays
+        [steps, n_starts]."""
         torch = _torch()
         if psi0 is not None:
             psi0 = psi0.to(device="cuda", dtype=torch.complex128 if self.is_complex else torch.float64).contiguous()
         u = np.zeros((steps, n_starts))
         h2 = np.zeros((steps, n_starts))
         nr = np.zeros((steps, n_starts))
+        bt = np.zeros((steps, n_starts))
         p = TpqParams(n_starts, steps, l, n_s, seed, _dptr(psi0) if psi0 is not None else None, prec, int(profile))
-        r = TpqResult(u.ctypes.data, h2.ctypes.data, nr.ctypes.data, 0.0, 0, 0.0, 0)
+        r = TpqResult(u.ctypes.data, h2.ctypes.data, nr.ctypes.data, 0.0, 0, 0.0, 0, bt.ctypes.data)
         self._check(self._L.hphi_tpq_run(self._h, ctypes.byref(p), ctypes.byref(r), _stream()))
-        return dict(u=u, h2=h2, norm=nr, ms=r.device_ms, launches=r.kernel_launches, hv_ms=r.hv_ms,
+        return dict(u=u, h2=h2, norm=nr, beta=bt, ms=r.device_ms, launches=r.kernel_launches, hv_ms=r.hv_ms,
                     hv_launches=r.hv_launches)
 
 

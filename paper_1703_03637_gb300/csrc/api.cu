@@ -1456,6 +1456,13 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   if (r->u) memcpy(r->u, host.data(), sizeof(double) * kn);
   if (r->h2) memcpy(r->h2, host.data() + kn, sizeof(double) * kn);
   if (r->norm) memcpy(r->norm, host.data() + 2 * kn, sizeof(double) * kn);
+  if (r->beta) {
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < nvec; ++c) {
+        const size_t o = (size_t)k * nvec + c;
+        r->beta[o] = (2.0 * k / ns) / (p->l - host[o]);  // host[o] = u_k of start c
+      }
+  }
   r->device_ms = ms;
   r->kernel_launches = (p->psi0 ? 0 : 1) + 2 + (1 + hv_kernels(m, prec, nvec, hphi::Epi::kTpq)) * K;
   r->hv_ms = 0.f;

@@ -301,6 +301,9 @@ def test_tpq_fp64_parity(name, mk, nv, K):
         assert _rel(res["u"][:, c], u) < 1e-11
         assert _rel(res["h2"][:, c], h2) < 1e-11
         assert _rel(res["norm"][:, c], nrm) < 1e-11
+        # section 3.5's inverse temperature of record k: (2k / N_s) / (l - u_k), beta_0 = 0
+        beta = 2.0 * np.arange(K) / spec.n_sites / (1.0 - u)
+        assert res["beta"][0, c] == 0.0 and _rel(res["beta"][:, c], beta) < 1e-10
 
 
 def test_tpq_fp32_parity():
