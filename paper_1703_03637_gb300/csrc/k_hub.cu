@@ -432,10 +432,20 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
   const bool c_p2 = same_c && (cbits & 0xfffffffffffffll) == 0 && cexp > 0 && cexp < 0x7ff;
   const bool c_neg = cbits < 0;
   const int c_l2 = cexp - 1023;
+  // With such a hopping the element is computed in units of 2^e2, e2 = eoff + k:
+  // hv = (dg 2^-k xr + (+-(acc + wq))) 2^e2 with xr = q as fp64, so the two per-element
+  // power-of-two scalings fold into the diagonal table, the Lanczos coefficient and the
+  // per-CTA partial sum (both scales must be normal numbers).
+  const int e2 = eoff + c_l2;
+  const bool fold = c_p2 && eoff >= -1022 && eoff <= 1023 && e2 >= -1022 && e2 <= 1023 &&
+                    (E == Epi::kStore || E == Epi::kLanczos1);
+  const double s_eoff = fold ? __longlong_as_double((long long)(eoff + 1023) << 52) : 1.0;
+  const double s_e2 = fold ? __longlong_as_double((long long)(e2 + 1023) << 52) : 1.0;
+  const double r_k = fold ? __longlong_as_double((long long)(1023 - c_l2) << 52) : 1.0;  // 2^-k
   // diagonal = c0 + U * popcount(up & dn & mask) in the common single-group case: table
   __shared__ double s_dtab[33];
   const bool dtab = md.n_ulin == 1 && md.n_mulin == 0 && md.n_pairs == 0;
-  if (dtab && tid <= 32) s_dtab[tid] = md.c0 + md.ulin[0].coef * (double)tid;
+  if (dtab && tid <= 32) s_dtab[tid] = (md.c0 + md.ulin[0].coef * (double)tid) * r_k;
   __syncthreads();
   Red<true> red;
   red.zero();
@@ -481,8 +491,8 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
         const int64_t idx = (d0 + m) * dim_up + u;
         // the row's own value from the quantised tile: H v is then H applied to the
         // quantised vector (each element within 2^-57 max|x| of v, as in the gathers)
-        const double x = fix_to_double(tile[u * K + m], eoff);
-        double dg;
+        const double xr = __ll2double_rn(tile[u * K + m]);
+        double dg;  // (times 2^-k when folding)
         if (dtab) {
           dg = s_dtab[__popc(up & dn[m] & (uint32_t)s_ulin[0].mask)];
         } else {
@@ -507,13 +517,30 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
           }
           dg += s_pcoef[grp] * (double)cnt;
         }
+        if (fold) dg *= r_k;
         }
         const long long wq = __ldg(WQ + idx);
-        double hv;
-        if (c_p2) hv = fma(dg, x, fix_to_double(c_neg ? -(acc[m] + wq) : acc[m] + wq, eoff + c_l2));
-        else if (same_c) hv = fma(dg, x, md.c_up * fix_to_double(acc[m] + wq, eoff));
-        else hv = fma(dg, x, fma(md.c_up, fix_to_double(acc[m], eoff), md.c_dn * fix_to_double(wq, eoff)));
-        epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, w, fa, es, s_inv, red);
+        if (fold) {
+          const long long y = c_neg ? -(acc[m] + wq) : acc[m] + wq;
+          const double hvu = fma(dg, xr, __ll2double_rn(y));  // hv = hvu 2^e2
+          if constexpr (E == Epi::kStore) {
+            w[idx] = hvu * s_e2;
+          } else if constexpr (E == Epi::kLanczos1) {
+            // P <- c1 hv - c2 P; partial <x, hv> in units of 2^(eoff + e2)
+            double* P = reinterpret_cast<double*>(fa.out);
+            const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
+            P[idx] = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+            red.add(0, xr, hvu);
+            red.tick();
+          }
+        } else {
+          const double x = fix_to_double(tile[u * K + m], eoff);
+          double hv;
+          if (c_p2) hv = fma(dg, x, fix_to_double(c_neg ? -(acc[m] + wq) : acc[m] + wq, eoff + c_l2));
+          else if (same_c) hv = fma(dg, x, md.c_up * fix_to_double(acc[m] + wq, eoff));
+          else hv = fma(dg, x, fma(md.c_up, fix_to_double(acc[m], eoff), md.c_dn * fix_to_double(wq, eoff)));
+          epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, w, fa, es, s_inv, red);
+        }
       }
     }
   }
@@ -523,6 +550,7 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
 #pragma unroll
     for (int q = 0; q < nq; ++q) {
       double x = red.get(q);
+      if (fold) x = (x * s_eoff) * s_e2;  // back from units of 2^(eoff + e2)
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
       if (lane == 0) s_red[wid * kMaxRedQ + q] = x;
