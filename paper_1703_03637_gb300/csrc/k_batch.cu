@@ -4,20 +4,24 @@
 // The vectors are stored [row][column], so the nvec entries a term gathers from row s ^ mask
 // are contiguous.  A row is handled by nvec / CPL lanes, lane l owning CPL consecutive
 // columns (32 or 64 bytes: two or four 16-byte loads per neighbour); a warp takes
-// 32 / (nvec / CPL) rows at once.  The per-term work (entry, phase code, neighbour row) is paid once per lane for CPL
-// columns instead of once per column as in the generic kernel, and the loads are 16 bytes wide.
+// 32 / (nvec / CPL) rows at once.  The per-term work (entry, phase code, neighbour row) is
+// paid once per lane for CPL columns instead of once per column as in the generic kernel,
+// and the loads are 16 bytes wide.
 //
 // fp64 runs the gathers on a copy of the input quantised to 64-bit integers with one scale
 // per column (q = round(x 2^(1078 - E_c)), |q| < 2^56): the sum of a class run of at most 127
 // terms is an exact integer sum, converted to fp64 once (the same trick as the two-pass
 // Hubbard path, for the same reason: fp64 adds run at 1/64 of the fp32 rate on this part).
+//
+// Optional window passes (section 4.3's continuous memory access on one GPU): each pass takes
+// the terms whose flipped sites lie in one cyclic window and visits the rows with that
+// window's bits varying fastest, keeping its partial sums in the buffer the last pass writes.
 #include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
 #include "epilogue.cuh"
 #include "reduce.cuh"
-
 
 namespace hphi {
 
