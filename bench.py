@@ -35,8 +35,9 @@ import workloads as wl  # noqa: E402
 METRIC = "H·v Gelem/s & %HBM peak; Lanczos/mTPQ steps/s, FP64 vs mixed+batched at ΔE"
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per fused H v launch group from one ncu capture of the current
-# kernels (profiles/hubbard_4x4_8u8d_hv_group_dram.md); None where no capture exists
-MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): 11_880_000_000}
+# kernels (profiles/hubbard_4x4_8u8d_hv_group_dram.md: quantise + pass D + pass U, the group
+# of every step after the first); None where no capture exists
+MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): 10_560_000_000}
 FP64_PEAK_TINST = 0.625   # nominal GB300 fp64 rate, 1.25 TFLOP/s = 0.625 T FMA/s
 
 

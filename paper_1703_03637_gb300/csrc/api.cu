@@ -617,6 +617,11 @@ int hv_kernels(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
     const int passes = plan ? plan->n_pass : 1;
     return passes + (hphi::batch_scratch_bytes(m->sdev, plan, prec, m->cplx_model, nvec) ? 2 : 0);
   }
+  if (m->kind == HPHI_SPIN_HALF) {
+    // the quantised copy (max-exponent and quantise kernels) when the workspace holds it
+    const size_t q = hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, nvec);
+    return 1 + ((q != 0 && m->ws.work.p != nullptr && m->ws.work.bytes >= q) ? 2 : 0);
+  }
   return 1;
 }
 
@@ -1111,9 +1116,14 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
     ++L.launches;  // buffer A holds C_0 (regenerated bit-identically for the second pass)
     return hphi::launch_random(c0, m->dim, cplx, prec == HPHI_FP64, L.seed, st);
   };
+  // fp64 two-pass Hubbard: pass 2 also finds the next vector's largest exponent, so the next
+  // step's H v skips its own max-exponent scan
+  int* emax = (prec == HPHI_FP64 && L.scratch != nullptr && use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1))
+                  ? hphi::hub_exponent_slot(m->hdev, L.scratch)
+                  : nullptr;
   auto run_pass = [&](bool with_x) -> hphi::Status {
     hphi::Status q;
-    L.launches += 2 + (3 + hv_kernels(m, prec, 1, hphi::Epi::kLanczos1)) * steps;
+    L.launches += 2 + (3 + hv_kernels(m, prec, 1, hphi::Epi::kLanczos1)) * steps - (emax ? steps - 1 : 0);
     if ((q = hphi::launch_lz_init(prec, cplx, L.v0, c0, p0, L.n_real, L.partials, L.vgrid, st)).code) return q;
     if ((q = hphi::launch_lz_init_fin(L.lz, L.partials, L.vgrid, st)).code) return q;
     if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)L.n_real, st));
@@ -1132,13 +1142,15 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
       fa.scal = L.lz.s;
       fa.partials = L.partials;
       fa.done = L.lz.done;
+      fa.exp_ready = (emax != nullptr && k > 0) ? 1 : 0;
       const bool timed = L.profile && !with_x;
       if (timed) HPHI_CUDA_TRY(cudaEventRecord(L.ev[2 * k], st));
       if ((q = hv_launch(m, prec, C, nullptr, 1, hphi::Epi::kLanczos1, fa, L.grid, L.scratch, st)).code) return q;
       if (timed) HPHI_CUDA_TRY(cudaEventRecord(L.ev[2 * k + 1], st));
       if ((q = hphi::launch_lz_fin1(L.lz, k, L.partials, L.grid, st)).code) return q;
+      if (emax) HPHI_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int), st));
       if ((q = hphi::launch_lz_pass2(prec, cplx, L.lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, L.n_real,
-                                     L.partials, L.vgrid, st)).code)
+                                     L.partials, L.vgrid, emax, st)).code)
         return q;
       if ((q = hphi::launch_lz_fin2(L.lz, k, L.brk, L.partials, L.vgrid, with_x, st)).code) return q;
       if (!L.store) std::swap(C, P);

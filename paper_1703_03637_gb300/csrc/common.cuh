@@ -173,6 +173,8 @@ struct FusedArgs {
   double* partials = nullptr;      // [grid][nvec][kMaxRedQ]
   const int* done = nullptr;       // device flag: skip all work when set
   double l = 0.0, inv_ns = 0.0;
+  int exp_ready = 0;               // fp64 two-pass Hubbard: the input's exponent is already in
+                                   // the scratch slot (computed by the previous Lanczos pass 2)
 };
 
 // Launches w = H v (or a fused step) over all rows; grid chosen by the library.  Spin models
@@ -190,6 +192,8 @@ Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_
 bool hub_fast_ok(const HubDev& md, int prec, bool cplx, int nvec, Epi epi);
 int hub_up_grid(const HubDev& md, int prec, Epi epi);
 size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi);  // scratch the launch needs
+// the fp64 input-exponent slot inside that scratch (see FusedArgs::exp_ready)
+int* hub_exponent_slot(const HubDev& md, void* scratch);
 // fp64 H v of the two-pass path with its scratch in a fixed device array (no allocation)
 Status launch_hub_store_noalloc(const HubDev& md, const void* v, void* w, cudaStream_t st);
 size_t noalloc_capacity_bytes();
@@ -243,8 +247,9 @@ Status launch_lz_init(int prec, bool cplx, const void* v0_f64, void* C, void* P,
                       int grid, cudaStream_t st);
 Status launch_lz_init_fin(const LzDev& lz, const double* partials, int grid, cudaStream_t st);
 Status launch_lz_fin1(const LzDev& lz, int k, const double* partials, int grid, cudaStream_t st);
+// emax (fp64 only, may be null): atomicMax of the exponent fields of the new P
 Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* C, void* P, double* x,
-                       int64_t n_real, double* partials, int grid, cudaStream_t st);
+                       int64_t n_real, double* partials, int grid, int* emax, cudaStream_t st);
 // replay: the refinement's second pass (stops after the last step with a significant Ritz
 // coefficient, keeps the first pass's step count)
 Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, bool replay,

@@ -651,9 +651,11 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
   int* Ep = reinterpret_cast<int*>(WQ + md.dim);
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(WQ + md.dim) + 1;
   const int gv = (int)std::max<int64_t>(1, std::min<int64_t>((md.dim + kThreads - 1) / kThreads, (int64_t)num_sms() * 8));
-  HPHI_CUDA_TRY(cudaMemsetAsync(Ep, 0, sizeof(int), st));
-  k_maxexp<<<gv, kThreads, 0, st>>>(X, md.dim, Ep, fa.done);
-  HPHI_CUDA_TRY(cudaGetLastError());
+  if (!fa.exp_ready) {
+    HPHI_CUDA_TRY(cudaMemsetAsync(Ep, 0, sizeof(int), st));
+    k_maxexp<<<gv, kThreads, 0, st>>>(X, md.dim, Ep, fa.done);
+    HPHI_CUDA_TRY(cudaGetLastError());
+  }
   k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done);
   HPHI_CUDA_TRY(cudaGetLastError());
   Status sd = launch_dn<long long>(md, Q, WQ, fa.done, counter, st);
@@ -673,6 +675,10 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
 #undef HPHI_UPQ
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
+}
+
+int* hub_exponent_slot_impl(const HubDev& md, void* scratch) {
+  return reinterpret_cast<int*>(reinterpret_cast<long long*>(scratch) + 2 * md.dim);
 }
 
 int upq_grid(const HubDev& md, Epi epi) {
@@ -803,6 +809,8 @@ int hub_up_grid(const HubDev& md0, int prec, Epi epi) {
   const HubDev md = with_shape(md0, prec);
   return prec == HPHI_FP64 ? upq_grid(md, epi) : up_grid_r<float>(md, epi);
 }
+
+int* hub_exponent_slot(const HubDev& md, void* scratch) { return hub_exponent_slot_impl(md, scratch); }
 
 size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi) {
   if (prec == HPHI_FP64) return quant_scratch_bytes(md);

@@ -94,11 +94,12 @@ __global__ void __launch_bounds__(kThreads) k_lz_fin(LzDev lz, int mode, int k, 
   }
 }
 
-// P <- P - gamma C ; partial |P|^2 ; optionally x += xc * C (fp64 accumulator)
+// P <- P - gamma C ; partial |P|^2 ; optionally x += xc * C (fp64 accumulator); optionally
+// (emax) the largest exponent field of the new P, which the next step's quantisation needs
 template <class R, bool X>
 __global__ void __launch_bounds__(kThreads) k_lz_pass2(LzDev lz, const R* __restrict__ C, R* __restrict__ P,
                                                         double* __restrict__ x, int64_t n_real,
-                                                        double* __restrict__ partials) {
+                                                        double* __restrict__ partials, int* __restrict__ emax) {
   constexpr bool F64 = sizeof(R) == 8;
   __shared__ double sm[kThreads];
   if (*lz.done) return;
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_lz_pass2(LzDev lz, const R* __rest
   const double xc = X ? lz.s[3] : 0.0;
   Red<F64> red;
   red.zero();
+  int mx = 0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += (int64_t)gridDim.x * kThreads) {
     const R c = C[i];
     const R p = P[i] - gr * c;
@@ -114,6 +116,12 @@ __global__ void __launch_bounds__(kThreads) k_lz_pass2(LzDev lz, const R* __rest
     red.add(0, p, p);
     red.tick();
     if (X) x[i] = fma(xc, (double)c, x[i]);
+    if constexpr (F64) mx = max(mx, (int)((__double_as_longlong((double)p) >> 52) & 0x7ff));
+  }
+  if (F64 && emax != nullptr) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(emax, mx);
   }
   const double t = block_sum(red.get(0), sm);
   if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kMaxRedQ] = t;
@@ -399,23 +407,23 @@ Status launch_lz_fin1(const LzDev& lz, int k, const double* partials, int grid, 
 }
 
 Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* C, void* P, double* x, int64_t n_real,
-                       double* partials, int grid, cudaStream_t st) {
+                       double* partials, int grid, int* emax, cudaStream_t st) {
   (void)cplx;
   (void)k;
   if (prec == HPHI_FP64) {
     if (x)
       k_lz_pass2<double, true><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const double*>(C),
-                                                          reinterpret_cast<double*>(P), x, n_real, partials);
+                                                          reinterpret_cast<double*>(P), x, n_real, partials, emax);
     else
       k_lz_pass2<double, false><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const double*>(C),
-                                                           reinterpret_cast<double*>(P), x, n_real, partials);
+                                                           reinterpret_cast<double*>(P), x, n_real, partials, emax);
   } else {
     if (x)
       k_lz_pass2<float, true><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const float*>(C),
-                                                         reinterpret_cast<float*>(P), x, n_real, partials);
+                                                         reinterpret_cast<float*>(P), x, n_real, partials, nullptr);
     else
       k_lz_pass2<float, false><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const float*>(C),
-                                                          reinterpret_cast<float*>(P), x, n_real, partials);
+                                                          reinterpret_cast<float*>(P), x, n_real, partials, nullptr);
   }
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
