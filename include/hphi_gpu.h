@@ -121,8 +121,9 @@ int hphi_basis_ranks(hphi_model* m, const uint64_t* states, int64_t n, int64_t* 
  * scalar type in precision prec (HPHI_FP64 or HPHI_FP32); v and w must not overlap.
  * Matrix-free: every element is generated on the fly from the bit strings.  Scratch the
  * kernels need lives in the model's workspace, allocated on first use and kept: the two-pass
- * Hubbard path one vector, fp64 with nvec in {32, 64, 128, 256} on a full-basis spin model
- * (when v and w start on 32-byte boundaries) one vector of 64-bit integers. */
+ * Hubbard path one vector; fp64 on spin models one vector of 64-bit integers (the quantised
+ * input; for the generic kernel only if the device has room, else its per-term fixed-point
+ * sums run instead). */
 int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void* stream);
 
 /* Allocation-free w = H v.  The paper has no counterpart: this is a service for callers
