@@ -44,6 +44,11 @@ def test_host_validation_without_gpu():
     assert L.hphi_set_basis(h, hp.BASIS_SZ, 2, 0) == 0
     assert L.hphi_dim(h) == -4                                  # not built
     assert L.hphi_apply_H(h, None, None, 1, 0, None) == -4
+    assert L.hphi_set_window_bits(h, -2) == -1                  # window size: -1, 0 or 1..32
+    assert L.hphi_set_window_bits(h, 33) == -1
+    assert L.hphi_set_window_bits(h, 6) == 0 and L.hphi_set_window_bits(h, -1) == 0
+    assert L.hphi_set_window_bits(None, 6) == -1
+    assert L.hphi_tpq_run(h, None, None, None) == -4            # not built before the arguments
     L.hphi_destroy(h)
 
 
