@@ -34,6 +34,7 @@ namespace {
 
 // columns per thread in pass D (stripe = kThreads * EPT columns); the stripe of all rows is
 // the L2 working set of pass D
+// built-in pass-D columns per thread per precision (hphi_autotune replaces them per model)
 #ifndef HPHI_DN_EPT32
 #define HPHI_DN_EPT32 4
 #endif
