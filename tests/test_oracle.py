@@ -347,3 +347,14 @@ def test_gaussian_moments():
     for part in (g.real, g.imag):
         assert abs(part.mean()) < 0.01 and abs(part.var() - 1.0) < 0.01
         assert abs(np.mean(part ** 4) - 3.0) < 0.05
+
+
+def test_tpq_deferred_norm_identity():
+    """The identity the GPU's mTPQ step uses instead of a third reduction: for a unit psi,
+    |(l - H/N_s) psi|^2 = l^2 - 2 l u + <H^2>/N_s^2, with u = <psi|H|psi>/N_s (section 3.5).
+    Checked on the oracle's own records, which take the norm directly."""
+    spec = wl.kitaev_honeycomb(2, 2)
+    psi0 = wl.gaussian_vector(17, oracle.dim(spec), 1, complex_=True)[:, 0]
+    for l in (1.0, 1.5):
+        u, h2, nrm = oracle.tpq(spec, psi0, 12, l)
+        assert np.max(np.abs(nrm ** 2 - (l * l - 2.0 * l * u + h2))) < 1e-12
