@@ -568,3 +568,71 @@ def test_autotune_keeps_results_exact():
         w = m.apply_H(_to_dev(m, v[:, None], prec)).cpu().numpy()[:, 0]
         assert _rel(w, ref) < (1e-12 if prec == hp.FP64 else 2e-5)
     assert hp.Model.from_spec(wl.heisenberg_ring(8)).autotune()["n_candidates"] == 0
+
+
+# ----------------------------------------------------------------------------- bench kernel instance
+@pytest.mark.parametrize("n_up,n_dn", [(8, 2), (8, 3)])
+def test_lanczos_hubbard_4x4_up_row_instance(n_up, n_dn):
+    """The 4x4 torus with 8 up electrons: up rows of C(16,8) = 12,870 entries, so pass U runs
+    the instance the full 8+8 benchmark times (two int64 rows per 206 KB tile, 1024 threads,
+    the power-of-two hopping folded into the scales).  Few down electrons keep the dimension
+    (1.5 M and 7.2 M) small enough for the oracle.  Checked with the built-in launch shape
+    and again after the FP64 autotuner has picked its own."""
+    spec = wl.hubbard_square(4, 4, 1.0, 8.0).with_basis(wl.BASIS_NUMBER, n_up, n_dn)
+    m = hp.Model.from_spec(spec)
+    v0 = wl.gaussian_vector(61 + n_dn, m.dim)[:, 0]
+    steps = 40
+    a, b = oracle.lanczos(spec, v0, steps)
+    e0 = oracle.ritz_values(a, b)[0]
+    for tuned in (False, True):
+        if tuned:
+            t = m.autotune(hp.FP64)
+            assert t["n_candidates"] >= 4
+        res = m.lanczos(steps, v0=torch.as_tensor(v0), n_eig=2)
+        assert res["steps"] == len(a)
+        assert _rel(res["alpha"][:12], a[:12]) < 1e-12
+        assert _rel(res["beta"][:12], b[:12]) < 1e-12
+        assert abs(res["eig"][0] - e0) <= 1e-10 * abs(e0)
+
+
+# ----------------------------------------------------------------------------- wide dynamic range
+WIDE_CASES = [
+    ("spin_sector_4x3", lambda: wl.heisenberg_square(4, 3).with_basis(wl.BASIS_SZ, 6), 1),
+    ("xxz_complex_sector", lambda: wl.random_xxz_model(11, 20, seed=8).with_basis(wl.BASIS_SZ, 5), 1),
+    ("ring10_full", lambda: wl.heisenberg_ring(10), 1),
+    ("kitaev_2x2_32vec", lambda: wl.kitaev_honeycomb(2, 2), 32),
+    ("hubbard_ring7_33_two_pass", lambda: wl.hubbard_ring(7, 1.0, 4.0).with_basis(wl.BASIS_NUMBER, 3, 3), 1),
+]
+
+
+@pytest.mark.parametrize("name,mk,nvec", WIDE_CASES, ids=[c[0] for c in WIDE_CASES])
+def test_apply_H_wide_dynamic_range(name, mk, nvec):
+    """Inputs spanning 30 decades (Gaussian x 10^-U(0,30)), like late mTPQ states or converged
+    Lanczos vectors.  The fp64 paths round the input once onto a 64-bit fixed-point grid (one
+    scale per vector column, step <= 2^-56 max|x|), so a small output element is accurate to
+    an absolute, not a relative, bound.  Per element r the test checks
+        fp64: |w_r - (Hx)_r| <= ||H_r||_1 max|x| 2^-55 + 2^-50 (|H| |x|)_r
+        fp32: |w_r - (Hx32)_r| <= (n_r + 4) 2^-24 (|H| |x32|)_r   (n_r terms in row r)
+    with the exact product taken from the oracle's dense matrix."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    H = oracle.dense_H(spec)
+    absH = np.abs(H)
+    rng = np.random.default_rng(99)
+    x = wl.gaussian_vector(98, m.dim, nvec, complex_=m.is_complex) * 10.0 ** (-rng.uniform(0, 30, size=(m.dim, nvec)))
+    w = m.apply_H(_to_dev(m, x)).cpu().numpy()
+    ref = H @ x
+    ax = np.abs(x)
+    row1 = absH.sum(axis=1)[:, None]
+    bound = row1 * ax.max(axis=0)[None, :] * 2.0 ** -55 + 2.0 ** -50 * (absH @ ax)
+    err = np.abs(w - (ref if m.is_complex else ref.real))
+    assert np.all(err <= bound), float(np.max(err / bound))
+    # fp32 storage: relative to each row's sum of |terms|
+    x32 = _to_dev(m, x, hp.FP32)
+    w32 = m.apply_H(x32).cpu().numpy().astype(np.complex128 if m.is_complex else np.float64)
+    xr = x32.cpu().numpy().astype(np.complex128)
+    ref32 = H @ xr
+    nterms = np.count_nonzero(absH, axis=1)[:, None]
+    bound32 = (nterms + 4) * 2.0 ** -24 * (absH @ np.abs(xr))
+    err32 = np.abs(w32 - (ref32 if m.is_complex else ref32.real))
+    assert np.all(err32 <= bound32), float(np.max(err32 / np.maximum(bound32, 1e-300)))

@@ -71,20 +71,38 @@ def test_rank_unrank_36_bits_random():
 
 
 def test_paper_fermion_4ary_example():
-    """Section 3.1: |0, up, dn, updn> = [0123]_4 = 27 in the paper's interleaved layout.
+    """Section 3.1: the 4-site configuration |0, up, dn, updn> is [0123]_4 = 27, one base-4
+    digit per site (0 empty, 1 up, 2 down, 3 both; site 0 is the lowest digit).
 
-    The oracle keeps separate up / down strings; interleaving them (up -> bit 2i, down ->
-    bit 2i+1) must reproduce the paper's label."""
+    The digits of the paper's label give each site's up and down occupations.  On a model
+    with distinct on-site U_i and chemical potentials mu_i, the oracle must put
+    sum_i U_i n_i,up n_i,dn - mu_i n_i on the row of this configuration (row = dn * 2^N + up,
+    its documented full-basis order), and an up-spin hop between sites 2 and 3 must connect
+    that row to exactly one other: the configuration whose up electron moved from site 2 to
+    site 3, with element -t (no modes lie between the two in the order up 0..3, dn 0..3).
+    This pins the oracle's Hubbard diagonal, species assignment and row order against the
+    paper's example."""
     g = [int(x) for x in _golden("paper_examples.txt")["fermion_4ary"]]
-    digits, want = g[:4], g[4]  # sites 3, 2, 1, 0
-    up = dn = 0
-    for pos, d in zip((3, 2, 1, 0), digits):
-        up |= (d & 1) << pos
-        dn |= ((d >> 1) & 1) << pos
-    inter = 0
-    for i in range(4):
-        inter |= ((up >> i) & 1) << (2 * i) | ((dn >> i) & 1) << (2 * i + 1)
-    assert inter == want
+    label = g[4]
+    digits = [(label >> (2 * site)) & 3 for site in range(4)]  # base-4 digits, site 0 first
+    assert digits[::-1] == g[:4]                                 # the paper writes site 3 first
+    n, t = 4, 0.75
+    U = [1.0, 10.0, 100.0, 1000.0]
+    mu = [0.001, 0.003, 0.009, 0.027]
+    spec = wl.ModelSpec(kind=wl.HUBBARD, n_sites=n, onsite_U=list(enumerate(U)), chem_pot=list(enumerate(mu)),
+                        hops=[(3, 2, 0, t)])
+    want = sum(U[i] * (digits[i] == 3) - mu[i] * ((digits[i] & 1) + (digits[i] >> 1)) for i in range(n))
+    up = sum(((d & 1) << i) for i, d in enumerate(digits))
+    dn = sum((((d >> 1) & 1) << i) for i, d in enumerate(digits))
+    assert (up, dn) == (0b0101, 0b0011)
+    row = dn * (1 << n) + up
+    H = oracle.dense_H(spec)
+    assert abs(H[row, row].real - want) < 1e-12
+    col = H[:, row].copy()
+    col[row] = 0.0
+    moved = dn * (1 << n) + (up ^ 0b1100)
+    assert np.flatnonzero(np.abs(col) > 1e-15).tolist() == [moved]
+    assert abs(col[moved] - (-t)) < 1e-15
 
 
 # ----------------------------------------------------------------------------- spin H
@@ -358,3 +376,31 @@ def test_tpq_deferred_norm_identity():
     for l in (1.0, 1.5):
         u, h2, nrm = oracle.tpq(spec, psi0, 12, l)
         assert np.max(np.abs(nrm ** 2 - (l * l - 2.0 * l * u + h2))) < 1e-12
+
+
+# ----------------------------------------------------------------------------- sampled rows
+@pytest.mark.parametrize("name,mk", [
+    ("heisenberg_4x3_sz6", lambda: wl.heisenberg_square(4, 3).with_basis(wl.BASIS_SZ, 6)),
+    ("xxz_complex_sector", lambda: wl.random_xxz_model(11, 20, seed=8).with_basis(wl.BASIS_SZ, 5)),
+    ("kitaev_2x2_full", lambda: wl.kitaev_honeycomb(2, 2)),
+    ("hubbard_3x2_32", lambda: wl.hubbard_square(3, 2).with_basis(wl.BASIS_NUMBER, 3, 2)),
+    ("hubbard_random_complex", lambda: wl.random_hubbard_model(5, 10, seed=4).with_basis(wl.BASIS_NUMBER, 2, 3)),
+])
+@pytest.mark.parametrize("nvec", [1, 4])
+def test_apply_H_rows_philox_matches_full_product(name, mk, nvec):
+    """The sampled-row product behind the full-size GPU checks regenerates each element of v
+    from its Philox index: column c of a [dim][nvec] block is element r * nvec + c.  Rows of
+    it must equal the plain product H v on the same vector built from the generator's
+    element values (column c of the block, all rows)."""
+    spec = mk()
+    D = oracle.dim(spec)
+    cplx = spec.is_complex
+    seed = 4711 + nvec
+    rows = np.unique(np.concatenate([[0, D - 1], np.random.default_rng(3).integers(0, D, size=200)]))
+    for c in sorted({0, nvec - 1}):
+        v = oracle.gauss_at(seed, np.arange(D, dtype=np.uint64) * nvec + c, cplx)
+        full = oracle.apply_H(spec, v)
+        got = oracle.apply_H_rows_philox(spec, rows.astype(np.uint64), seed, cplx, nvec, c)
+        assert np.max(np.abs(got - full[rows])) <= 1e-13 * np.max(np.abs(full))
+        if not cplx:
+            assert np.max(np.abs(got.imag)) == 0.0
