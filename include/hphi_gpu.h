@@ -153,15 +153,40 @@ typedef struct {
   float best_ms;       /* H v time of the chosen configuration                                  */
   float default_ms;    /* H v time of the built-in default                                      */
   float worst_ms;      /* H v time of the slowest candidate                                     */
+  int best_split_L;    /* split-row spin path: chosen low-part length L (0: path not tuned)      */
+  int best_split_K;    /* split-row spin path: chosen rows per shared-memory tile                */
 } hphi_tune_result;
 
 /* Times the launch configurations of the model's H v at precision prec (HPHI_FP64 or
  * HPHI_FP32) on a seeded vector and keeps the fastest for every later hphi_apply_H /
  * hphi_lanczos_run / hphi_tpq_run on this model.  Today the two-pass Hubbard path is tuned
  * (columns per thread of the down-spin pass x rows per tile of the up-spin pass); other
- * models report n_candidates = 0.  Uses the model's workspace; synchronises the stream.
- * *out may be NULL.  No counterpart in the paper (its CPU code has no launch shapes). */
+ * models report n_candidates = 0.  Real spin models in an S^z sector that take the
+ * split-row path (see hphi_set_sector_split) are tuned over the split: the default low part
+ * and up to two bits fewer, each with every tile height that fits.  Uses the model's
+ * workspace; synchronises the stream.  *out may be NULL.  No counterpart in the paper (its
+ * CPU code has no launch shapes). */
 int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream);
+
+/* Split-row H v of real spin models in an S^z sector, section 3.1's split of a configuration
+ * into a high and a low part (the split-half search) turned into the data layout: the rows
+ * of one high part are contiguous, K of them are staged in shared memory, exchange bonds
+ * inside the low part act in the staged rows, bonds inside the high part add whole rows
+ * (one stripe-ordered pass through L2), and the few bonds that straddle the split gather
+ * from one partner row each.  It applies to one real vector (nvec = 1) when every exchange
+ * term flips two antiparallel spins with one real element and the diagonal has at most two
+ * coefficient groups beyond a constant (Heisenberg, XXZ and J1-J2 models on regular lattices);
+ * fp64 also needs the exchange couplings to be small integer multiples of one power of two.
+ * Other models use the generic gather kernel.  This call chooses the split used for prec:
+ * L = -1 turns the path off (generic kernel), L = 0 restores the default (the largest low
+ * part whose rows fit one shared-memory tile), 1..20 forces the low part's length; K = 0
+ * picks the widest tile that fits, 1/2/4/8 forces the rows per tile.  The device tables of
+ * the split are built here (a host loop over 2^L low and 2^(N-L) high parts, then an upload
+ * on `stream`, which is synchronised).  Results agree with the generic kernel to rounding
+ * (fp32) or exactly up to the final conversion (fp64 fixed-point sums).  Returns
+ * HPHI_ERR_UNSUPPORTED (with the reason) for a model the path does not cover and
+ * HPHI_ERR_INVALID_ARG when the forced split does not fit.  No counterpart in the paper. */
+int hphi_set_sector_split(hphi_model* m, int prec, int L, int K, void* stream);
 
 /* Window passes of the many-vector H v (full-basis spin models, nvec in {32, 64, 128, 256}):
  * section 4.3's continuous-memory-access idea on one GPU.  Each pass takes the terms whose

@@ -29,7 +29,7 @@ EXPORTS = [
     "hphi_add_hopping", "hphi_add_onsite_U", "hphi_add_density", "hphi_add_chemical_potential", "hphi_set_basis",
     "hphi_build_sector", "hphi_dim", "hphi_is_complex", "hphi_basis_states", "hphi_basis_ranks", "hphi_apply_H",
     "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run", "hphi_apply_H_noalloc",
-    "hphi_lanczos_run_sectors", "hphi_autotune", "hphi_set_window_bits",
+    "hphi_lanczos_run_sectors", "hphi_autotune", "hphi_set_window_bits", "hphi_set_sector_split",
 ]
 
 
@@ -54,7 +54,8 @@ class LanczosResult(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int), ("best_dn_ept", ctypes.c_int), ("best_up_k", ctypes.c_int),
-                ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float), ("worst_ms", ctypes.c_float)]
+                ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float), ("worst_ms", ctypes.c_float),
+                ("best_split_L", ctypes.c_int), ("best_split_K", ctypes.c_int)]
 
 
 class TpqParams(ctypes.Structure):
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = True):
         L.hphi_tpq_run.argtypes = [P, ctypes.POINTER(TpqParams), ctypes.POINTER(TpqResult), P]
         L.hphi_autotune.argtypes = [P, I, ctypes.POINTER(TuneResult), P]
         L.hphi_set_window_bits.argtypes = [P, I]
+        L.hphi_set_sector_split.argtypes = [P, I, I, I, P]
         L.hphi_lanczos_run_sectors.argtypes = [P, P, I, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         _lib = L
         return L
@@ -260,7 +262,13 @@ class Model:
         r = TuneResult()
         self._check(self._L.hphi_autotune(self._h, prec, ctypes.byref(r), _stream()))
         return dict(n_candidates=r.n_candidates, dn_ept=r.best_dn_ept, up_k=r.best_up_k, best_ms=r.best_ms,
-                    default_ms=r.default_ms, worst_ms=r.worst_ms)
+                    default_ms=r.default_ms, worst_ms=r.worst_ms, split_L=r.best_split_L, split_K=r.best_split_K)
+
+    def set_sector_split(self, prec=FP64, L: int = 0, K: int = 0):
+        """Split-row spin path (see hphi_set_sector_split): L = -1 off, 0 default, else the low
+        part's length; K = 0 widest tile, else rows per tile."""
+        _torch()
+        self._check(self._L.hphi_set_sector_split(self._h, prec, int(L), int(K), _stream()))
 
     def set_window_bits(self, bits: int):
         """Window passes of the many-vector H v: 0 automatic, -1 off, else the window's sites."""

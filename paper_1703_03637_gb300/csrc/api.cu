@@ -130,6 +130,14 @@ struct hphi_model {
     hphi::BatchPlan plan;
   };
   std::map<int, std::unique_ptr<WinCache>> win;
+  // split-row path of real S^z-sector spin models: the compiled terms, whether each precision
+  // may take the path, the split asked for per precision (-1 off, 0 default, else L) and
+  // rows per tile (0 default), and the device tables built so far by (L, K)
+  hphi::SecTerms sec_terms;
+  bool sec_ok[2] = {false, false};
+  std::string sec_why;
+  int sec_L[2] = {0, 0}, sec_K[2] = {0, 0};
+  std::map<std::pair<int, int>, std::unique_ptr<hphi::SecTables, hphi::SecTablesDeleter>> sec_tab;
 };
 
 namespace {
@@ -340,6 +348,20 @@ hphi::Status compile_spin(hphi_model* m, cudaStream_t st) {
   d.pairs = m->d_pairs.as<hphi::PairEntry>();
   d.pair_coef = m->d_pcoef.as<double>();
   m->cplx_model = cplx_model;
+  m->sec_terms = hphi::SecTerms{};
+  m->sec_tab.clear();
+  m->sec_ok[0] = m->sec_ok[1] = false;
+  if (sector && !cplx_model) {
+    hphi::SecTerms& t = m->sec_terms;
+    t.n_sites = N;
+    t.n_ones = m->a;
+    t.ents = ents;
+    t.cls = cls;
+    t.c0 = c0;
+    t.lin = lg;
+    t.pairs = pe;
+    t.pcoef = pc;
+  }
   return {};
 }
 
@@ -497,6 +519,52 @@ hphi::Status build_hub_fast(hphi_model* m, cudaStream_t st) {
   return {};
 }
 
+// ------------------------------------------------------------------ split-row spin path
+// The split (L, K) precision prec runs with: the one asked for, else the default (largest
+// low part whose rows fit one tile, widest tile that fits); (0, 0) when the path is off.
+std::pair<int, int> sec_shape(const hphi_model* m, int prec) {
+  const int pi = prec == HPHI_FP64 ? 0 : 1;
+  if (!m->sec_ok[pi] || m->sec_L[pi] < 0) return {0, 0};
+  const int esz = prec == HPHI_FP64 ? 8 : 4;
+  const int L = m->sec_L[pi] > 0 ? m->sec_L[pi] : hphi::sec_default_L(m->sec_terms, esz);
+  if (L <= 0) return {0, 0};
+  const int K = m->sec_K[pi] > 0 ? m->sec_K[pi] : hphi::sec_default_K(m->sec_terms, L, esz);
+  return {L, K};
+}
+
+// Builds (once) the tables of the shape prec runs with.  Never called inside a stream capture.
+hphi::Status sec_ensure(hphi_model* m, int prec, cudaStream_t st) {
+  const std::pair<int, int> sh = sec_shape(m, prec);
+  if (sh.first == 0 || m->sec_tab.count(sh)) return {};
+  hphi::SecTables* t = nullptr;
+  hphi::Status s = hphi::sec_build(m->sec_terms, sh.first, sh.second, &t, st);
+  if (s.code) return s;
+  m->sec_tab[sh].reset(t);
+  return {};
+}
+
+// Tables of the shape prec runs with, or null (path off, not applicable, or not built).
+const hphi::SecDev* sec_find(hphi_model* m, int prec) {
+  auto it = m->sec_tab.find(sec_shape(m, prec));
+  return it == m->sec_tab.end() ? nullptr : &hphi::sec_dev(it->second.get());
+}
+
+hphi::Status sec_prepare(hphi_model* m, cudaStream_t st) {
+  m->sec_why.clear();
+  if (m->basis != HPHI_BASIS_SZ || m->cplx_model) {
+    m->sec_why = "split-row path: real models in an S^z sector only";
+    return {};
+  }
+  for (int prec : {HPHI_FP64, HPHI_FP32}) {
+    std::string why;
+    m->sec_ok[prec == HPHI_FP64 ? 0 : 1] = hphi::sec_applicable(m->sec_terms, prec, &why);
+    if (!why.empty()) m->sec_why = why;
+    hphi::Status s = sec_ensure(m, prec, st);
+    if (s.code) return s;
+  }
+  return {};
+}
+
 hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
   HPHI_CUDA_TRY(cudaGetDevice(&m->device));
   hphi::Status s;
@@ -525,6 +593,7 @@ hphi::Status build_sector_impl(hphi_model* m, cudaStream_t st) {
     }
     d.counter = m->d_counter.as<unsigned long long>();
     m->dim = d.dim;
+    if ((s = sec_prepare(m, st)).code) return s;
   } else {
     if ((s = compile_hub(m, st)).code) return s;
     hphi::HubDev& d = m->hdev;
@@ -578,6 +647,14 @@ bool use_hub_fast(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
 
 bool use_batch(hphi_model* m, int nvec) { return m->kind == HPHI_SPIN_HALF && hphi::batch_applies(m->sdev, nvec); }
 
+// Split-row tables when the split-row path applies to this launch (one real vector of an
+// S^z-sector spin model), else null.  The path also needs its scratch (sec_scratch_bytes).
+const hphi::SecDev* use_sec(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
+  if (m->kind != HPHI_SPIN_HALF || nvec != 1 || m->cplx_model) return nullptr;
+  if (epi == hphi::Epi::kRefine && prec != HPHI_FP64) return nullptr;
+  return sec_find(m, prec);
+}
+
 // Window plan of the batched-row kernel for nvec vectors in precision prec, or null for one
 // pass in natural row order (windows off, one window holds every term, or no plan found).
 // Built on first use for each window size and kept until the terms change.
@@ -612,6 +689,9 @@ const hphi::BatchPlan* batch_plan(hphi_model* m, int prec, int nvec) {
 // kernels one hv_launch runs (for the launch counts the results report)
 int hv_kernels(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
   if (use_hub_fast(m, prec, nvec, epi)) return prec == HPHI_FP64 ? 4 : 2;  // (max-exponent, quantise,) D, U
+  if (use_sec(m, prec, nvec, epi) && m->ws.work.p != nullptr &&
+      m->ws.work.bytes >= hphi::sec_scratch_bytes(*use_sec(m, prec, nvec, epi), prec, epi))
+    return prec == HPHI_FP64 ? 4 : 2;  // (max-exponent, quantise,) pass H, pass R
   if (use_batch(m, nvec)) {
     const hphi::BatchPlan* plan = epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec);
     const int passes = plan ? plan->n_pass : 1;
@@ -628,6 +708,7 @@ int hv_kernels(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
 // scratch an H v launch needs beyond its vectors (0: none)
 size_t hv_scratch_bytes(hphi_model* m, int prec, int nvec, hphi::Epi epi) {
   if (use_hub_fast(m, prec, nvec, epi)) return hphi::hub_scratch_bytes(m->hdev, prec, epi);
+  if (const hphi::SecDev* sd = use_sec(m, prec, nvec, epi)) return hphi::sec_scratch_bytes(*sd, prec, epi);
   if (use_batch(m, nvec))
     return hphi::batch_scratch_bytes(m->sdev, epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec), prec,
                                      m->cplx_model, nvec);
@@ -646,8 +727,19 @@ void* optional_scratch(hphi_model* m, size_t need) {
   return m->ws.work.p;
 }
 
+// true when the split-row kernels run this launch: they apply and `scratch_bytes` of scratch
+// (the workspace buffer) hold what they need
+bool sec_runs(hphi_model* m, int prec, int nvec, hphi::Epi epi, size_t scratch_bytes) {
+  const hphi::SecDev* sd = use_sec(m, prec, nvec, epi);
+  return sd != nullptr && scratch_bytes >= hphi::sec_scratch_bytes(*sd, prec, epi);
+}
+
 int hv_grid_for(hphi_model* m, int nvec, int prec, hphi::Epi epi) {
   if (use_hub_fast(m, prec, nvec, epi)) return hphi::hub_up_grid(m->hdev, prec, epi);
+  if (const hphi::SecDev* sd = use_sec(m, prec, nvec, epi)) {
+    if (m->ws.work.p != nullptr && m->ws.work.bytes >= hphi::sec_scratch_bytes(*sd, prec, epi))
+      return hphi::sec_grid(*sd, prec, epi);
+  }
   if (use_batch(m, nvec)) return hphi::batch_grid(prec, m->cplx_model, nvec, epi, m->dim);
   const bool hub = m->kind == HPHI_HUBBARD;
   const int64_t cap = hphi::hv_resident_grid(hub, prec, m->cplx_model, epi);
@@ -665,6 +757,8 @@ hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec
                        const hphi::FusedArgs& fa, int grid, void* scratch, cudaStream_t st) {
   if (use_hub_fast(m, prec, nvec, epi) && (hphi::hub_scratch_bytes(m->hdev, prec, epi) == 0 || scratch != nullptr))
     return hphi::launch_hub_fast(m->hdev, prec, v, w, scratch, epi, fa, grid, st);
+  if (scratch != nullptr && scratch == m->ws.work.p && sec_runs(m, prec, nvec, epi, m->ws.work.bytes))
+    return hphi::launch_sec(*use_sec(m, prec, nvec, epi), prec, v, w, scratch, epi, fa, grid, st);
   if (use_batch(m, nvec) && hphi::batch_aligned(v, w)) {
     const hphi::BatchPlan* plan = epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec);
     if (scratch != nullptr || hphi::batch_scratch_bytes(m->sdev, plan, prec, m->cplx_model, nvec) == 0)
@@ -680,6 +774,90 @@ hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec
                  : nullptr;
   return hphi::launch_hv(m->kind == HPHI_HUBBARD, dev_model(m), prec, m->cplx_model, v, w, nvec, epi, fa, grid, sp,
                          st);
+}
+
+// Times one plain H v of the split-row path for every candidate split (L, K) -- the default
+// low part and one or two bits fewer, each with every tile height that fits -- and keeps the
+// fastest for precision prec.  Tables of the losing candidates are freed.
+hphi::Status sec_autotune(hphi_model* m, int prec, hphi_tune_result* res, cudaStream_t st) {
+  const int pi = prec == HPHI_FP64 ? 0 : 1;
+  const int esz = prec == HPHI_FP64 ? 8 : 4;
+  const int saved_L = m->sec_L[pi], saved_K = m->sec_K[pi];
+  const int L0 = hphi::sec_default_L(m->sec_terms, esz);
+  if (L0 <= 0) return {};
+  std::vector<std::pair<int, int>> cand;
+  for (int L = L0; L >= std::max(1, L0 - 2); --L) {
+    if (m->n_sites - L > hphi::kSecMaxH) break;
+    const int kmax = hphi::sec_default_K(m->sec_terms, L, esz);
+    for (int K = 1; K <= kmax; K *= 2) cand.emplace_back(L, K);
+  }
+  hphi::Status s;
+  if ((s = m->ws.vecA.ensure((size_t)esz * (size_t)m->dim)).code) return s;
+  if ((s = m->ws.vecB.ensure((size_t)esz * (size_t)m->dim)).code) return s;
+  if ((s = hphi::launch_random(m->ws.vecA.p, m->dim, false, prec == HPHI_FP64, 7, st)).code) return s;
+  struct Ev {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Ev() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } tm;
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
+  const std::pair<int, int> dflt = sec_shape(m, prec);
+  float best = 1e30f, worst = 0.f, dms = 0.f;
+  std::pair<int, int> best_sh = dflt;
+  hphi::FusedArgs fa;
+  for (const auto& sh : cand) {
+    m->sec_L[pi] = sh.first;
+    m->sec_K[pi] = sh.second;
+    if ((s = sec_ensure(m, prec, st)).code) {
+      if (s.code != HPHI_ERR_OUT_OF_MEMORY) break;
+      s = {};
+      continue;  // a candidate whose tables do not fit is skipped
+    }
+    const size_t need = hv_scratch_bytes(m, prec, 1, hphi::Epi::kStore);
+    if ((s = m->ws.work.ensure(need)).code) break;
+    const int grid = hv_grid_for(m, 1, prec, hphi::Epi::kStore);
+    s = hv_launch(m, prec, m->ws.vecA.p, m->ws.vecB.p, 1, hphi::Epi::kStore, fa, grid, m->ws.work.p, st);
+    if (s.code) break;
+    HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
+    for (int rep = 0; rep < 2 && !s.code; ++rep)
+      s = hv_launch(m, prec, m->ws.vecA.p, m->ws.vecB.p, 1, hphi::Epi::kStore, fa, grid, m->ws.work.p, st);
+    HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
+    if (s.code) break;
+    HPHI_CUDA_TRY(cudaEventSynchronize(tm.b));
+    float ms = 0.f;
+    HPHI_CUDA_TRY(cudaEventElapsedTime(&ms, tm.a, tm.b));
+    ms /= 2.f;
+    ++res->n_candidates;
+    if (sh == dflt) dms = ms;
+    worst = std::max(worst, ms);
+    if (ms < best) {
+      best = ms;
+      best_sh = sh;
+    }
+    // keep only the tables of this precision's default and best so far, and of the shape the
+    // other precision runs with
+    const std::pair<int, int> other = sec_shape(m, pi == 0 ? HPHI_FP32 : HPHI_FP64);
+    for (auto it = m->sec_tab.begin(); it != m->sec_tab.end();) {
+      if (it->first != dflt && it->first != best_sh && it->first != other) it = m->sec_tab.erase(it);
+      else ++it;
+    }
+  }
+  if (s.code) {
+    m->sec_L[pi] = saved_L;
+    m->sec_K[pi] = saved_K;
+    return s;
+  }
+  m->sec_L[pi] = best_sh.first;
+  m->sec_K[pi] = best_sh.second;
+  res->best_split_L = best_sh.first;
+  res->best_split_K = best_sh.second;
+  res->best_ms = best;
+  res->default_ms = dms;
+  res->worst_ms = worst;
+  return sec_ensure(m, prec, st);
 }
 
 }  // namespace
@@ -871,11 +1049,52 @@ int hphi_set_window_bits(hphi_model* m, int bits) {
   return HPHI_OK;
 }
 
+int hphi_set_sector_split(hphi_model* m, int prec, int L, int K, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (prec != HPHI_FP64 && prec != HPHI_FP32) return fail(m, HPHI_ERR_INVALID_ARG, "set_sector_split: prec FP64 or FP32");
+  if (L < -1 || L > hphi::kSecMaxL || K < 0 || K > 8 || (K & (K - 1)))
+    return fail(m, HPHI_ERR_INVALID_ARG, "set_sector_split: L in -1..20, K in {0, 1, 2, 4, 8}");
+  const int pi = prec == HPHI_FP64 ? 0 : 1;
+  if (L >= 0 && !m->sec_ok[pi])
+    return fail(m, HPHI_ERR_UNSUPPORTED,
+                m->sec_why.empty() ? std::string("set_sector_split: the model does not take the split-row path")
+                                   : m->sec_why);
+  const int oldL = m->sec_L[pi], oldK = m->sec_K[pi];
+  m->sec_L[pi] = L;
+  m->sec_K[pi] = L < 0 ? 0 : K;
+  if (L >= 0) {
+    const int esz = prec == HPHI_FP64 ? 8 : 4;
+    const std::pair<int, int> sh = sec_shape(m, prec);
+    if (sh.first == 0 || !hphi::sec_fits(m->sec_terms, sh.first, sh.second, esz)) {
+      m->sec_L[pi] = oldL;
+      m->sec_K[pi] = oldK;
+      return fail(m, HPHI_ERR_INVALID_ARG,
+                  "set_sector_split: the high part must have 1..22 bits and K rows of the longest row must fit one "
+                  "shared-memory tile");
+    }
+    hphi::Status s = sec_ensure(m, prec, (cudaStream_t)stream);
+    if (s.code) {
+      m->sec_L[pi] = oldL;
+      m->sec_K[pi] = oldK;
+      return fail(m, s);
+    }
+  }
+  return HPHI_OK;
+}
+
 int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream) {
   int rc = check_built(m);
   if (rc) return rc;
   if (prec != HPHI_FP64 && prec != HPHI_FP32) return fail(m, HPHI_ERR_INVALID_ARG, "autotune: prec FP64 or FP32");
   hphi_tune_result res{};
+  if (m->kind == HPHI_SPIN_HALF && m->sec_ok[prec == HPHI_FP64 ? 0 : 1] && m->sec_L[prec == HPHI_FP64 ? 0 : 1] >= 0 &&
+      !m->cplx_model) {
+    hphi::Status s = sec_autotune(m, prec, &res, (cudaStream_t)stream);
+    if (s.code) return fail(m, s);
+    if (out) *out = res;
+    return HPHI_OK;
+  }
   if (!use_hub_fast(m, prec, 1, hphi::Epi::kStore)) {
     if (out) *out = res;
     return HPHI_OK;
@@ -1032,10 +1251,6 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (L.cplx ? 2 : 1);
   L.n_real = m->dim * (L.cplx ? 2 : 1);
   const size_t vbytes = esz * (size_t)m->dim;
-  L.grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
-  L.rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);
-  L.vgrid = launch_grid(L.n_real);
-  const int pgrid = std::max(std::max(L.grid, L.rgrid), L.vgrid);
   Workspace& ws = m->ws;
   hphi::Status s;
   // the refinement's fp64 H x reuses buffer A, which must then hold an fp64 vector
@@ -1064,12 +1279,26 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
     if ((s = ws.work.ensure(need)).code) return s;
     L.scratch = ws.work.p;
   } else if (m->kind == HPHI_SPIN_HALF) {
-    // fp64 spin H v gathers from a quantised copy (one more vector); without the memory the
-    // per-term fixed-point sums run instead
-    size_t need = hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, 1);
-    if (L.refine) need = std::max(need, hphi::spin_scratch_bytes(m->sdev, HPHI_FP64, m->cplx_model, 1));
+    // split-row kernels (S^z sectors of real models): their scratch (fp64: the quantised copy;
+    // Lanczos: one more vector for the high-part sums); generic fp64 kernels gather from a
+    // quantised copy.  Without the memory the generic kernels' per-term sums run instead.
+    size_t need = std::max(hv_scratch_bytes(m, prec, 1, hphi::Epi::kLanczos1),
+                           hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, 1));
+    if (L.refine)
+      need = std::max(need, std::max(hv_scratch_bytes(m, HPHI_FP64, 1, hphi::Epi::kRefine),
+                                     hphi::spin_scratch_bytes(m->sdev, HPHI_FP64, m->cplx_model, 1)));
     L.scratch = optional_scratch(m, need);
+    if (L.scratch == nullptr) {
+      size_t gen = hphi::spin_scratch_bytes(m->sdev, prec, m->cplx_model, 1);
+      if (L.refine) gen = std::max(gen, hphi::spin_scratch_bytes(m->sdev, HPHI_FP64, m->cplx_model, 1));
+      L.scratch = optional_scratch(m, gen);
+    }
   }
+  // grids after the scratch: the split-row kernels run only when it holds what they need
+  L.grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
+  L.rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);
+  L.vgrid = launch_grid(L.n_real);
+  const int pgrid = std::max(std::max(L.grid, L.rgrid), L.vgrid);
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * hphi::kMaxRedQ)).code) return s;
   L.partials = ws.partials.as<double>();
   // scalars: alpha[m], beta[m], sig[m+1], coef[m], s[16], tri[16 + 5m], done, steps_done
@@ -1118,9 +1347,13 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   };
   // fp64 two-pass Hubbard: pass 2 also finds the next vector's largest exponent, so the next
   // step's H v skips its own max-exponent scan
-  int* emax = (prec == HPHI_FP64 && L.scratch != nullptr && use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1))
-                  ? hphi::hub_exponent_slot(m->hdev, L.scratch)
-                  : nullptr;
+  int* emax = nullptr;
+  if (prec == HPHI_FP64 && L.scratch != nullptr) {
+    if (use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1)) emax = hphi::hub_exponent_slot(m->hdev, L.scratch);
+    else if (sec_runs(m, prec, 1, hphi::Epi::kLanczos1, ws.work.bytes))
+      emax = hphi::sec_exponent_slot(*use_sec(m, prec, 1, hphi::Epi::kLanczos1), prec, hphi::Epi::kLanczos1,
+                                     L.scratch);
+  }
   auto run_pass = [&](bool with_x) -> hphi::Status {
     hphi::Status q;
     L.launches += 2 + (3 + hv_kernels(m, prec, 1, hphi::Epi::kLanczos1)) * steps - (emax ? steps - 1 : 0);
@@ -1364,17 +1597,17 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   const bool cplx = m->cplx_model;
   const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (cplx ? 2 : 1);
   const size_t vbytes = esz * (size_t)m->dim * nvec;
-  const int grid = hv_grid_for(m, nvec, prec, hphi::Epi::kTpq);
-  const int vgrid = launch_grid(m->dim * nvec);
-  const int pgrid = std::max(grid, vgrid);
   Workspace& ws = m->ws;
   hphi::Status s;
   if ((s = ws.vecA.ensure(vbytes)).code) return s;
   if ((s = ws.vecB.ensure(vbytes)).code) return s;
-  if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * nvec * hphi::kMaxRedQ)).code) return s;
   const size_t tneed = hv_scratch_bytes(m, prec, nvec, hphi::Epi::kTpq);
   if (tneed && (s = ws.work.ensure(tneed)).code) return s;
   void* tscratch = tneed ? ws.work.p : nullptr;
+  const int grid = hv_grid_for(m, nvec, prec, hphi::Epi::kTpq);
+  const int vgrid = launch_grid(m->dim * nvec);
+  const int pgrid = std::max(grid, vgrid);
+  if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * nvec * hphi::kMaxRedQ)).code) return s;
   const size_t nsc = 2 * (size_t)nvec + 3 * (size_t)K * nvec;
   if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;
   hphi::TpqDev tq;

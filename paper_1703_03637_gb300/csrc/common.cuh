@@ -116,6 +116,76 @@ struct HubDev {
   const uint8_t* npos_dn;
 };
 
+// Split-row view of a fixed-S^z sector (section 3.1's split of a configuration into a high
+// and a low part, used as the data layout of H v): s = (hi << L) | lo.  The rows with one
+// value of hi are contiguous in the vector (ascending order sorts by hi first), start at
+// hi_off[hi] and hold the C(L, q) low parts of popcount q = n_ones - popcount(hi).
+// Exchange bonds fall into three groups: both sites low (act inside a row), both high (add
+// whole rows), one of each ("straddling": row hi ^ 2^a, low part lo ^ 2^b).
+constexpr int kSecMaxCls = 8;    // distinct exchange coefficients
+constexpr int kSecMaxStr = 24;   // straddling exchange bonds
+constexpr int kSecMaxStrSites = 16;  // distinct low sites of straddling bonds
+constexpr int kSecMaxSp = 24;    // straddling S^z S^z pairs
+constexpr int kSecMaxSl = 8;     // layers of straddling pairs
+constexpr int kSecMaxL = 20;
+constexpr int kSecMaxH = 22;
+constexpr int kSecDtab = 2048;   // diagonal table entries
+
+struct SecDev {
+  int L, H, n_ones;
+  int64_t dim;
+  int K;                        // rows per tile of the row pass
+  int nq_max;                   // longest row present
+  // coefficients: exchange class c has coef[c]; the fp64 path sums integer multiples
+  // mult[c] of one unit (coef[c] = mult[c] * unit) and scales once
+  int n_cls;
+  int one_cls;                  // every exchange bond has the same coefficient
+  double coef[kSecMaxCls];
+  int mult[kSecMaxCls];
+  double unit;
+  int qextra;                   // extra headroom bits of the quantised copy
+  // low side
+  // low-part tables cover the classes present: entry j - jbase for list position j, nJ of them
+  uint32_t lo_off[kSecMaxL + 2];     // start of popcount class q in the list of all 2^L low parts
+  uint32_t jbase, nJ;
+  const uint32_t* lo_list;      // [nJ] low parts grouped by popcount, ascending
+  int lo_slots;                 // slots of the low neighbour table
+  const uint16_t* lo_nbr;       // [lo_slots][nJ] rank (in its class) of the q-th neighbour
+  const uint8_t* lo_cnt;        // [nJ] neighbours; entries are class-sorted
+  const uint8_t* lo_cls;        // [lo_slots][nJ] class of the q-th neighbour (multi-class only)
+  const uint16_t* lo_diag;      // [nJ] packed diagonal counts of the low part
+  // high side
+  const uint64_t* hi_off;       // [2^H] first row element of each high part
+  int hi_slots;
+  const uint32_t* hi_nbr;       // [hi_slots][2^H] neighbour high part | class << 24
+  const uint8_t* hi_cnt;        // [2^H]
+  const uint16_t* hi_diag;      // [2^H] packed diagonal counts of the high part
+  // straddling exchange: high bit a, low bit b, class, index of b's rank table
+  int n_str;
+  uint8_t str_a[kSecMaxStr], str_b[kSecMaxStr], str_cls[kSecMaxStr], str_t[kSecMaxStr];
+  const uint16_t* str_rank;     // [sites][nJ] rank (in its class) of lo ^ 2^b
+  // straddling S^z S^z pairs: high bit a, low bit b, layer l.  Pairs of one layer have
+  // distinct low bits, so per row the pairs whose high bit is set give one mask of low bits
+  // per layer and the count is a popcount per layer; layer l counts into diagonal field sp_lg[l]
+  int n_sp, n_sl;
+  uint8_t sp_a[kSecMaxSp], sp_b[kSecMaxSp], sp_l[kSecMaxSp];
+  uint8_t sp_lg[kSecMaxSl];
+  // diagonal = dtab[n0 + d1 * n1] with n_g the packed counts (field g: 8 bits)
+  int n_dg;                     // diagonal count groups (0, 1 or 2)
+  int dstride;                  // d1
+  int dtab_n;
+  const double* dtab;           // [dtab_n]
+  // row pass work: tiles of up to K rows of one class, in processing order
+  int64_t n_tiles;
+  const uint32_t* hi_seq;       // [2^H] high parts in processing order
+  const uint32_t* tiles;        // [n_tiles] start in hi_seq | (rows - 1) << 24
+  // high pass work: classes p ascending, stripes, rows of class p
+  int n_pc;                     // classes present
+  int pc_p[kSecMaxH + 1];       // popcount of each class present
+  uint32_t pc_row0[kSecMaxH + 2];   // start of the class in hi_cls
+  const uint32_t* hi_cls;       // [2^H] high parts grouped by popcount, ascending
+};
+
 // ------------------------------------------------------------------ scalar traits
 template <class T> struct Cx { T x, y; };
 
@@ -230,6 +300,44 @@ size_t batch_scratch_bytes(const SpinDev& md, const BatchPlan* plan, int prec, b
 int batch_grid(int prec, bool cplx, int nvec, Epi epi, int64_t dim);
 Status launch_batch(const SpinDev& md, const BatchPlan* plan, int prec, bool cplx, const void* v, void* w,
                     void* scratch, int nvec, Epi epi, const FusedArgs& fa, int grid, cudaStream_t st);
+
+// fp64 -> 64-bit fixed point at one scale per vector (k_hub.cu): q = round(x 2^(1078 - E - extra)),
+// E the largest exponent field of x (computed into *Ep unless exp_ready), |q| < 2^(56 - extra)
+Status launch_quant_vec(const double* X, long long* Q, int64_t n, int* Ep, const int* done, bool exp_ready, int extra,
+                        cudaStream_t st);
+
+// Split-row spin-sector H v (k_sector.cu) ---------------------------------------------
+// The compiled terms of a real S^z-sector spin model, as the term compiler produced them.
+struct SecTerms {
+  int n_sites = 0, n_ones = 0;
+  std::vector<SpinEntry> ents;
+  std::vector<double2> cls;
+  double c0 = 0.0;
+  std::vector<LinGroup> lin;
+  std::vector<PairEntry> pairs;
+  std::vector<double> pcoef;
+};
+struct SecTables;  // device tables of one split (L, K); defined in k_sector.cu
+void sec_free(SecTables* t);
+struct SecTablesDeleter {
+  void operator()(SecTables* t) const { sec_free(t); }
+};
+// true when the model takes the split-row path (empty *why), else the reason
+bool sec_applicable(const SecTerms& t, int prec, std::string* why);
+// the split used when nothing else is asked: the largest L whose longest row fits one tile
+// of K = 1 rows of element size esz (0: none fits)
+int sec_default_L(const SecTerms& t, int esz);
+// tile rows K for low-part length L at element size esz (largest power of two that fits)
+int sec_default_K(const SecTerms& t, int L, int esz);
+// K rows of the longest row of split L fit one tile at element size esz
+bool sec_fits(const SecTerms& t, int L, int K, int esz);
+Status sec_build(const SecTerms& t, int L, int K, SecTables** out, cudaStream_t st);
+const SecDev& sec_dev(const SecTables* t);
+size_t sec_scratch_bytes(const SecDev& d, int prec, Epi epi);
+int sec_grid(const SecDev& d, int prec, Epi epi);
+int* sec_exponent_slot(const SecDev& d, int prec, Epi epi, void* scratch);
+Status launch_sec(const SecDev& d, int prec, const void* v, void* w, void* scratch, Epi epi, const FusedArgs& fa,
+                  int grid, cudaStream_t st);
 
 // Streaming vector kernels and finalisers (k_solver.cu) -------------------------------
 struct LzDev {           // device scalars of one Lanczos run

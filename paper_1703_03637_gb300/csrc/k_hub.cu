@@ -373,10 +373,12 @@ __global__ void __launch_bounds__(kThreads) k_maxexp(const double* __restrict__ 
   if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(E, mx);
 }
 
+// extra: headroom bits; q = round(x 2^(1078 - E - extra)), |q| < 2^(56 - extra)
 __global__ void __launch_bounds__(kThreads) k_quant(const double* __restrict__ X, long long* __restrict__ Q, int64_t n,
-                                                     const int* __restrict__ Ep, const int* __restrict__ done) {
+                                                     const int* __restrict__ Ep, const int* __restrict__ done,
+                                                     int extra) {
   if (done != nullptr && *done) return;
-  const int E = *Ep;
+  const int E = *Ep + extra;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
     const double x = __ldg(X + i);
     const int hi = __double2hiint(x);
@@ -657,7 +659,7 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
     k_maxexp<<<gv, kThreads, 0, st>>>(X, md.dim, Ep, fa.done);
     HPHI_CUDA_TRY(cudaGetLastError());
   }
-  k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done);
+  k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done, 0);
   HPHI_CUDA_TRY(cudaGetLastError());
   Status sd = launch_dn<long long>(md, Q, WQ, fa.done, counter, st);
   if (sd.code) return sd;
@@ -777,6 +779,19 @@ Status launch_hub_store_noalloc(const HubDev& md0, const void* v, void* w, cudaS
   if (s.code) return s;
   FusedArgs fa;  // plain H v: no reductions, no breakdown flag
   return launch_q<Epi::kStore>(md, v, w, scratch, fa, upq_grid(md, Epi::kStore), st);
+}
+
+Status launch_quant_vec(const double* X, long long* Q, int64_t n, int* Ep, const int* done, bool exp_ready, int extra,
+                        cudaStream_t st) {
+  const int gv = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)num_sms() * 8));
+  if (!exp_ready) {
+    HPHI_CUDA_TRY(cudaMemsetAsync(Ep, 0, sizeof(int), st));
+    k_maxexp<<<gv, kThreads, 0, st>>>(X, n, Ep, done);
+    HPHI_CUDA_TRY(cudaGetLastError());
+  }
+  k_quant<<<gv, kThreads, 0, st>>>(X, Q, n, Ep, done, extra);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
 }
 
 Status build_hub_neighbours(const HubDev& md, int species, uint32_t* nbr, uint8_t* deg, uint8_t* npos,

@@ -610,10 +610,14 @@ def test_apply_H_wide_dynamic_range(name, mk, nvec):
     """Inputs spanning 30 decades (Gaussian x 10^-U(0,30)), like late mTPQ states or converged
     Lanczos vectors.  The fp64 paths round the input once onto a 64-bit fixed-point grid (one
     scale per vector column, step <= 2^-56 max|x|), so a small output element is accurate to
-    an absolute, not a relative, bound.  Per element r the test checks
-        fp64: |w_r - (Hx)_r| <= ||H_r||_1 max|x| 2^-55 + 2^-50 (|H| |x|)_r
-        fp32: |w_r - (Hx32)_r| <= (n_r + 4) 2^-24 (|H| |x32|)_r   (n_r terms in row r)
-    with the exact product taken from the oracle's dense matrix."""
+    an absolute, not a relative, bound.  The diagonal element is evaluated as a sum of its
+    coefficient terms (constant, per-site and per-pair parts), whose rounding scales with
+    D = sum of |those terms| rather than with |H_rr| when they cancel.  Per element r:
+        fp64: |w_r - (Hx)_r| <= ||H_r||_1 max|x| 2^-55 + 2^-50 ((|H| |x|)_r + D |x_r|)
+        fp32: |w_r - (Hx32)_r| <= (n_r + 4) 2^-24 (|H| |x32|)_r + n_D 2^-24 D |x32_r|
+    (n_r terms in row r, n_D diagonal terms) with the exact product from the oracle's dense
+    matrix and D bounded by 9/4 |J^zz| per bond and 3/2 |h^z| per site (spin), or
+    |U| + |mu| per site and 2 |V| per pair (Hubbard)."""
     spec = mk()
     m = hp.Model.from_spec(spec)
     H = oracle.dense_H(spec)
@@ -624,7 +628,14 @@ def test_apply_H_wide_dynamic_range(name, mk, nvec):
     ref = H @ x
     ax = np.abs(x)
     row1 = absH.sum(axis=1)[:, None]
-    bound = row1 * ax.max(axis=0)[None, :] * 2.0 ** -55 + 2.0 ** -50 * (absH @ ax)
+    if spec.kind == wl.SPIN:
+        D = sum(2.25 * abs(np.asarray(J)[2][2]) for _, _, J in spec.couplings) + sum(1.5 * abs(h[2]) for _, h in spec.fields)
+        nD = 2 * len(spec.couplings) + len(spec.fields) + 2
+    else:
+        D = sum(abs(u) for _, u in spec.onsite_U) + sum(abs(mu) for _, mu in spec.chem_pot) + sum(
+            2 * abs(v) for *_, v in spec.density)
+        nD = len(spec.onsite_U) + len(spec.chem_pot) + len(spec.density) + 2
+    bound = row1 * ax.max(axis=0)[None, :] * 2.0 ** -55 + 2.0 ** -50 * (absH @ ax + D * ax)
     err = np.abs(w - (ref if m.is_complex else ref.real))
     assert np.all(err <= bound), float(np.max(err / bound))
     # fp32 storage: relative to each row's sum of |terms|
@@ -633,6 +644,167 @@ def test_apply_H_wide_dynamic_range(name, mk, nvec):
     xr = x32.cpu().numpy().astype(np.complex128)
     ref32 = H @ xr
     nterms = np.count_nonzero(absH, axis=1)[:, None]
-    bound32 = (nterms + 4) * 2.0 ** -24 * (absH @ np.abs(xr))
+    bound32 = (nterms + 4) * 2.0 ** -24 * (absH @ np.abs(xr)) + nD * 2.0 ** -24 * D * np.abs(xr)
     err32 = np.abs(w32 - (ref32 if m.is_complex else ref32.real))
     assert np.all(err32 <= bound32), float(np.max(err32 / np.maximum(bound32, 1e-300)))
+
+
+# ----------------------------------------------------------------------------- split-row sector path
+def _xxz_alt(n, n_up):
+    """Real XXZ ring: exchange J_xy alternating 1.0 / 0.5 (two coefficient classes), Ising 0.75
+    on every bond and a z field 0.3 on the even sites (one more diagonal count group)."""
+    cp = [(i, (i + 1) % n, np.diag([1.0 if i % 2 == 0 else 0.5] * 2 + [0.75])) for i in range(n)]
+    fl = [(i, (0.0, 0.0, 0.3)) for i in range(0, n, 2)]
+    return wl.ModelSpec(kind=wl.SPIN, n_sites=n, couplings=cp, fields=fl, name=f"xxz_alt_{n}").with_basis(
+        wl.BASIS_SZ, n_up)
+
+
+def _ring_irrational(n, n_up):
+    """Exchange values 1.0 and 0.7 (Ising part 1.0 everywhere): not integer multiples of one
+    power of two, so fp64 keeps the generic kernel while fp32 takes the split-row path."""
+    cp = [(i, (i + 1) % n, np.diag([1.0 if i % 3 else 0.7] * 2 + [1.0])) for i in range(n)]
+    return wl.ModelSpec(kind=wl.SPIN, n_sites=n, couplings=cp, name=f"ring_07_{n}").with_basis(wl.BASIS_SZ, n_up)
+
+
+SPLIT_MODELS = [
+    ("heisenberg_4x4_sz8", lambda: wl.heisenberg_square(4, 4).with_basis(wl.BASIS_SZ, 8), [(8, 1), (8, 4), (5, 1), (12, 2)]),
+    ("heisenberg_6x3_sz9", lambda: wl.heisenberg_square(6, 3).with_basis(wl.BASIS_SZ, 9), [(9, 1), (9, 2), (11, 1), (6, 8)]),
+    ("j1j2_ring18_sz7", lambda: wl.j1j2_ring(18).with_basis(wl.BASIS_SZ, 7), [(9, 1), (10, 4), (14, 1), (3, 8)]),
+    ("xxz_alt16_sz7", lambda: _xxz_alt(16, 7), [(8, 2), (10, 1), (15, 1)]),
+    ("ring_irrational14_sz6", lambda: _ring_irrational(14, 6), [(7, 1), (9, 2)]),
+]
+SPLIT_CASES = [(name, mk, L, K) for name, mk, shapes in SPLIT_MODELS for (L, K) in shapes]
+
+
+@pytest.mark.parametrize("name,mk,L,K", SPLIT_CASES, ids=[f"{c[0]}-L{c[2]}-K{c[3]}" for c in SPLIT_CASES])
+def test_sector_split_apply_H(name, mk, L, K):
+    """The split-row kernels (pass H row combinations + pass R row tiles) against the oracle,
+    for several splits and tile heights, in both precisions; the default split too."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    v = wl.gaussian_vector(131, m.dim)
+    ref = oracle.apply_H(spec, v).real
+    vf = _to_dev(m, v, hp.FP32)
+    ref32 = oracle.apply_H(spec, vf.cpu().numpy().astype(np.complex128)).real
+    for prec in (hp.FP64, hp.FP32):
+        try:
+            m.set_sector_split(prec, L, K)
+        except hp.LibraryError as e:
+            assert prec == hp.FP64 and name.startswith("ring_irrational") and e.code == -7
+            continue
+        for shape in ((L, K), (0, 0)):
+            m.set_sector_split(prec, *shape)
+            if prec == hp.FP64:
+                assert _rel(m.apply_H(_to_dev(m, v)).cpu().numpy(), ref) < 1e-12
+            else:
+                assert _rel(m.apply_H(vf).cpu().numpy(), ref32) < 2e-5
+
+
+@pytest.mark.parametrize("n,n_up", [(16, 0), (16, 16), (16, 1), (16, 15), (12, 6)])
+def test_sector_split_degenerate_sectors(n, n_up):
+    """Tiny sectors (one state, N states) and a split whose high part has one bit."""
+    spec = wl.j1j2_ring(n).with_basis(wl.BASIS_SZ, n_up)
+    m = hp.Model.from_spec(spec)
+    v = wl.gaussian_vector(133, m.dim)
+    ref = oracle.apply_H(spec, v).real
+    for L in (0, n - 1):
+        m.set_sector_split(hp.FP64, L, 0)
+        m.set_sector_split(hp.FP32, L, 0)
+        assert _rel(m.apply_H(_to_dev(m, v)).cpu().numpy(), ref) < 1e-12
+        w32 = m.apply_H(_to_dev(m, v, hp.FP32)).cpu().numpy()
+        assert _rel(w32, ref) < 2e-5
+
+
+def test_sector_split_switch_and_errors():
+    spec = wl.heisenberg_square(4, 4).with_basis(wl.BASIS_SZ, 8)
+    m = hp.Model.from_spec(spec)
+    v = wl.gaussian_vector(135, m.dim)
+    ref = oracle.apply_H(spec, v).real
+    m.set_sector_split(hp.FP64, -1, 0)  # generic kernel
+    assert _rel(m.apply_H(_to_dev(m, v)).cpu().numpy(), ref) < 1e-12
+    with pytest.raises(hp.LibraryError) as e:
+        m.set_sector_split(hp.FP64, 15, 8)  # rows of C(15, 7) x 8 do not fit one tile
+    assert e.value.code == -1
+    with pytest.raises(hp.LibraryError) as e:
+        m.set_sector_split(hp.FP64, 8, 3)
+    assert e.value.code == -1
+    cm = hp.Model.from_spec(wl.random_xxz_model(10, 15, seed=3).with_basis(wl.BASIS_SZ, 5))
+    assert cm.is_complex
+    with pytest.raises(hp.LibraryError) as e:
+        cm.set_sector_split(hp.FP64, 5, 1)
+    assert e.value.code == -7
+
+
+@pytest.mark.parametrize("L,K", [(0, 0), (8, 4), (11, 1)])
+def test_sector_split_lanczos_and_tpq(L, K):
+    """Fused Lanczos pass 1 and the mTPQ step through the split-row kernels."""
+    spec = wl.heisenberg_square(4, 4).with_basis(wl.BASIS_SZ, 8)
+    m = hp.Model.from_spec(spec)
+    m.set_sector_split(hp.FP64, L, K)
+    m.set_sector_split(hp.FP32, L, K)
+    v0 = wl.gaussian_vector(137, m.dim)[:, 0]
+    a, b = oracle.lanczos(spec, v0, 40)
+    r = m.lanczos(40, v0=torch.as_tensor(v0))
+    assert _rel(r["alpha"][:12], a[:12]) < 1e-12 and _rel(r["beta"][:12], b[:12]) < 1e-12
+    e0 = oracle.ritz_values(a, b)[0]
+    assert abs(r["eig"][0] - e0) <= 1e-10 * abs(e0)
+    r32 = m.lanczos(40, prec=hp.FP32, v0=torch.as_tensor(v0))
+    assert _rel(r32["alpha"][:8], a[:8]) < 1e-5
+    psi0 = wl.gaussian_vector(139, m.dim)
+    u, h2, nrm = oracle.tpq(spec, psi0[:, 0], 15, 1.0)
+    for prec, tol in ((hp.FP64, 1e-11), (hp.FP32, 2e-5)):
+        res = m.tpq(1, 15, l=1.0, prec=prec, psi0=torch.as_tensor(psi0))
+        assert _rel(res["u"][:, 0], u) < tol and _rel(res["h2"][:, 0], h2) < tol
+        assert _rel(res["norm"][:, 0], nrm) < tol
+
+
+def test_sector_split_refinement_and_autotune():
+    """fp32 Lanczos + fp64 refinement (pass R's refine epilogue) and the split autotuner."""
+    spec = wl.j1j2_ring(18).with_basis(wl.BASIS_SZ, 9)
+    m = hp.Model.from_spec(spec)
+    for prec in (hp.FP64, hp.FP32):
+        t = m.autotune(prec)
+        assert t["n_candidates"] >= 2 and t["split_L"] > 0 and t["split_K"] >= 1
+        assert t["best_ms"] <= t["default_ms"] + 1e-6
+    v0 = wl.gaussian_vector(141, m.dim)[:, 0]
+    a, b = oracle.lanczos(spec, v0, 120)
+    e0 = oracle.ritz_values(a, b)[0]
+    r = m.lanczos(120, prec=hp.FP32, v0=torch.as_tensor(v0), refine=True, keep_basis=-1)
+    assert abs(r["e_refined"] - e0) <= 1e-8 * abs(e0) and r["e_refined"] >= e0 - 1e-12 * abs(e0)
+    r64 = m.lanczos(120, prec=hp.FP64, v0=torch.as_tensor(v0), refine=True, keep_basis=1)
+    assert abs(r64["e_refined"] - e0) <= 1e-10 * abs(e0)
+
+
+def _chunked_dot(x, y, chunk=1 << 28):
+    """fp64 dot product of two long CUDA vectors in chunks (cuBLAS takes 32-bit lengths)."""
+    acc = 0.0
+    for c in range(0, x.shape[0], chunk):
+        acc += torch.dot(x[c:c + chunk].double(), y[c:c + chunk].double()).item()
+    return acc
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_heisenberg_6x6_sz0_full_size_lanczos_steps(prec):
+    """The 9,075,135,300-row sector (more than 2^32 rows) through the fused Lanczos kernels:
+    alpha_0 of a 4-step run equals <v, H v> / <v, v> assembled from the sampled-row-checked
+    apply_H output on the same Philox start vector; the fp32 run agrees with the fp64 run to
+    fp32 rounding.  For a random vector alpha_0 is close to the sector average of H,
+    Tr H / D = 72 (P_parallel - P_antiparallel) / 4 = -18/35 (18 of 36 spins up)."""
+    W = wl.workload("heisenberg_6x6_sz0")
+    m = hp.Model.from_spec(W["model"])
+    seed = 123432
+    p = hp.FP64 if prec == "fp64" else hp.FP32
+    v = m.random_vector(seed, prec=p)
+    w = m.apply_H(v)
+    a0 = _chunked_dot(v[:, 0], w[:, 0]) / _chunked_dot(v[:, 0], v[:, 0])
+    del v, w
+    torch.cuda.empty_cache()
+    r = m.lanczos(4, prec=p, seed=seed)
+    assert r["steps"] == 4
+    assert abs(r["alpha"][0] - a0) <= (1e-12 if p == hp.FP64 else 1e-6) * abs(a0)
+    assert abs(a0 - (-18.0 / 35.0)) < 1e-3
+    if p == hp.FP32:
+        r64 = m.lanczos(4, prec=hp.FP64, seed=seed)
+        assert _rel(r["alpha"], r64["alpha"]) < 1e-6 and _rel(r["beta"], r64["beta"]) < 1e-6
+    m.close()
+    torch.cuda.empty_cache()
