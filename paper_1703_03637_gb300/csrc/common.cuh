@@ -149,10 +149,13 @@ struct SecDev {
   uint32_t lo_off[kSecMaxL + 2];     // start of popcount class q in the list of all 2^L low parts
   uint32_t jbase, nJ;
   const uint32_t* lo_list;      // [nJ] low parts grouped by popcount, ascending
-  int lo_slots;                 // slots of the low neighbour table
-  const uint16_t* lo_nbr;       // [lo_slots][nJ] rank (in its class) of the q-th neighbour
+  // low neighbours in groups of four 16-bit slots: group g of entry j is lo_nbr4[g * nJ + j];
+  // slot 4g + t holds the rank (in its class) of neighbour 4g + t, unused slots hold nq_max,
+  // the index of a zero entry placed after the staged rows
+  int lo_groups;
+  const uint2* lo_nbr4;         // [lo_groups][nJ]
   const uint8_t* lo_cnt;        // [nJ] neighbours; entries are class-sorted
-  const uint8_t* lo_cls;        // [lo_slots][nJ] class of the q-th neighbour (multi-class only)
+  const uint32_t* lo_cls4;      // [lo_groups][nJ] class byte of each slot (multi-class only)
   const uint16_t* lo_diag;      // [nJ] packed diagonal counts of the low part
   // high side
   const uint64_t* hi_off;       // [2^H] first row element of each high part

@@ -265,8 +265,10 @@ bool sec_fits(const SecTerms& t, int L, int K, int esz) {
 
 int sec_default_K(const SecTerms& t, int L, int esz) {
   const uint64_t r = std::max<uint64_t>(1, longest_row(t.n_sites, t.n_ones, L));
+  // 8-byte elements stop at 4 rows (8 int64 rows run out of registers)
+  const int kmax = esz >= 8 ? 4 : 8;
   int K = 1;
-  while (K < 8 && r * esz * (uint64_t)(2 * K) <= (uint64_t)kTileBudget) K *= 2;
+  while (K < kmax && r * esz * (uint64_t)(2 * K) <= (uint64_t)kTileBudget) K *= 2;
   return K;
 }
 
@@ -379,8 +381,10 @@ Status sec_build(const SecTerms& t, int L, int K, SecTables** out, cudaStream_t 
     lo_cnt[j] = (uint8_t)c;
     lo_slots = std::max(lo_slots, c);
   }
-  std::vector<uint16_t> lo_nbr((size_t)std::max(1, lo_slots) * nJ, 0);
-  std::vector<uint8_t> lo_cls(d.one_cls ? 1 : (size_t)std::max(1, lo_slots) * nJ, 0);
+  // groups of four slots; slots past an entry's count point at the zero entry (index nq_max)
+  const int G = std::max(1, (lo_slots + 3) / 4);
+  std::vector<uint16_t> lo_nbr((size_t)G * nJ * 4, (uint16_t)nqmax);
+  std::vector<uint8_t> lo_cls(d.one_cls ? 4 : (size_t)G * nJ * 4, 0);
   for (uint32_t j = 0; j < nJ; ++j) {
     const uint32_t lo = lo_list[j0 + j];
     int s = 0;
@@ -388,12 +392,13 @@ Status sec_build(const SecTerms& t, int L, int K, SecTables** out, cudaStream_t 
       const Bond& b = a.bonds[k];
       if (!(((lo >> b.i) ^ (lo >> b.j)) & 1u)) continue;
       const uint32_t lo2 = lo ^ ((1u << b.i) | (1u << b.j));
-      lo_nbr[(size_t)s * nJ + j] = (uint16_t)lo_rank[lo2];  // same class: rank < C(L, q) <= 65535
-      if (!d.one_cls) lo_cls[(size_t)s * nJ + j] = (uint8_t)a.bond_cls[k];
+      const size_t o = ((size_t)(s / 4) * nJ + j) * 4 + (s % 4);
+      lo_nbr[o] = (uint16_t)lo_rank[lo2];  // same class: rank < C(L, q) <= 65535
+      if (!d.one_cls) lo_cls[o] = (uint8_t)a.bond_cls[k];
       ++s;
     }
   }
-  d.lo_slots = lo_slots;
+  d.lo_groups = G;
   // straddling bonds (a = high site - L, b = low site) and one rank table per distinct low site
   std::vector<int> str_sites;
   d.n_str = (int)stb.size();
@@ -539,9 +544,17 @@ Status sec_build(const SecTerms& t, int L, int K, SecTables** out, cudaStream_t 
   Status s;
   const std::vector<uint32_t> lo_used(lo_list.begin() + j0, lo_list.begin() + j0 + nJ);
   if ((s = up(T.get(), lo_used, &d.lo_list, st)).code) return s;
-  if ((s = up(T.get(), lo_nbr, &d.lo_nbr, st)).code) return s;
+  {
+    const uint16_t* p16 = nullptr;
+    if ((s = up(T.get(), lo_nbr, &p16, st)).code) return s;
+    d.lo_nbr4 = reinterpret_cast<const uint2*>(p16);
+  }
   if ((s = up(T.get(), lo_cnt, &d.lo_cnt, st)).code) return s;
-  if ((s = up(T.get(), lo_cls, &d.lo_cls, st)).code) return s;
+  {
+    const uint8_t* p8 = nullptr;
+    if ((s = up(T.get(), lo_cls, &p8, st)).code) return s;
+    d.lo_cls4 = reinterpret_cast<const uint32_t*>(p8);
+  }
   if ((s = up(T.get(), lo_diag, &d.lo_diag, st)).code) return s;
   if ((s = up(T.get(), hi_off, &d.hi_off, st)).code) return s;
   if ((s = up(T.get(), hi_nbr, &d.hi_nbr, st)).code) return s;
@@ -691,22 +704,30 @@ __device__ __forceinline__ void tile_load(const T* p, T* out) {
   }
 }
 
-// pass R: K rows of one class in shared memory; low-low exchange from the neighbour table,
-// straddling exchange gathered from the partner rows, diagonal from packed counts, plus the
-// pass-H sums Wh, then the fused epilogue.  X is the input (fp32) or its fixed-point copy.
+// pass R: K rows of one class in shared memory; low-low exchange from the grouped neighbour
+// table, straddling exchange gathered from the partner rows, diagonal from packed counts, plus
+// the pass-H sums Wh, then the fused epilogue.  X is the input (fp32) or its fixed-point copy.
+// Every thread owns E elements of the tile at a time (E * K values); the straddling bonds run
+// in an outer loop that is the same for all threads, so each bond's constants (low bit, rank
+// table, partner row pointers, activating bit values) are read once per thread and used for
+// all its elements, and the loads of the E elements are independent.
 template <class T, int K, Epi E, int NT, bool ONE>
-__global__ void __launch_bounds__(NT) k_sec_lo(const SecDev d, const T* __restrict__ X, const T* Wh, void* w,
-                                               FusedArgs fa, const int* __restrict__ Ep) {
+__global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDev d, const T* __restrict__ X,
+                                                                    const T* Wh, void* w, FusedArgs fa,
+                                                                    const int* __restrict__ Ep) {
   using R = std::conditional_t<sizeof(T) == 4, float, double>;
   constexpr bool FIX = sizeof(T) == 8;
+  constexpr int EL = (K >= 4) ? 1 : 4 / K;  // elements per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
-  R* s_dtab = reinterpret_cast<R*>(smem_raw + (((size_t)d.nq_max * K * sizeof(T) + 15) / 16) * 16);
+  R* s_dtab = reinterpret_cast<R*>(smem_raw + (((size_t)(d.nq_max + 1) * K * sizeof(T) + 15) / 16) * 16);
   __shared__ uint64_t s_roff[K];
-  __shared__ uint32_t s_hbits[K];
+  __shared__ uint32_t s_hrow[K];
   __shared__ uint32_t s_hdiag[K];
   __shared__ uint32_t s_spm[K][kSecMaxSl];
-  __shared__ uint64_t s_poff[K][kSecMaxStr];
+  __shared__ uint2 s_sb[kSecMaxStr];         // low bit | class << 16, offset of the bond's rank table
+  __shared__ uint32_t s_need[kSecMaxStr];    // bit m: low-bit value that activates the bond in row m
+  __shared__ const T* s_ptr[kSecMaxStr][K];  // partner row of row m through the bond
   __shared__ uint32_t s_hi0;
   __shared__ int s_nk;
   __shared__ T s_w[kSecMaxCls];
@@ -715,7 +736,7 @@ __global__ void __launch_bounds__(NT) k_sec_lo(const SecDev d, const T* __restri
 
   if (fa.done != nullptr && *fa.done) return;
   const int tid = threadIdx.x;
-  const size_t nJ = d.nJ;
+  const uint32_t nJ = d.nJ;
   // fixed point: element = q 2^eoff; a power-of-two unit 2^k folds into the scales (see
   // k_hub_up_q): hv = (dg 2^-k xr + (+-S)) 2^(eoff + k)
   const int eoff = FIX ? (*Ep + d.qextra - 1078) : 0;
@@ -732,6 +753,9 @@ __global__ void __launch_bounds__(NT) k_sec_lo(const SecDev d, const T* __restri
   const double r_k = fold ? __longlong_as_double((long long)(1023 - u_l2) << 52) : 1.0;
   for (int k = tid; k < d.dtab_n; k += NT) s_dtab[k] = (R)(d.dtab[k] * r_k);
   if (tid < kSecMaxCls) s_w[tid] = tid < d.n_cls ? sec_w<T>(d, tid) : (T)0;
+  if (tid < d.n_str)
+    s_sb[tid] = make_uint2((uint32_t)d.str_b[tid] | ((uint32_t)d.str_cls[tid] << 16), (uint32_t)d.str_t[tid] * nJ);
+  if (tid < K) tile[(size_t)d.nq_max * K + tid] = (T)0;  // the zero entry unused neighbour slots point at
   if constexpr (E == Epi::kTpq) {
     if (tid == 0) s_inv[0] = fa.scal[0];
   }
@@ -741,7 +765,9 @@ __global__ void __launch_bounds__(NT) k_sec_lo(const SecDev d, const T* __restri
     es.c2 = fa.scal[1];
   }
   const R coef0 = (R)d.coef[0];
-  Red<!FIX ? false : true> red;
+  const int n_str = d.n_str;
+  const uint32_t pad2 = (uint32_t)d.nq_max | ((uint32_t)d.nq_max << 16);
+  Red<FIX> red;
   red.zero();
 
   for (int64_t t = blockIdx.x; t < d.n_tiles; t += gridDim.x) {
@@ -751,115 +777,164 @@ __global__ void __launch_bounds__(NT) k_sec_lo(const SecDev d, const T* __restri
       const uint32_t start = tw & 0xffffffu;
       const int nk = (int)(tw >> 24) + 1;
       uint64_t roff = 0;
-      uint32_t hb = 0, hd = 0;
+      uint32_t hd = 0, hi = 0;
       for (int l = 0; l < kSecMaxSl; ++l) s_spm[tid][l] = 0u;
       if (tid < nk) {
-        const uint32_t hi = __ldg(d.hi_seq + start + tid);
+        hi = __ldg(d.hi_seq + start + tid);
         if (tid == 0) s_hi0 = hi;
         roff = __ldg(d.hi_off + hi);
         hd = __ldg(d.hi_diag + hi);
-        for (int n = 0; n < d.n_str; ++n) {
-          hb |= ((hi >> d.str_a[n]) & 1u) << n;
-          s_poff[tid][n] = __ldg(d.hi_off + (hi ^ (1u << d.str_a[n])));
-        }
         for (int n = 0; n < d.n_sp; ++n)
           if ((hi >> d.sp_a[n]) & 1u) s_spm[tid][d.sp_l[n]] |= 1u << d.sp_b[n];
       }
       if (tid == 0) s_nk = nk;
       s_roff[tid] = roff;
-      s_hbits[tid] = hb;
+      s_hrow[tid] = hi;
       s_hdiag[tid] = hd;
     }
     __syncthreads();
     const int nk = s_nk;
+    // straddling bonds of this tile's rows, one bond per thread (read after the staging barrier)
+    if (tid < n_str) {
+      const uint32_t a = d.str_a[tid];
+      uint32_t need = 0u;
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        const uint32_t hi = s_hrow[m];
+        // active when bit b of lo differs from bit a of hi
+        need |= (1u - ((hi >> a) & 1u)) << m;
+        s_ptr[tid][m] = X + (m < nk ? __ldg(d.hi_off + (hi ^ (1u << a))) : 0ull);
+      }
+      s_need[tid] = need;
+    }
     const int q = d.n_ones - __popc(s_hi0);
     const uint32_t loff = d.lo_off[q] - d.jbase;  // the class in the tables of the present classes
     const int nq = (int)(d.lo_off[q + 1] - d.lo_off[q]);
-    // stage the rows: tile[u * K + m] = X[row m][u]
-    for (int u = tid; u < nq; u += NT) {
+    // stage the rows, tile[u * K + m] = X[row m][u], with kStage elements per thread in flight
+    constexpr int kStage = (K >= 8) ? 1 : 8 / K;
+    for (int u0 = tid; u0 < nq; u0 += NT * kStage) {
+      T tmp[kStage][K];
 #pragma unroll
-      for (int m = 0; m < K; ++m) tile[u * K + m] = (m < nk) ? __ldg(X + s_roff[m] + u) : (T)0;
-    }
-    __syncthreads();
-    for (int u = tid; u < nq; u += NT) {
-      const uint32_t j = loff + (uint32_t)u;
-      const uint32_t lo = __ldg(d.lo_list + j);
-      T acc[K];
+      for (int e = 0; e < kStage; ++e) {
+        const int u = u0 + e * NT;
 #pragma unroll
-      for (int m = 0; m < K; ++m) acc[m] = (T)0;
-      // low-low exchange: the row's neighbours in the staged tile
-      const int cnt = __ldg(d.lo_cnt + j);
-      int s = 0;
-      for (; s + 2 <= cnt; s += 2) {
-        const int n0 = __ldg(d.lo_nbr + (size_t)s * nJ + j), n1 = __ldg(d.lo_nbr + (size_t)(s + 1) * nJ + j);
-        T v0[K], v1[K];
-        tile_load<T, K>(tile + n0 * K, v0);
-        tile_load<T, K>(tile + n1 * K, v1);
-        if constexpr (ONE) {
+        for (int m = 0; m < K; ++m) tmp[e][m] = (u < nq && m < nk) ? __ldg(X + s_roff[m] + u) : (T)0;
+      }
 #pragma unroll
-          for (int m = 0; m < K; ++m) acc[m] += v0[m] + v1[m];
-        } else {
-          const T w0 = s_w[__ldg(d.lo_cls + (size_t)s * nJ + j)], w1 = s_w[__ldg(d.lo_cls + (size_t)(s + 1) * nJ + j)];
+      for (int e = 0; e < kStage; ++e) {
+        const int u = u0 + e * NT;
+        if (u < nq) {
 #pragma unroll
-          for (int m = 0; m < K; ++m) acc[m] += w0 * v0[m] + w1 * v1[m];
+          for (int m = 0; m < K; ++m) tile[u * K + m] = tmp[e][m];
         }
       }
-      if (s < cnt) {
-        const int n0 = __ldg(d.lo_nbr + (size_t)s * nJ + j);
-        T v0[K];
-        tile_load<T, K>(tile + n0 * K, v0);
-        const T w0 = ONE ? (T)1 : s_w[__ldg(d.lo_cls + (size_t)s * nJ + j)];
+    }
+    __syncthreads();
+    const uint32_t kmask = (1u << nk) - 1u;
+    for (int u0 = tid; u0 < nq; u0 += NT * EL) {
+      uint32_t lo[EL], jj[EL];
+      int ng[EL];
+      T acc[EL][K];
+      int gmax = 0;
 #pragma unroll
-        for (int m = 0; m < K; ++m) acc[m] += ONE ? v0[m] : w0 * v0[m];
+      for (int e = 0; e < EL; ++e) {
+        const int u = u0 + e * NT;
+        const bool ok = u < nq;
+        jj[e] = loff + (uint32_t)(ok ? u : 0);
+        lo[e] = __ldg(d.lo_list + jj[e]);
+        ng[e] = ok ? ((int)__ldg(d.lo_cnt + jj[e]) + 3) >> 2 : 0;
+        gmax = max(gmax, ng[e]);
+#pragma unroll
+        for (int m = 0; m < K; ++m) acc[e][m] = (T)0;
       }
-      // straddling exchange: (hi, lo) <- (hi ^ 2^a, lo ^ 2^b) when bit a of hi differs from bit b of lo
-      for (int n = 0; n < d.n_str; ++n) {
-        const uint32_t lb = (lo >> d.str_b[n]) & 1u;
-        bool any = false;
+      // low-low exchange: four neighbours per table load, unused slots read the zero entry
+      for (int g = 0; g < gmax; ++g) {
+        uint2 rec[EL];
+        uint32_t cw[EL];
 #pragma unroll
-        for (int m = 0; m < K; ++m) any |= (m < nk) && (((s_hbits[m] >> n) & 1u) != lb);
-        if (!any) continue;
-        const uint32_t col = __ldg(d.str_rank + (size_t)d.str_t[n] * nJ + j);
-        const T wn = ONE ? (T)1 : s_w[d.str_cls[n]];
+        for (int e = 0; e < EL; ++e) {
+          const uint32_t o = (uint32_t)g * nJ + jj[e];  // < 2^28
+          rec[e] = g < ng[e] ? __ldg(d.lo_nbr4 + o) : make_uint2(pad2, pad2);
+          if constexpr (!ONE) cw[e] = g < ng[e] ? __ldg(d.lo_cls4 + o) : 0u;
+        }
 #pragma unroll
-        for (int m = 0; m < K; ++m) {
-          if ((m < nk) && (((s_hbits[m] >> n) & 1u) != lb)) {
-            const T x = __ldg(X + s_poff[m][n] + col);
-            acc[m] += ONE ? x : wn * x;
+        for (int e = 0; e < EL; ++e) {
+#pragma unroll
+          for (int t4 = 0; t4 < 4; ++t4) {
+            const uint32_t word = (t4 < 2) ? rec[e].x : rec[e].y;
+            const uint32_t nb = (t4 & 1) ? (word >> 16) : (word & 0xffffu);
+            T v[K];
+            tile_load<T, K>(tile + nb * K, v);
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+              if constexpr (ONE) acc[e][m] += v[m];
+              else acc[e][m] += s_w[(cw[e] >> (8 * t4)) & (kSecMaxCls - 1)] * v[m];
+            }
           }
         }
       }
-      const uint32_t ld = __ldg(d.lo_diag + j);
+      // straddling exchange, one bond at a time for all elements of the thread
+      for (int n = 0; n < n_str; ++n) {
+        const uint2 sb = s_sb[n];
+        const uint32_t b = sb.x & 31u;
+        const uint32_t need = s_need[n];
+        const T wn = ONE ? (T)1 : s_w[(sb.x >> 16) & (kSecMaxCls - 1)];
+        const T* pm[K];
 #pragma unroll
-      for (int m = 0; m < K; ++m) {
-        if (m >= nk) break;
-        uint32_t c = ld + s_hdiag[m];
-        for (int l = 0; l < d.n_sl; ++l) c += (uint32_t)__popc(lo & s_spm[m][l]) << (8 * d.sp_lg[l]);
-        const R dg = s_dtab[(c & 0xffu) + d.dstride * (c >> 8)];
-        const int64_t idx = (int64_t)s_roff[m] + u;
-        const T xq = tile[u * K + m];
-        const T wv = Wh[idx];
-        if constexpr (!FIX) {
-          const R hv = ONE ? dg * xq + coef0 * (acc[m] + wv) : dg * xq + (acc[m] + wv);
-          epilogue<float, E>(idx, 0, xq, 0.f, hv, 0.f, reinterpret_cast<float*>(w), fa, es, s_inv, red);
-        } else {
-          const long long S = acc[m] + wv;
-          const double xr = __ll2double_rn(xq);
-          if (fold) {
-            const double hvu = fma(dg, xr, __ll2double_rn(u_neg ? -S : S));  // hv = hvu 2^e2
-            if constexpr (E == Epi::kStore) {
-              reinterpret_cast<double*>(w)[idx] = hvu * s_e2;
-            } else if constexpr (E == Epi::kLanczos1) {
-              double* P = reinterpret_cast<double*>(fa.out);
-              const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
-              P[idx] = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
-              red.add(0, xr, hvu);
-              red.tick();
-            }
+        for (int m = 0; m < K; ++m) pm[m] = s_ptr[n][m];
+        uint32_t col[EL], act[EL];
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+          const uint32_t lb = (lo[e] >> b) & 1u;
+          act[e] = (lb ? need : ~need) & kmask & (ng[e] >= 0 && u0 + e * NT < nq ? 0xffffffffu : 0u);
+          col[e] = act[e] ? (uint32_t)__ldg(d.str_rank + sb.y + jj[e]) : 0u;
+        }
+#pragma unroll
+        for (int e = 0; e < EL; ++e)
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            const T x = ((act[e] >> m) & 1u) ? __ldg(pm[m] + col[e]) : (T)0;
+            if constexpr (ONE) acc[e][m] += x;
+            else acc[e][m] += wn * x;
+          }
+      }
+      // diagonal, pass-H sums and the epilogue
+#pragma unroll
+      for (int e = 0; e < EL; ++e) {
+        const int u = u0 + e * NT;
+        if (u >= nq) break;
+        const uint32_t ld = __ldg(d.lo_diag + jj[e]);
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          if (m >= nk) break;
+          uint32_t c = ld + s_hdiag[m];
+          for (int l = 0; l < d.n_sl; ++l) c += (uint32_t)__popc(lo[e] & s_spm[m][l]) << (8 * d.sp_lg[l]);
+          const R dg = s_dtab[(c & 0xffu) + d.dstride * (c >> 8)];
+          const int64_t idx = (int64_t)s_roff[m] + u;
+          const T xq = tile[u * K + m];
+          const T wv = Wh[idx];
+          if constexpr (!FIX) {
+            const R hv = ONE ? dg * xq + coef0 * (acc[e][m] + wv) : dg * xq + (acc[e][m] + wv);
+            epilogue<float, E>(idx, 0, xq, 0.f, hv, 0.f, reinterpret_cast<float*>(w), fa, es, s_inv, red);
           } else {
-            const double x = fix_to_double(xq, eoff);
-            const double hv = fma((double)dg, x, d.unit * fix_to_double(S, eoff));
-            epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, reinterpret_cast<double*>(w), fa, es, s_inv, red);
+            const long long S = acc[e][m] + wv;
+            const double xr = __ll2double_rn(xq);
+            if (fold) {
+              const double hvu = fma(dg, xr, __ll2double_rn(u_neg ? -S : S));  // hv = hvu 2^e2
+              if constexpr (E == Epi::kStore) {
+                reinterpret_cast<double*>(w)[idx] = hvu * s_e2;
+              } else if constexpr (E == Epi::kLanczos1) {
+                double* P = reinterpret_cast<double*>(fa.out);
+                const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
+                P[idx] = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+                red.add(0, xr, hvu);
+                red.tick();
+              }
+            } else {
+              const double x = fix_to_double(xq, eoff);
+              const double hv = fma((double)dg, x, d.unit * fix_to_double(S, eoff));
+              epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, reinterpret_cast<double*>(w), fa, es, s_inv, red);
+            }
           }
         }
       }
@@ -886,8 +961,8 @@ __global__ void __launch_bounds__(NT) k_sec_lo(const SecDev d, const T* __restri
 }
 
 // ---------------------------------------------------------------- launch helpers
-size_t lo_smem(const SecDev& d, int esz) {
-  return (((size_t)d.nq_max * d.K * esz + 15) / 16) * 16 + (size_t)d.dtab_n * esz;
+size_t lo_smem(const SecDev& d, int esz) {  // the rows, their zero entry, the diagonal table
+  return (((size_t)(d.nq_max + 1) * d.K * esz + 15) / 16) * 16 + (size_t)d.dtab_n * esz;
 }
 
 // row-pass threads: 1024 (one CTA per SM) for tiles above ~110 KB, else 512
