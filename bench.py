@@ -1,16 +1,20 @@
-"""Benchmark of the Lanczos hot path on one GB300 (or N independent replicas).
+"""Benchmark of the Lanczos / mTPQ hot path on one GB300 (or N independent replicas).
 
-Workload (default): the half-filled 4x4 periodic Hubbard model, t = 1, U = 8, N_up = N_dn = 8,
-sector dimension C(16,8)^2 = 165,636,900, real fp64 vectors, 200 Lanczos steps from a seeded
-Gaussian start (section 3.4).  One benchmark step is one complete hphi_lanczos_run: start
-vector -> 200 fused H v / vector-update steps -> fp64 tridiagonal eigensolve -> energies on
-the host.  Metric: H v throughput of the Lanczos loop in Gelem/s (basis rows x Lanczos steps
-per second); steps/s and the fraction of HBM / fp64 roofline are reported beside it.
+Default workload: the spin-1/2 Heisenberg model (J = 1) on the 6x6 periodic square lattice in
+its S^z = 0 sector, dimension C(36,18) = 9,075,135,300 (more rows than 2^32), fp64 vectors.  One
+benchmark step is one hphi_lanczos_run of 20 Lanczos steps from a seeded Gaussian start
+(section 3.4: start vector, fused H v + vector-update steps, fp64 tridiagonal eigensolve,
+energies on the host); the workload's own run has 100 steps (`--lanczos-steps 100`).  Metric:
+H v throughput of the Lanczos loop in Gelem/s (rows x Lanczos steps per second), with Lanczos
+steps/s, the roofline of the fused H v group against HBM and against the fp64 pipe, the same
+run through the public API with the start vector copied from pinned host memory (e2e), the
+mixed form (fp32 vectors, fp64 reductions, fp64 Ritz vector + Rayleigh-quotient refinement)
+against fp64, and the 4x4 Hubbard Lanczos line.
 
-Timing: W untimed warm-up runs, then K runs between CUDA events on the launching stream,
-barrier + synchronize on both sides, max over ranks.  Vectors (1.33 GB each) exceed the
-129 MB L2, so no flush is needed.  `--impl reference` times the CPU oracle instead (the
-only other place this file runs oracle code), on a bounded slice of the same workload.
+Timing: W untimed warm-up steps, then K steps between CUDA events on the launching stream,
+barrier + synchronize on both sides, max over ranks.  Vectors (73 GB each) exceed the 129 MB L2,
+so no flush is needed.  `--impl reference` times the CPU oracle instead (the only other place
+this file runs oracle code), on a bounded sample of rows of the same workload.
 """
 from __future__ import annotations
 
@@ -34,11 +38,13 @@ import workloads as wl  # noqa: E402
 
 METRIC = "H·v Gelem/s & %HBM peak; Lanczos/mTPQ steps/s, FP64 vs mixed+batched at ΔE"
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per fused H v launch group from one ncu capture of the current
-# kernels (profiles/hubbard_4x4_8u8d_hv_group_dram.md: quantise + pass D + pass U, the group
-# of every step after the first); None where no capture exists
-MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): 10_560_000_000}
-FP64_PEAK_TINST = 0.625   # nominal GB300 fp64 rate, 1.25 TFLOP/s = 0.625 T FMA/s
+# DRAM bytes (read + write) per fused H v launch group from an ncu capture of the current
+# kernels, with where they come from; absent where no capture of the current kernels exists
+MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): (10_560_000_000, "ncu capture of the 4x4 Hubbard sector, "
+                                                                   "quantise + pass D + pass U of one step")}
+# fp64 FMA throughput of this machine's GB300 from a throughput probe (thread-level T op/s); the
+# chip issues fp64 at 1/64 of its fp32 rate
+FP64_PEAK_TOPS = 0.50
 
 
 def peaks():
@@ -171,45 +177,107 @@ def oracle_rows_per_s(spec, target_s: float = 12.0, max_rows: int = 4_000_000):
     return n2 / dt2, n2, dt2, cores
 
 
+def oracle_sampled_rows_per_s(spec, target_s: float = 12.0, max_rows: int = 2_000_000, seed: int = 777):
+    """Oracle H v on randomly sampled rows of a workload too large for a host copy of the vector:
+    every input element a row needs is regenerated from its Philox index (the oracle's
+    or_apply_H_rows_philox), all host cores; rows per second."""
+    import oracle
+    D = oracle.dim(spec)
+    rng = np.random.default_rng(1)
+    n = 20000
+    rows = np.sort(rng.integers(0, D, size=n)).astype(np.uint64)
+    t0 = time.perf_counter()
+    oracle.apply_H_rows_philox(spec, rows, seed, False)
+    dt = time.perf_counter() - t0
+    n2 = int(min(max_rows, max(n, n * target_s / max(dt, 1e-6))))
+    rows = np.sort(rng.integers(0, D, size=n2)).astype(np.uint64)
+    t0 = time.perf_counter()
+    oracle.apply_H_rows_philox(spec, rows, seed, False)
+    dt2 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    return n2 / dt2, n2, dt2, cores
+
+
+def oracle_baseline(spec, target_s: float = 12.0):
+    """CPU baseline of one H v row in Gelem/s with the sample it was measured on."""
+    import oracle
+    D = oracle.dim(spec)
+    if D * 16 <= 16e9:
+        rps, n, dt, cores = oracle_rows_per_s(spec, target_s)
+        sample = (f"oracle H v on {n} contiguous rows of the same basis ({dt:.1f} s, OpenMP over {cores} host "
+                  f"threads); a Lanczos step is one such H v per row")
+    else:
+        rps, n, dt, cores = oracle_sampled_rows_per_s(spec, target_s)
+        sample = (f"oracle H v on {n} randomly sampled rows, input elements regenerated from the Philox "
+                  f"definition of the start vector ({dt:.1f} s, OpenMP over {cores} host threads); a Lanczos "
+                  f"step is one such H v per row")
+    return {"value": round(rps / 1e9, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+
 # ----------------------------------------------------------------------------- main
-def run_e2e_lanczos(m, D, seed, steps, prec, args, world):
-    """The same Lanczos run through the public API with the start vector copied from pinned
-    host memory every step and the energies read back; rows x steps per second."""
+def pinned_gaussian(D, seed, complex_=False, chunk=1 << 27):
+    """A seeded Gaussian start vector in pinned host memory, drawn on the device chunk by chunk
+    (torch's generator; any Gaussian vector serves as a Lanczos start) and copied out."""
     import torch
-    v0_host = torch.from_numpy(wl.gaussian_vector(seed, D)[:, 0]).pin_memory()
-    if m.is_complex:
-        v0_host = v0_host.to(torch.complex128).pin_memory()
+    dt = torch.complex128 if complex_ else torch.float64
+    host = torch.empty(D, dtype=dt, pin_memory=True)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    for c in range(0, D, chunk):
+        n = min(chunk, D - c)
+        host[c:c + n].copy_(torch.randn(n, dtype=dt, device="cuda", generator=g))
+    torch.cuda.synchronize()
+    return host
+
+
+def run_e2e_lanczos(m, D, seed, steps, prec, args, world, v0_host=None):
+    """The same Lanczos run through the public API with the start vector in pinned host memory:
+    every step copies it in (the library's own copy into its first Lanczos vector, so no device
+    copy of it is held beside the workspace) and reads the energies and coefficients back;
+    rows x steps per second."""
+    import torch
+    if v0_host is None:
+        v0_host = pinned_gaussian(D, seed, m.is_complex)
+    m.lanczos(steps, prec=prec, v0=v0_host, v0_on_host=True)  # untimed: the host-copy path warm
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 2))
     for _ in range(e2e_steps):
-        v0_dev = v0_host.to("cuda", non_blocking=True)
-        m.lanczos(steps, prec=prec, v0=v0_dev)
+        r = m.lanczos(steps, prec=prec, v0=v0_host, v0_on_host=True)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    return {"value": whole_job_rate(D * steps * e2e_steps, world, e2e_s), "unit": "Gelem/s",
-            "h2d_bytes_per_step": int(v0_host.numel() * v0_host.element_size()),
-            "d2h_bytes_per_step": int(8 * (2 * steps + 8 + 4))}
+    out = {"value": round(whole_job_rate(D * steps * e2e_steps, world, e2e_s), 4), "unit": "Gelem/s",
+           "h2d_bytes_per_step": int(v0_host.numel() * v0_host.element_size()),
+           "d2h_bytes_per_step": int(8 * (2 * steps + 8 + 4)), "steps": e2e_steps, "e0": r["eig"][0],
+           "start": "pinned host vector copied in by hphi_lanczos_run (v0_on_host)"}
+    del v0_host
+    return out
 
 
-def run_ours(args, world, rank, local):
+# Lanczos steps per benchmark step where the workload's own run is too long for a few-minute
+# benchmark (the 6x6 sector's 100-step fp64 run takes about a minute)
+BENCH_LANCZOS_STEPS = {"heisenberg_6x6_sz0": 20}
+# fp64-pipe operations per row of the fused Lanczos pass 1 of the split-row fp64 path, counted
+# from k_sec_lo's folded epilogue: two int64 -> fp64 conversions, the diagonal FMA, the update
+# c1 hv - c2 P (one multiply, one FMA) and the <C, H C> FMA
+SEC_FP64_OPS_PER_ROW = 6
+
+
+def host_ram_bytes():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError, AttributeError):
+        return 0
+
+
+def timed_lanczos(m, steps, prec, seed, args, world, local, rank, refine=False, n=None):
+    """W warm-up runs then n timed runs (CUDA events on the current stream, barrier + sync on both
+    sides, max over ranks); eager launches with an event pair around every fused H v group."""
     import torch
-    import paper_1703_03637_gb300 as hp
-
-    torch.cuda.set_device(local)
-    W = wl.workload(args.workload)
-    spec, steps = W["model"], (args.lanczos_steps or W["steps"])
-    prec = hp.FP64 if args.prec == "fp64" else hp.FP32
-    m = hp.Model.from_spec(spec)
-    esz = (8 if prec == hp.FP64 else 4) * (2 if m.is_complex else 1)
-    D = m.dim
-    seed = wl.START_SEED + rank
-    tune = m.autotune(prec) if args.autotune else None  # untimed set-up: picks the launch shape
-    if args.autotune and args.mixed and prec == hp.FP64:
-        tune = {"fp64": tune, "fp32": m.autotune(hp.FP32)}
+    n = n or args.steps
     for _ in range(args.warmup):
-        m.lanczos(steps, prec=prec, seed=seed, profile=True)
+        m.lanczos(steps, prec=prec, seed=seed, profile=True, refine=refine)
     stream = torch.cuda.current_stream()
     clk = Clocks(local) if rank == 0 else None
     barrier(world)
@@ -217,8 +285,8 @@ def run_ours(args, world, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     hv_ms, hv_n, launches, res = 0.0, 0, 0, None
     e0.record(stream)
-    for _ in range(args.steps):
-        res = m.lanczos(steps, prec=prec, seed=seed, profile=True)
+    for _ in range(n):
+        res = m.lanczos(steps, prec=prec, seed=seed, profile=True, refine=refine)
         hv_ms += res["hv_ms"]
         hv_n += res["hv_launches"]
         launches += res["launches"]
@@ -227,73 +295,160 @@ def run_ours(args, world, rank, local):
     barrier(world)
     clocks = clk.stop() if clk else None
     ms = max_over_ranks(e0.elapsed_time(e1), world)
-    ms_step = ms / args.steps
-    rows_per_step = D * steps
-    value = whole_job_rate(rows_per_step * args.steps, world, ms / 1e3)
+    return dict(ms=ms, hv_avg_ms=hv_ms / max(hv_n, 1), launches=launches, res=res, clocks=clocks, n=n)
 
-    # end to end: host (pinned) start vector -> device each step, energies back to the host
-    # (skipped above 16 GB of host vector: the 6x6 sector's would be 73 GB)
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1703_03637_gb300 as hp
+
+    torch.cuda.set_device(local)
+    W = wl.workload(args.workload)
+    spec = W["model"]
+    steps = args.lanczos_steps or BENCH_LANCZOS_STEPS.get(args.workload, W["steps"])
+    prec = hp.FP64 if args.prec == "fp64" else hp.FP32
+    seed = wl.START_SEED + rank
+    m = hp.Model.from_spec(spec)
+    D = m.dim
+    esz = (8 if prec == hp.FP64 else 4) * (2 if m.is_complex else 1)
+    # end-to-end input: a start vector in pinned host memory, made before the workspace exists
+    host_v0 = None
+    e2e_note = None
+    if args.e2e:
+        need = D * 8 * (2 if m.is_complex else 1)
+        if need * 1.3 < host_ram_bytes():
+            host_v0 = pinned_gaussian(D, seed, m.is_complex)
+            torch.cuda.empty_cache()
+        else:
+            e2e_note = f"not run: a {need / 1e9:.0f} GB pinned start vector does not fit the host memory"
+    # untimed set-up: the launch shapes of both precisions
+    tune = None
+    if args.autotune:
+        tune = {"fp64" if prec == hp.FP64 else "fp32": m.autotune(prec)}
+        if args.mixed and prec == hp.FP64:
+            tune["fp32"] = m.autotune(hp.FP32)
+    m.release_workspace()
+    t = timed_lanczos(m, steps, prec, seed, args, world, local, rank)
+    ms_step = t["ms"] / t["n"]
+    res = t["res"]
+    value = whole_job_rate(D * steps * t["n"], world, t["ms"] / 1e3)
     e2e = None
-    if D * 8 <= 16e9:
-        e2e = run_e2e_lanczos(m, D, seed, steps, prec, args, world)
-
-    # mixed precision (fp32 vectors, fp64 reductions) + fp64 Rayleigh-quotient refinement on the
-    # same workload, timed the same way, with its energy error against the fp64 run
+    if host_v0 is not None:
+        e2e = run_e2e_lanczos(m, D, seed, steps, prec, args, world, host_v0)
+        del host_v0
+    # mixed precision (fp32 vectors, fp64 reductions) + fp64 Ritz vector and Rayleigh quotient
     mixed = None
     if args.mixed and prec == hp.FP64:
-        m.lanczos(steps, prec=hp.FP32, seed=seed, refine=True)
-        torch.cuda.synchronize()
-        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nmix = max(1, min(args.steps, 2))
-        e2.record(stream)
-        for _ in range(nmix):
-            rm = m.lanczos(steps, prec=hp.FP32, seed=seed, refine=True)
-        e3.record(stream)
-        torch.cuda.synchronize()
-        ms_mix = max_over_ranks(e2.elapsed_time(e3), world) / nmix
+        m.release_workspace()
+        a = argparse.Namespace(**vars(args))
+        a.warmup = 1
+        tm = timed_lanczos(m, steps, hp.FP32, seed, a, world, local, rank, refine=True, n=1)
+        rm = tm["res"]
         e64 = float(res["eig"][0])
-        mixed = {"value": round(whole_job_rate(rows_per_step, world, ms_mix / 1e3), 4), "unit": "Gelem/s",
-                 "ms_per_step": round(ms_mix, 3), "lanczos_steps_per_s": round(steps / (ms_mix / 1e3), 2),
-                 "includes": "fp32 Lanczos (basis kept in HBM) + fp64 Ritz vector, fp64 H x, Rayleigh quotient",
-                 "e_refined": rm["e_refined"], "e_fp64": e64,
+        ms_mix = tm["ms"]
+        mixed = {"value": round(whole_job_rate(D * steps, world, ms_mix / 1e3), 4), "unit": "Gelem/s",
+                 "ms_per_step": round(ms_mix, 3), "lanczos_steps_per_s": round(steps / (ms_mix / 1e3), 3),
+                 "includes": "fp32 Lanczos + fp64 Ritz vector (stored basis if it fits in 60% of free HBM, "
+                             "else a replayed second pass), fp64 H x, Rayleigh quotient, residual",
+                 "e_refined": rm["e_refined"], "e_fp64": e64, "e_fp32_ritz": float(rm["eig"][0]),
                  "rel_energy_diff_vs_fp64": abs(rm["e_refined"] - e64) / abs(e64),
-                 "residual": rm["residual"], "speedup_vs_fp64": round(ms_step / ms_mix, 3)}
-
+                 "residual": rm["residual"], "speedup_vs_fp64": round(ms_step / ms_mix, 3),
+                 "fused_hv_ms": round(tm["hv_avg_ms"], 3)}
+    m.release_workspace()
+    m.close()
+    torch.cuda.empty_cache()
+    sub = run_hubbard_sub(args, world, local, rank) if (args.sub and args.workload != "hubbard_4x4_8u8d") else None
     if rank != 0:
         return None
+    out = assemble_lanczos_line(args, world, spec, D, steps, prec, esz, value, ms_step, t, e2e, e2e_note, mixed, tune)
+    if sub is not None:
+        out["hubbard_4x4_8u8d"] = sub
+    return out
+
+
+def hv_group_kernels(spec, m, prec):
+    """The kernels of one fused Lanczos pass-1 launch group, as the library picks them."""
+    import paper_1703_03637_gb300 as hp
+    if spec.kind == wl.SPIN and spec.basis == wl.BASIS_SZ and not m.is_complex:
+        ks = "k_quant + k_sec_hi + k_sec_lo" if prec == hp.FP64 else "k_sec_hi + k_sec_lo"
+        return ks + " (split-row H v fused with Lanczos pass 1; k_maxexp in the first step only)"
+    return hv_group_name(spec, m, prec, 1, "Lanczos pass 1")
+
+
+def assemble_lanczos_line(args, world, spec, D, steps, prec, esz, value, ms_step, t, e2e, e2e_note, mixed, tune):
+    import paper_1703_03637_gb300 as hp
     hbm, src = peaks()
-    bytes_row = 3 * esz   # fused H v + Lanczos pass 1: gather-read C once, read P, write P
-    hv_avg_ms = hv_ms / max(hv_n, 1)
+    bytes_row = 3 * esz   # fused H v + Lanczos pass 1: read C once, read P, write P
+    hv_avg_ms = t["hv_avg_ms"]
     achieved = D * bytes_row / (hv_avg_ms / 1e3) / 1e9
+    traffic = MEASURED_TRAFFIC.get((args.workload, args.prec))
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": MEASURED_TRAFFIC.get((args.workload, args.prec)),
-            "peak_source": src,
-            "kernel": hv_group_name(spec, m, prec, 1, "Lanczos pass 1"), "kernel_avg_ms": round(hv_avg_ms, 4),
+            "frac": round(achieved / hbm, 4), "traffic": traffic[0] if traffic else None,
+            "traffic_source": traffic[1] if traffic else "no ncu capture of this kernel version",
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
+            "kernel": hv_group_kernels(spec, hp_model_stub(spec), prec), "kernel_avg_ms": round(hv_avg_ms, 4),
             "algorithmic_bytes_per_launch": D * bytes_row}
+    if prec == hp.FP64 and spec.kind == wl.SPIN and spec.basis == wl.BASIS_SZ:
+        ops = SEC_FP64_OPS_PER_ROW * D
+        roof["fp64_pipe"] = {"ops_per_row": SEC_FP64_OPS_PER_ROW, "achieved_tops": round(ops / (hv_avg_ms / 1e3) / 1e12, 4),
+                             "peak_tops": FP64_PEAK_TOPS, "frac": round(ops / (hv_avg_ms / 1e3) / 1e12 / FP64_PEAK_TOPS, 4),
+                             "peak_source": "fp64 FMA throughput probe on this pool's GB300 (DFMA 0.50 T thread-op/s; "
+                                            "int64->fp64 conversions 0.60 T/s)"}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == hp.FP64 else "f32+f64acc", "data": "synthetic",
-        "config": {"workload": args.workload, "dim": D, "lanczos_steps": steps, "model": spec.name,
+        "config": {"workload": args.workload, "dim": D, "lanczos_steps_per_bench_step": steps,
+                   "workload_lanczos_steps": wl.workload(args.workload)["steps"], "model": spec.name,
                    "sector": {0: "full", 1: f"S^z: n_up={spec.n_a}", 2: f"N_up={spec.n_a}, N_dn={spec.n_b}"}[spec.basis],
-                   "start": "philox gaussian, seed 123432+rank", "l2": l2_note(D * esz),
-                   "parallelism": f"replicas{world}"},
-        "lanczos_steps_per_s": round(steps / (ms_step / 1e3), 2),
-        "e0": res["eig"][0], "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                   "start": "philox gaussian, seed 123432+rank, generated inside each bench step",
+                   "l2": l2_note(D * esz), "parallelism": f"replicas{world}"},
+        "lanczos_steps_per_s": round(steps / (ms_step / 1e3), 3),
+        "e0": t["res"]["eig"][0], "roofline": roof, "e2e": e2e, "gpu_launches": t["launches"], "clocks": t["clocks"],
     }
+    if e2e is None and e2e_note:
+        out["e2e_note"] = e2e_note
     if mixed is not None:
         out["mixed"] = mixed
     if tune is not None:
         out["autotune"] = tune
-    if args.cpu_baseline and D * 16 <= 16e9:
-        rps, n, dt, cores = oracle_rows_per_s(spec)
-        out["cpu_baseline"] = {"value": round(rps / 1e9, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
-                               "sample": f"oracle H v on {n} contiguous rows of the same sector ({dt:.1f} s, "
-                                         f"OpenMP over {cores} host threads); a Lanczos step is one such H v per row"}
-    elif args.cpu_baseline:
-        out["cpu_baseline"] = None
-        out["cpu_baseline_note"] = "not run: the oracle needs the whole input vector in host memory (16 B per row)"
+    if args.cpu_baseline:
+        out["cpu_baseline"] = oracle_baseline(spec)
     return out
+
+
+def hp_model_stub(spec):
+    """The is_complex flag hv_group_name needs, without building a model."""
+    class _S:
+        is_complex = spec.is_complex
+    return _S()
+
+
+def run_hubbard_sub(args, world, local, rank):
+    """The 4x4 Hubbard Lanczos line (200 fp64 steps per run, autotuned two-pass kernels) as a
+    sub-object of the default line."""
+    import torch
+    import paper_1703_03637_gb300 as hp
+    W = wl.workload("hubbard_4x4_8u8d")
+    spec = W["model"]
+    m = hp.Model.from_spec(spec)
+    D = m.dim
+    tune = m.autotune(hp.FP64)
+    t = timed_lanczos(m, W["steps"], hp.FP64, wl.START_SEED, args, world, local, rank)
+    m.close()
+    torch.cuda.empty_cache()
+    hbm, _ = peaks()
+    ms_step = t["ms"] / t["n"]
+    achieved = D * 24 / (t["hv_avg_ms"] / 1e3) / 1e9
+    traffic = MEASURED_TRAFFIC.get(("hubbard_4x4_8u8d", "fp64"))
+    return {"value": round(whole_job_rate(D * W["steps"] * t["n"], world, t["ms"] / 1e3), 4), "unit": "Gelem/s",
+            "ms_per_step": round(ms_step, 3), "lanczos_steps": W["steps"],
+            "lanczos_steps_per_s": round(W["steps"] / (ms_step / 1e3), 2), "e0": t["res"]["eig"][0],
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": traffic[0] if traffic else None,
+                         "kernel": "k_quant + k_hub_dn + k_hub_up_q (Lanczos pass 1)",
+                         "kernel_avg_ms": round(t["hv_avg_ms"], 4), "algorithmic_bytes_per_launch": D * 24},
+            "autotune": tune, "gpu_launches": t["launches"], "clocks": t["clocks"]}
 
 
 def run_tpq(args, world, rank, local):
@@ -443,35 +598,47 @@ def run_sectors(args, world, rank, local):
 
 
 def run_reference(args, world, rank):
-    """The CPU oracle, as it stands, on a bounded slice of the same workload per step."""
+    """The CPU oracle, as it stands, on the host cores: each step is a bounded sample of the same
+    workload's H v -- a slice of rows when the oracle can hold the input vector in host memory,
+    else randomly sampled rows whose input elements it regenerates from their Philox index."""
     if rank != 0:
         return None
     import oracle
     W = wl.workload(args.workload)
     spec = W["model"]
     D = oracle.dim(spec)
-    if D * 16 > 16e9:
-        return {"impl": "reference", "unavailable": "the oracle needs the whole input vector in host memory "
-                                                    f"({D * 16 / 1e9:.0f} GB for this workload)"}
-    rng = np.random.default_rng(0)
-    v = np.empty(D, dtype=np.complex128)
-    v.real = rng.standard_normal(D)
-    v.imag = 0.0
-    n = min(300_000, D)
-    for _ in range(args.warmup):
-        oracle.apply_H_slice(spec, v, 0, n // 10)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        oracle.apply_H_slice(spec, v, (k * n) % max(D - n, 1), n)
-    dt = time.perf_counter() - t0
     cores = os.cpu_count() or 1
+    if D * 16 <= 16e9:
+        rng = np.random.default_rng(0)
+        v = np.empty(D, dtype=np.complex128)
+        v.real = rng.standard_normal(D)
+        v.imag = 0.0
+        n = min(300_000, D)
+        for _ in range(args.warmup):
+            oracle.apply_H_slice(spec, v, 0, n // 10)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            oracle.apply_H_slice(spec, v, (k * n) % max(D - n, 1), n)
+        dt = time.perf_counter() - t0
+        sample = f"oracle H v on {n} contiguous rows per step of the {args.workload} basis"
+    else:
+        rng = np.random.default_rng(0)
+        n = 200_000
+        for _ in range(args.warmup):
+            oracle.apply_H_rows_philox(spec, np.sort(rng.integers(0, D, size=n // 10)).astype(np.uint64), 777, False)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.apply_H_rows_philox(spec, np.sort(rng.integers(0, D, size=n)).astype(np.uint64), 777, False)
+        dt = time.perf_counter() - t0
+        sample = (f"oracle H v on {n} randomly sampled rows per step of the {args.workload} basis, input elements "
+                  f"regenerated from the Philox definition of the start vector")
     val = n * args.steps / dt / 1e9
     return {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "Gelem/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "dim": D, "parallelism": "host cores"},
             "cpu_baseline": {"value": round(val, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
-                             "sample": f"oracle H v on {n} rows per step of the {args.workload} sector"},
+                             "sample": sample},
             "e2e": {"value": round(val, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -481,7 +648,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hubbard_4x4_8u8d", choices=wl.WORKLOADS)
+    ap.add_argument("--workload", default="heisenberg_6x6_sz0", choices=wl.WORKLOADS)
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--lanczos-steps", "--iters", dest="lanczos_steps", type=int, default=0,
                     help="Lanczos steps (or mTPQ multiplications) per benchmark step; 0: the workload's "
@@ -489,6 +656,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false", help="skip the fp32 + fp64-refinement run")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", help="use the built-in launch shape")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the pinned-host-start-vector run")
+    ap.add_argument("--no-sub", dest="sub", action="store_false", help="skip the 4x4 Hubbard sub-line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

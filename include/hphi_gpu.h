@@ -144,6 +144,14 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
  * held by every GPU that loads the library until the process exits. */
 int hphi_apply_H_noalloc(hphi_model* m, const void* v, void* w, void* stream);
 
+/* Frees the solver workspace of m (the vectors and scratch that hphi_apply_H,
+ * hphi_lanczos_run, hphi_tpq_run and hphi_autotune allocate on first use and keep); the terms,
+ * basis tables and launch choices stay.  The next call allocates what it needs again.  Waits
+ * for the device first (cudaDeviceSynchronize).  Useful between runs of different precision or
+ * size on large bases, whose buffers would otherwise stay at their largest size.  No
+ * counterpart in the paper. */
+int hphi_release_workspace(hphi_model* m);
+
 /* ---------------------------------------------------------------- autotuning */
 
 typedef struct {
@@ -208,7 +216,9 @@ int hphi_set_window_bits(hphi_model* m, int bits);
  * transform: element e = r * nvec + c uses counter (e mod 2^32, e >> 32, 0, 0) and key
  * (seed mod 2^32, seed >> 32); the four output words give two 53-bit uniforms
  * u_a = ((w0 << 21) | (w1 >> 11)) + 0.5) / 2^53 and u_b likewise from w2, w3; the real part
- * is sqrt(-2 ln u_a) cos(2 pi u_b) and the imaginary part (complex models) the sine.
+ * is sqrt(-2 ln u_a) cos(2 pi u_b) and the imaginary part (complex models) the sine, in fp64
+ * for prec = HPHI_FP64.  For prec = HPHI_FP32 the same two uniforms are rounded to fp32 and
+ * the transform runs in fp32 arithmetic (values within a few fp32 ulps of the fp64 numbers).
  * This replaces the paper's dSFMT draws (appendix A.2 / A.4), whose stream depends on the
  * process count. */
 int hphi_random_vector(hphi_model* m, void* v, int nvec, int prec, uint64_t seed, void* stream);
@@ -236,6 +246,12 @@ typedef struct {
                           (section 3.4's second pass), stopping after the last step whose
                           Ritz coefficient still matters at the storage precision; 0 keep
                           them when they fit in 60% of the free device memory, else replay */
+  int v0_on_host;      /* 1: v0 is a HOST array [dim] of fp64 (complex128 for complex models),
+                          copied by the call into its own first Lanczos vector (for prec =
+                          HPHI_FP32 through the model's fp64 work vector), so the caller needs no
+                          device copy of it; the refinement's second pass copies it again.  Such
+                          runs launch their kernels one by one instead of as one CUDA graph.
+                          Pinned (page-locked) memory copies fastest.  0: v0 is a device array */
 } hphi_lanczos_params;
 
 typedef struct {

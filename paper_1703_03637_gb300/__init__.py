@@ -30,6 +30,7 @@ EXPORTS = [
     "hphi_build_sector", "hphi_dim", "hphi_is_complex", "hphi_basis_states", "hphi_basis_ranks", "hphi_apply_H",
     "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run", "hphi_apply_H_noalloc",
     "hphi_lanczos_run_sectors", "hphi_autotune", "hphi_set_window_bits", "hphi_set_sector_split",
+    "hphi_release_workspace",
 ]
 
 
@@ -42,7 +43,7 @@ class LibraryError(RuntimeError):
 class LanczosParams(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("v0", ctypes.c_void_p),
                 ("n_eig", ctypes.c_int), ("refine", ctypes.c_int), ("breakdown", ctypes.c_double),
-                ("profile", ctypes.c_int), ("keep_basis", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("keep_basis", ctypes.c_int), ("v0_on_host", ctypes.c_int)]
 
 
 class LanczosResult(ctypes.Structure):
@@ -116,6 +117,7 @@ def load(build_if_missing: bool = True):
         L.hphi_autotune.argtypes = [P, I, ctypes.POINTER(TuneResult), P]
         L.hphi_set_window_bits.argtypes = [P, I]
         L.hphi_set_sector_split.argtypes = [P, I, I, I, P]
+        L.hphi_release_workspace.argtypes = [P]
         L.hphi_lanczos_run_sectors.argtypes = [P, P, I, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         _lib = L
         return L
@@ -270,6 +272,11 @@ class Model:
         _torch()
         self._check(self._L.hphi_set_sector_split(self._h, prec, int(L), int(K), _stream()))
 
+    def release_workspace(self):
+        """Free the solver workspace (vectors and scratch kept between calls); tables stay."""
+        _torch()
+        self._check(self._L.hphi_release_workspace(self._h))
+
     def set_window_bits(self, bits: int):
         """Window passes of the many-vector H v: 0 automatic, -1 off, else the window's sites."""
         self._check(self._L.hphi_set_window_bits(self._h, int(bits)))
@@ -304,15 +311,28 @@ class Model:
         return out
 
     def lanczos(self, steps: int, prec=FP64, seed: int = 123432, v0=None, n_eig: int = 1, refine: bool = False,
-                breakdown: float = 0.0, profile: bool = False, keep_basis: int = 0):
-        """Section 3.4 Lanczos; returns dict(alpha, beta, steps, eig, e_refined, residual, variance, ms)."""
+                breakdown: float = 0.0, profile: bool = False, keep_basis: int = 0, v0_on_host: bool = False):
+        """Section 3.4 Lanczos; returns dict(alpha, beta, steps, eig, e_refined, residual, variance, ms).
+        v0: start vector (a CUDA tensor, or any tensor moved to the device here); with v0_on_host
+        it must be a host tensor, which the library copies in itself (hphi_lanczos_params.v0_on_host)."""
         torch = _torch()
-        if v0 is not None:
+        on_host = v0 is not None and v0_on_host
+        if on_host:  # the library copies the host vector itself (no device copy is made here)
+            if v0.is_cuda:
+                raise LibraryError(-1, "v0_on_host: v0 must be a host tensor")
+            want = torch.complex128 if self.is_complex else torch.float64
+            if v0.dtype != want or not v0.is_contiguous() or v0.numel() != self.dim:
+                raise LibraryError(-1, f"host v0 must be a contiguous {want} tensor of length dim")
+            vptr = ctypes.c_void_p(v0.data_ptr())
+        elif v0 is not None:
             v0 = v0.to(device="cuda", dtype=torch.complex128 if self.is_complex else torch.float64).contiguous()
+            vptr = _dptr(v0)
+        else:
+            vptr = None
         a = np.zeros(steps)
         b = np.zeros(steps)
-        p = LanczosParams(steps, prec, seed, _dptr(v0) if v0 is not None else None, n_eig, int(refine), breakdown,
-                          int(profile), int(keep_basis))
+        p = LanczosParams(steps, prec, seed, vptr, n_eig, int(refine), breakdown, int(profile), int(keep_basis),
+                          int(on_host))
         r = LanczosResult()
         r.alpha = a.ctypes.data
         r.beta = b.ctypes.data
@@ -334,7 +354,7 @@ class Model:
         for i in range(ns):
             res[i].alpha = al[i].ctypes.data
             res[i].beta = be[i].ctypes.data
-        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0, int(keep_basis))
+        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0, int(keep_basis), 0)
         self._check(self._L.hphi_lanczos_run_sectors(self._h, nu.ctypes.data, ns, ctypes.byref(p), res, _stream()))
         out = []
         for i in range(ns):

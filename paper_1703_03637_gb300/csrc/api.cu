@@ -1042,6 +1042,15 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
   return s.code ? fail(m, s) : HPHI_OK;
 }
 
+int hphi_release_workspace(hphi_model* m) {
+  if (!m) return HPHI_ERR_INVALID_ARG;
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(m, HPHI_ERR_CUDA, std::string("release_workspace: ") + cudaGetErrorString(e));
+  Workspace& ws = m->ws;
+  for (DBuf* b : {&ws.vecA, &ws.vecB, &ws.x, &ws.partials, &ws.scal, &ws.work, &ws.basis}) b->release();
+  return HPHI_OK;
+}
+
 int hphi_set_window_bits(hphi_model* m, int bits) {
   if (!m) return HPHI_ERR_INVALID_ARG;
   if (bits < -1 || bits > 32) return fail(m, HPHI_ERR_INVALID_ARG, "window bits: -1, 0 or 1..32");
@@ -1227,6 +1236,7 @@ struct LzPlan {
   int* flags = nullptr;
   double brk = 1e-13;
   const double* v0 = nullptr;
+  const double* v0_host = nullptr;  // start vector in host memory (copied in by start())
   uint64_t seed = 0;
   int launches = 0;
   std::vector<cudaEvent_t> ev;  // profile: events around every fused H v launch
@@ -1245,6 +1255,10 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   L.refine = p->refine != 0;
   L.profile = p->profile != 0;
   L.v0 = reinterpret_cast<const double*>(p->v0);
+  if (p->v0_on_host && p->v0) {
+    L.v0_host = L.v0;
+    L.v0 = nullptr;
+  }
   L.seed = p->seed;
   L.brk = p->breakdown > 0 ? p->breakdown : 1e-13;
   const int steps = L.steps, prec = L.prec;
@@ -1272,7 +1286,7 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   }
   if ((s = ws.vecA.ensure(L.store ? (size_t)8 * (size_t)L.n_real : need_a)).code) return s;
   if (!L.store && (s = ws.vecB.ensure(vbytes)).code) return s;
-  if (L.refine && (s = ws.x.ensure(8 * (size_t)L.n_real)).code) return s;
+  if ((L.refine || (L.v0_host && prec != HPHI_FP64)) && (s = ws.x.ensure(8 * (size_t)L.n_real)).code) return s;
   if (use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1)) {
     size_t need = hphi::hub_scratch_bytes(m->hdev, prec, hphi::Epi::kLanczos1);
     if (L.refine) need = std::max(need, hphi::hub_scratch_bytes(m->hdev, HPHI_FP64, hphi::Epi::kRefine));
@@ -1340,8 +1354,16 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   };
   void* c0 = L.store ? slot(0) : ws.vecA.p;
   void* p0 = L.store ? slot(1) : ws.vecB.p;
+  // fp32 runs take a host start vector through the fp64 vector x, which lz_init reads before
+  // the second pass clears it
+  const double* v0_dev = L.v0 ? L.v0 : ((L.v0_host && prec != HPHI_FP64) ? ws.x.as<double>() : nullptr);
   auto start = [&]() -> hphi::Status {
     if (L.v0) return {};
+    if (L.v0_host) {  // copied in again for the second pass
+      void* dst = prec == HPHI_FP64 ? c0 : ws.x.p;
+      HPHI_CUDA_TRY(cudaMemcpyAsync(dst, L.v0_host, 8 * (size_t)L.n_real, cudaMemcpyHostToDevice, st));
+      return {};
+    }
     ++L.launches;  // buffer A holds C_0 (regenerated bit-identically for the second pass)
     return hphi::launch_random(c0, m->dim, cplx, prec == HPHI_FP64, L.seed, st);
   };
@@ -1357,7 +1379,7 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   auto run_pass = [&](bool with_x) -> hphi::Status {
     hphi::Status q;
     L.launches += 2 + (3 + hv_kernels(m, prec, 1, hphi::Epi::kLanczos1)) * steps - (emax ? steps - 1 : 0);
-    if ((q = hphi::launch_lz_init(prec, cplx, L.v0, c0, p0, L.n_real, L.partials, L.vgrid, st)).code) return q;
+    if ((q = hphi::launch_lz_init(prec, cplx, v0_dev, c0, p0, L.n_real, L.partials, L.vgrid, st)).code) return q;
     if ((q = hphi::launch_lz_init_fin(L.lz, L.partials, L.vgrid, st)).code) return q;
     if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)L.n_real, st));
     void* C = c0;
@@ -1518,9 +1540,9 @@ hphi::Status lanczos_impl(hphi_model* m, const hphi_lanczos_params* p, hphi_lanc
   Timer tm;
   HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
   HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
-  if (L.profile) {
+  if (L.profile || L.v0_host) {
     // profiled runs launch eagerly: events recorded inside a captured graph cannot be
-    // queried with cudaEventElapsedTime
+    // queried with cudaEventElapsedTime; so do runs copying a host start vector
     HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
     if ((s = lz_enqueue(L, st)).code) return s;
     HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));

@@ -767,7 +767,8 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
   const R coef0 = (R)d.coef[0];
   const int n_str = d.n_str;
   const uint32_t pad2 = (uint32_t)d.nq_max | ((uint32_t)d.nq_max << 16);
-  Red<FIX> red;
+  constexpr int NQ = n_red<E>() > 0 ? n_red<E>() : 1;  // reduced quantities of the epilogue
+  Red<FIX, NQ> red;
   red.zero();
 
   for (int64_t t = blockIdx.x; t < d.n_tiles; t += gridDim.x) {
@@ -915,7 +916,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
           const T wv = Wh[idx];
           if constexpr (!FIX) {
             const R hv = ONE ? dg * xq + coef0 * (acc[e][m] + wv) : dg * xq + (acc[e][m] + wv);
-            epilogue<float, E>(idx, 0, xq, 0.f, hv, 0.f, reinterpret_cast<float*>(w), fa, es, s_inv, red);
+            epilogue<float, E, NQ>(idx, 0, xq, 0.f, hv, 0.f, reinterpret_cast<float*>(w), fa, es, s_inv, red);
           } else {
             const long long S = acc[e][m] + wv;
             const double xr = __ll2double_rn(xq);
@@ -933,7 +934,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
             } else {
               const double x = fix_to_double(xq, eoff);
               const double hv = fma((double)dg, x, d.unit * fix_to_double(S, eoff));
-              epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, reinterpret_cast<double*>(w), fa, es, s_inv, red);
+              epilogue<double, E, NQ>(idx, 0, x, 0.0, hv, 0.0, reinterpret_cast<double*>(w), fa, es, s_inv, red);
             }
           }
         }

@@ -41,16 +41,24 @@ __global__ void __launch_bounds__(kThreads) k_lz_init(const double* __restrict__
                                                        int64_t n_real, double* __restrict__ partials) {
   __shared__ double sm[kThreads];
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += (int64_t)gridDim.x * kThreads) {
-    R x;
-    if (v0 != nullptr) {
-      x = (R)v0[i];
-      C[i] = x;
-    } else {
-      x = C[i];
+  // four elements per thread and iteration, one grid stride apart (coalesced, loads first)
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += 4 * stride) {
+    R x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = i + u * stride;
+      x[u] = k < n_real ? (v0 != nullptr ? (R)v0[k] : C[k]) : (R)0;
     }
-    P[i] = (R)0;
-    acc = fma((double)x, (double)x, acc);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = i + u * stride;
+      if (k < n_real) {
+        if (v0 != nullptr) C[k] = x[u];
+        P[k] = (R)0;
+        acc = fma((double)x[u], (double)x[u], acc);
+      }
+    }
   }
   const double t = block_sum(acc, sm);
   if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kMaxRedQ] = t;
@@ -106,17 +114,31 @@ __global__ void __launch_bounds__(kThreads) k_lz_pass2(LzDev lz, const R* __rest
   const double g = lz.s[2];
   const R gr = (R)g;
   const double xc = X ? lz.s[3] : 0.0;
-  Red<F64> red;
+  Red<F64, 1> red;  // one reduced quantity, |P|^2
   red.zero();
   int mx = 0;
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += (int64_t)gridDim.x * kThreads) {
-    const R c = C[i];
-    const R p = P[i] - gr * c;
-    P[i] = p;
-    red.add(0, p, p);
-    red.tick();
-    if (X) x[i] = fma(xc, (double)c, x[i]);
-    if constexpr (F64) mx = max(mx, (int)((__double_as_longlong((double)p) >> 52) & 0x7ff));
+  // four elements per thread and iteration, one grid stride apart (coalesced, loads first)
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_real; i += 4 * stride) {
+    R c[4], pp[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = i + u * stride;
+      c[u] = k < n_real ? C[k] : (R)0;
+      pp[u] = k < n_real ? P[k] : (R)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = i + u * stride;
+      if (k < n_real) {
+        const R p = pp[u] - gr * c[u];
+        P[k] = p;
+        red.add(0, p, p);
+        red.tick();
+        if (X) x[k] = fma(xc, (double)c[u], x[k]);
+        if constexpr (F64) mx = max(mx, (int)((__double_as_longlong((double)p) >> 52) & 0x7ff));
+      }
+    }
   }
   if (F64 && emax != nullptr) {
 #pragma unroll

@@ -808,3 +808,33 @@ def test_heisenberg_6x6_sz0_full_size_lanczos_steps(prec):
         assert _rel(r["alpha"], r64["alpha"]) < 1e-6 and _rel(r["beta"], r64["beta"]) < 1e-6
     m.close()
     torch.cuda.empty_cache()
+
+
+def test_start_vector_fp32_transform():
+    """fp32 start vectors: the same Philox uniforms through Box-Muller in fp32 arithmetic, within
+    a few fp32 ulps (relative 1e-6, plus an absolute 1e-6 near zero) of the oracle's fp64
+    numbers, over 2^22 elements (including the tails)."""
+    spec = wl.heisenberg_ring(22)
+    m = hp.Model.from_spec(spec)
+    v = m.random_vector(4711, prec=hp.FP32).double().cpu().numpy()[:, 0]
+    ref = oracle.gauss_at(4711, np.arange(m.dim, dtype=np.uint64), False)
+    assert np.all(np.abs(v - ref) <= 1e-6 * np.abs(ref) + 1e-6)
+    assert np.max(np.abs(ref)) > 5.0  # the tail is present in the sample
+
+
+@pytest.mark.parametrize("name,mk", [
+    ("heisenberg_4x4_sz8_split", lambda: wl.heisenberg_square(4, 4).with_basis(wl.BASIS_SZ, 8)),
+    ("hubbard_2x4_44", lambda: wl.hubbard_square(4, 2).with_basis(wl.BASIS_NUMBER, 4, 4)),
+])
+def test_lanczos_start_vector_from_host(name, mk):
+    """A start vector in (pinned) host memory, copied in by the library itself, gives the run of
+    the same vector passed on the device, in both precisions and with the refinement's second
+    pass (which copies it again)."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    v0 = torch.as_tensor(wl.gaussian_vector(143, m.dim)[:, 0]).pin_memory()
+    for prec in (hp.FP64, hp.FP32):
+        dev = m.lanczos(30, prec=prec, v0=v0.cuda(), refine=True, keep_basis=-1)
+        host = m.lanczos(30, prec=prec, v0=v0, v0_on_host=True, refine=True, keep_basis=-1)
+        assert np.array_equal(dev["alpha"], host["alpha"]) and np.array_equal(dev["beta"], host["beta"])
+        assert dev["e_refined"] == host["e_refined"]
