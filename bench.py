@@ -323,7 +323,10 @@ def run_ours(args, world, rank, local):
             e2e_note = f"not run: a {need / 1e9:.0f} GB pinned start vector does not fit the host memory"
     # untimed set-up: the launch shapes of both precisions
     tune = None
-    if args.autotune:
+    if args.split:
+        L, K = (int(x) for x in args.split.split(","))
+        m.set_sector_split(prec, L, K)
+    elif args.autotune:
         tune = {"fp64" if prec == hp.FP64 else "fp32": m.autotune(prec)}
         if args.mixed and prec == hp.FP64:
             tune["fp32"] = m.autotune(hp.FP32)
@@ -658,6 +661,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", help="use the built-in launch shape")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the pinned-host-start-vector run")
     ap.add_argument("--no-sub", dest="sub", action="store_false", help="skip the 4x4 Hubbard sub-line")
+    ap.add_argument("--split", default="", help="L,K: fixed split-row shape of the S^z-sector kernels (no autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

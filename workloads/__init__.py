@@ -261,6 +261,11 @@ def workload(name: str) -> dict:
     if name == "j1j2_ring28_all_sectors":
         m = j1j2_ring(28, 1.0, 0.5)
         return dict(model=m, steps=150, sectors=list(range(29)), dim=1 << 28)
+    if name == "heisenberg_6x5_sz15":
+        # the 6x5 torus in its S^z = 0 sector (155,117,520 rows): the same split-row kernels as
+        # the 6x6 sector at a size for kernel profiling (a 1.24 GB fp64 vector, above L2)
+        m = heisenberg_square(6, 5).with_basis(BASIS_SZ, 15)
+        return dict(model=m, steps=100, prec="fp64", dim=math.comb(30, 15))
     if name == "heisenberg_6x6_sz0":
         m = heisenberg_square(6, 6).with_basis(BASIS_SZ, 18)
         return dict(model=m, steps=100, prec="mixed", dim=math.comb(36, 18))
@@ -268,4 +273,4 @@ def workload(name: str) -> dict:
 
 
 WORKLOADS = ["heisenberg_ring12_full", "hubbard_4x4_8u8d", "kitaev_24_tpq64", "j1j2_ring28_all_sectors",
-             "heisenberg_6x6_sz0", "kitaev_18_tpq64"]
+             "heisenberg_6x6_sz0", "kitaev_18_tpq64", "heisenberg_6x5_sz15"]
