@@ -518,25 +518,39 @@ Status sec_build(const SecTerms& t, int L, int K, SecTables** out, cudaStream_t 
     ++d.n_pc;
   }
   d.pc_row0[d.n_pc] = (uint32_t)hi_cls.size();
-  // row-pass tiles: chunks of 2^B consecutive high parts; in a chunk, class by class, up to K
-  // rows of one class per tile.  Straddling partners hi ^ 2^a with a < B share the chunk.
+  // row-pass tiles.  A row is read three times: staged by its own tile, and gathered by the
+  // tiles of its straddling partners hi ^ 2^a (a in S, the high bits of the straddling bonds),
+  // which lie one class above or below.  Blocks of high parts that agree outside S are closed
+  // under those flips; a block runs class by class, so a row's partners are read while its
+  // neighbouring classes run and it stays in L2 between the three reads.  Up to K rows of one
+  // class per tile.
   std::vector<uint32_t> hi_seq, tiles;
-  const int B = std::min(H, 8);
-  for (uint32_t c0 = 0; c0 < nH; c0 += (1u << B)) {
-    for (int i = 0; i < d.n_pc; ++i) {
-      const int p = d.pc_p[i];
-      int run = 0;
-      uint32_t start = 0;
-      for (uint32_t hi = c0; hi < c0 + (1u << B); ++hi) {
-        if (__builtin_popcount(hi) != p) continue;
-        if (run == 0) start = (uint32_t)hi_seq.size();
-        hi_seq.push_back(hi);
-        if (++run == K) {
-          tiles.push_back(start | ((uint32_t)(run - 1) << 24));
-          run = 0;
+  {
+    uint32_t S = 0;
+    for (int n = 0; n < d.n_str; ++n) S |= 1u << d.str_a[n];
+    // blocks of at least 2^8 high parts, so that the classes of a block fill tiles of K rows
+    for (int b = 0; b < H && __builtin_popcount(S) < std::min(H, 8); ++b) S |= 1u << b;
+    const uint32_t nonS = (uint32_t)(nH - 1) & ~S;
+    std::vector<uint32_t> sv;  // the 2^|S| settings of the bits of S
+    for (uint32_t x = S;; x = (x - 1) & S) {
+      sv.push_back(x);
+      if (x == 0) break;
+    }
+    std::sort(sv.begin(), sv.end());
+    std::vector<uint32_t> in_cls;
+    for (uint32_t o = 0;; o = ((o | S) + 1) & nonS) {  // the settings of the other bits, ascending
+      for (int i = 0; i < d.n_pc; ++i) {
+        const int p = d.pc_p[i];
+        in_cls.clear();
+        for (uint32_t x : sv)
+          if (__builtin_popcount(o | x) == p) in_cls.push_back(o | x);
+        for (size_t r = 0; r < in_cls.size(); r += (size_t)K) {
+          const size_t nk = std::min<size_t>((size_t)K, in_cls.size() - r);
+          tiles.push_back((uint32_t)hi_seq.size() | ((uint32_t)(nk - 1) << 24));
+          hi_seq.insert(hi_seq.end(), in_cls.begin() + (long)r, in_cls.begin() + (long)(r + nk));
         }
       }
-      if (run) tiles.push_back(start | ((uint32_t)(run - 1) << 24));
+      if (o == nonS) break;
     }
   }
   d.n_tiles = (int64_t)tiles.size();
@@ -714,7 +728,8 @@ __device__ __forceinline__ void tile_load(const T* p, T* out) {
 template <class T, int K, Epi E, int NT, bool ONE>
 __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDev d, const T* __restrict__ X,
                                                                     const T* Wh, void* w, FusedArgs fa,
-                                                                    const int* __restrict__ Ep) {
+                                                                    const int* __restrict__ Ep,
+                                                                    unsigned long long* __restrict__ claim) {
   using R = std::conditional_t<sizeof(T) == 4, float, double>;
   constexpr bool FIX = sizeof(T) == 8;
   constexpr int EL = (K >= 4) ? 1 : 4 / K;  // elements per thread
@@ -730,6 +745,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
   __shared__ const T* s_ptr[kSecMaxStr][K];  // partner row of row m through the bond
   __shared__ uint32_t s_hi0;
   __shared__ int s_nk;
+  __shared__ unsigned long long s_t;
   __shared__ T s_w[kSecMaxCls];
   __shared__ double s_inv[1];
   __shared__ double s_red[(NT / 32) * kMaxRedQ];
@@ -771,8 +787,14 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
   Red<FIX, NQ> red;
   red.zero();
 
-  for (int64_t t = blockIdx.x; t < d.n_tiles; t += gridDim.x) {
+  // tiles are claimed in order from a counter, so the tiles in flight stay a narrow window of
+  // the processing order (a fixed stride would let CTAs drift apart over thousands of tiles)
+  for (;;) {
     __syncthreads();  // the previous tile's rows are no longer read
+    if (tid == 0) s_t = atomicAdd(claim, 1ull);
+    __syncthreads();
+    const int64_t t = (int64_t)s_t;
+    if (t >= d.n_tiles) break;
     if (tid < K) {
       const uint32_t tw = __ldg(d.tiles + t);
       const uint32_t start = tw & 0xffffffu;
@@ -982,12 +1004,13 @@ int occupancy_of(KernelT kern, int nt, size_t smem) {
 
 template <class T, int K, Epi E, bool ONE>
 Status launch_lo_t(const SecDev& d, const T* X, const T* Wh, void* w, const FusedArgs& fa, const int* Ep, int grid,
-                   cudaStream_t st) {
+                   unsigned long long* claim, cudaStream_t st) {
   const size_t smem = lo_smem(d, (int)sizeof(T));
+  HPHI_CUDA_TRY(cudaMemsetAsync(claim, 0, sizeof(unsigned long long), st));
 #define HPHI_SECLO(NN)                                                                                        \
   HPHI_CUDA_TRY(cudaFuncSetAttribute(k_sec_lo<T, K, E, NN, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)smem));                                                             \
-  k_sec_lo<T, K, E, NN, ONE><<<grid, NN, smem, st>>>(d, X, Wh, w, fa, Ep);
+  k_sec_lo<T, K, E, NN, ONE><<<grid, NN, smem, st>>>(d, X, Wh, w, fa, Ep, claim);
   if (lo_threads(d, (int)sizeof(T)) == 1024) {
     HPHI_SECLO(1024)
   } else {
@@ -1007,11 +1030,11 @@ int lo_occupancy_t(const SecDev& d) {
 
 template <class T, Epi E>
 Status launch_lo_k(const SecDev& d, const T* X, const T* Wh, void* w, const FusedArgs& fa, const int* Ep, int grid,
-                   cudaStream_t st) {
+                   unsigned long long* claim, cudaStream_t st) {
   const bool one = d.one_cls != 0;
-#define HPHI_SECK(KK)                                                          \
-  return one ? launch_lo_t<T, KK, E, true>(d, X, Wh, w, fa, Ep, grid, st)      \
-             : launch_lo_t<T, KK, E, false>(d, X, Wh, w, fa, Ep, grid, st);
+#define HPHI_SECK(KK)                                                                 \
+  return one ? launch_lo_t<T, KK, E, true>(d, X, Wh, w, fa, Ep, grid, claim, st)      \
+             : launch_lo_t<T, KK, E, false>(d, X, Wh, w, fa, Ep, grid, claim, st);
   switch (d.K) {
     case 8: HPHI_SECK(8)
     case 4: HPHI_SECK(4)
@@ -1037,15 +1060,30 @@ Status launch_hi(const SecDev& d, const T* X, T* W, const int* done, unsigned lo
   HPHI_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   const int grid = num_sms() * 8;
   const bool one = d.one_cls != 0;
-  constexpr int EPT = sizeof(T) == 8 ? 2 : 4;  // 512-byte row segments per warp item
-  if (one) k_sec_hi<T, EPT, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
-  else k_sec_hi<T, EPT, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+  // stripes of 512 bytes per row, narrowed (down to one 32-element warp access) while one
+  // stripe of the largest class exceeds 48 MB: that stripe is the L2 working set
+  uint32_t rows = 0;
+  for (int i = 0; i < d.n_pc; ++i) rows = std::max(rows, d.pc_row0[i + 1] - d.pc_row0[i]);
+  int ept = sizeof(T) == 8 ? 2 : 4;
+  while (ept > 1 && (double)rows * 32.0 * ept * sizeof(T) > 48e6) ept /= 2;
+#define HPHI_SECHI(EE)                                                                     \
+  if (one) k_sec_hi<T, EE, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);       \
+  else k_sec_hi<T, EE, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+  if (ept == 4) {
+    HPHI_SECHI(4)
+  } else if (ept == 2) {
+    HPHI_SECHI(2)
+  } else {
+    HPHI_SECHI(1)
+  }
+#undef HPHI_SECHI
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
 
 // scratch layout: fp64 [Q: dim int64][W: dim int64, Lanczos only][tail]; fp32 [W: dim float,
-// Lanczos only][tail]; tail = 256 bytes: exponent (int) at 0, counter (u64) at 64
+// Lanczos only][tail]; tail = 256 bytes: exponent (int) at 0, pass-H counter (u64) at 64,
+// pass-R tile counter (u64) at 128
 size_t vec_bytes(const SecDev& d, int esz) { return (((size_t)d.dim * esz + 255) / 256) * 256; }
 
 }  // namespace
@@ -1083,6 +1121,7 @@ Status launch_sec(const SecDev& d, int prec, const void* v, void* w, void* scrat
   char* tail = sc + sec_scratch_bytes(d, prec, epi) - 256;
   int* Ep = reinterpret_cast<int*>(tail);
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(tail + 64);
+  unsigned long long* claim = reinterpret_cast<unsigned long long*>(tail + 128);
   // the output buffer receives the pass-H sums and is finished in place, except in Lanczos
   // steps, whose output (P) is also an input: their sums go to the scratch vector
   void* out = (epi == Epi::kStore) ? w : fa.out;
@@ -1095,10 +1134,10 @@ Status launch_sec(const SecDev& d, int prec, const void* v, void* w, void* scrat
     if (s.code) return s;
     if ((s = launch_hi<long long>(d, Q, W, fa.done, counter, st)).code) return s;
     switch (epi) {
-      case Epi::kStore: return launch_lo_k<long long, Epi::kStore>(d, Q, W, w, fa, Ep, grid, st);
-      case Epi::kLanczos1: return launch_lo_k<long long, Epi::kLanczos1>(d, Q, W, w, fa, Ep, grid, st);
-      case Epi::kTpq: return launch_lo_k<long long, Epi::kTpq>(d, Q, W, w, fa, Ep, grid, st);
-      case Epi::kRefine: return launch_lo_k<long long, Epi::kRefine>(d, Q, W, w, fa, Ep, grid, st);
+      case Epi::kStore: return launch_lo_k<long long, Epi::kStore>(d, Q, W, w, fa, Ep, grid, claim, st);
+      case Epi::kLanczos1: return launch_lo_k<long long, Epi::kLanczos1>(d, Q, W, w, fa, Ep, grid, claim, st);
+      case Epi::kTpq: return launch_lo_k<long long, Epi::kTpq>(d, Q, W, w, fa, Ep, grid, claim, st);
+      case Epi::kRefine: return launch_lo_k<long long, Epi::kRefine>(d, Q, W, w, fa, Ep, grid, claim, st);
     }
   } else {
     const float* X = reinterpret_cast<const float*>(v);
@@ -1106,9 +1145,9 @@ Status launch_sec(const SecDev& d, int prec, const void* v, void* w, void* scrat
     Status s = launch_hi<float>(d, X, W, fa.done, counter, st);
     if (s.code) return s;
     switch (epi) {
-      case Epi::kStore: return launch_lo_k<float, Epi::kStore>(d, X, W, w, fa, Ep, grid, st);
-      case Epi::kLanczos1: return launch_lo_k<float, Epi::kLanczos1>(d, X, W, w, fa, Ep, grid, st);
-      case Epi::kTpq: return launch_lo_k<float, Epi::kTpq>(d, X, W, w, fa, Ep, grid, st);
+      case Epi::kStore: return launch_lo_k<float, Epi::kStore>(d, X, W, w, fa, Ep, grid, claim, st);
+      case Epi::kLanczos1: return launch_lo_k<float, Epi::kLanczos1>(d, X, W, w, fa, Ep, grid, claim, st);
+      case Epi::kTpq: return launch_lo_k<float, Epi::kTpq>(d, X, W, w, fa, Ep, grid, claim, st);
       case Epi::kRefine: break;
     }
   }
