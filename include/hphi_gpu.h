@@ -252,6 +252,13 @@ typedef struct {
                           device copy of it; the refinement's second pass copies it again.  Such
                           runs launch their kernels one by one instead of as one CUDA graph.
                           Pinned (page-locked) memory copies fastest.  0: v0 is a device array */
+  double eps;          /* appendix C's convergence test (LanczosEps): after 5 steps and then
+                          every 2, the first excited eigenvalue of T_n is found on the device
+                          and the run stops when it agrees with the previous test's value to
+                          eps relative; steps is then the limit.  0: run all steps       */
+  void* ritz_out;      /* optional device fp64 [dim] (complex128 for complex models): with
+                          refine = 1 receives the fp64 Ritz vector x of the lowest eigenvalue
+                          (the start of hphi_inverse_iteration); NULL: not copied out     */
 } hphi_lanczos_params;
 
 typedef struct {
@@ -266,6 +273,7 @@ typedef struct {
   float hv_ms;         /* profile = 1: summed device time of the fused H v launches       */
   int hv_launches;     /* number of fused H v launches timed in hv_ms                      */
   int kernel_launches; /* CUDA kernels this call launched                                   */
+  int converged;       /* 1 when the eps test ended the run (steps_done < steps possible)  */
 } hphi_lanczos_result;
 
 /* Lanczos recurrence of section 3.4 (alpha_k = (H v_k, v_k), w = H v_k - beta_k v_{k-1} -
@@ -287,6 +295,37 @@ int hphi_lanczos_run(hphi_model* m, const hphi_lanczos_params* p, hphi_lanczos_r
 int hphi_lanczos_run_sectors(hphi_model* m, const int* n_up_list, int n_sectors, const hphi_lanczos_params* p,
                              hphi_lanczos_result* results, void* stream);
 
+/* ---------------------------------------------------------------- inverse iteration (section 3.4.1) */
+
+typedef struct {
+  double energy;       /* E_n: the eigenvalue estimate (e.g. hphi_lanczos_result.eig[0])   */
+  double shift;        /* delta > 0: the CG operator is H - E_n + delta, positive definite
+                          when E_n is at most delta above the lowest eigenvalue;
+                          0 -> 1e-4 * max(1, |E_n|)                                        */
+  int outer;           /* inverse-iteration steps y_k -> y_{k+1}: 1..64                     */
+  int max_cg;          /* CG iterations per solve: 1..100000                               */
+  double cg_tol;       /* a solve stops when |r| <= cg_tol |b| (0 -> 1e-12)               */
+} hphi_invit_params;
+
+typedef struct {
+  double e;            /* <x|H|x> of the final unit vector                                 */
+  double residual;     /* |H x - e x|                                                       */
+  double variance;     /* <x|H^2|x> - e^2                                                   */
+  int cg_steps;        /* CG iterations run over all solves                                */
+  float device_ms;     /* device time of the call                                           */
+  int kernel_launches; /* CUDA kernels this call launched                                   */
+} hphi_invit_result;
+
+/* Inverse iteration by conjugate gradients (section 3.4.1): (H - E_n + delta) y_{k+1} = y_k,
+ * y_0 = x, each solve starting from its right-hand side, y_{k+1} normalised into x.  x is a
+ * device fp64 [dim] vector (complex128 for complex models) owned by the caller: in, the start
+ * vector (the Lanczos eigenvector); out, the unit result.  Besides x the call keeps four more
+ * vectors of the model's dimension in the model's workspace (released by
+ * hphi_release_workspace).  Every product and reduction is fp64; a solve's scalars stay on
+ * the device, and the host reads its convergence flag every 16 iterations.  Synchronises
+ * the stream before returning. */
+int hphi_inverse_iteration(hphi_model* m, const hphi_invit_params* p, void* x, hphi_invit_result* r, void* stream);
+
 /* ---------------------------------------------------------------- mTPQ (section 3.5) */
 
 typedef struct {
@@ -300,6 +339,8 @@ typedef struct {
   int prec;            /* HPHI_FP64 or HPHI_FP32 (fp32 storage, fp64 norms and energies)   */
   int profile;         /* 1: launch the steps one by one (no graph) and time every fused H v
                           launch group with CUDA events (hv_ms below)                      */
+  int obs_every;       /* diagonal observables of psi_k for k % obs_every == 0 (0: none); one
+                          extra read of the state per measured record                     */
 } hphi_tpq_params;
 
 typedef struct {
@@ -312,6 +353,13 @@ typedef struct {
   int hv_launches;     /* number of fused H v launch groups timed in hv_ms                  */
   double* beta;        /* host [steps][n_starts] or NULL: inverse temperature of record k,
                           beta_k = (2k / N_s) / (l - u_k) (section 3.5)                     */
+  double* spec_heat;   /* host [steps][n_starts] or NULL: specific heat per site,
+                          beta_k^2 (<H^2>_k - <H>_k^2) / N_s = beta_k^2 N_s (h2 - u^2)      */
+  double* doublon;     /* host [steps][n_starts] or NULL: <psi_k| sum_i n_i,up n_i,dn |psi_k>
+                          / N_s (0 for spin models); NaN for records not measured          */
+  double* sz;          /* host [steps][n_starts] or NULL: <S^z_total> / N_s, NaN if not measured */
+  double* sz2;         /* host [steps][n_starts] or NULL: <(S^z_total)^2> / N_s, NaN if not
+                          measured (times beta: the uniform susceptibility per site)      */
 } hphi_tpq_result;
 
 /* Microcanonical TPQ (section 3.5): psi_{k+1} = (l - H/N_s) psi_k / |(l - H/N_s) psi_k| for
@@ -320,7 +368,9 @@ typedef struct {
  * <H^2>_k follows from them, so l must lie above the spectrum per site (the method's
  * condition), which keeps that difference free of cancellation.  Record k describes psi_k, the state
  * the (k+1)-th multiplication acts on, for k = 0 .. steps-1; the inverse temperature is
- * beta_k = (2k / N_s) / (l - u_k). */
+ * beta_k = (2k / N_s) / (l - u_k).  With obs_every > 0 the diagonal observables of section 3.5's
+ * estimate <A>_beta_k = <psi_k|A|psi_k> / N_s (doubly occupied sites, S^z_total, its square) are
+ * reduced in fp64 from the stored state by one extra kernel per measured record. */
 int hphi_tpq_run(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* r, void* stream);
 
 #ifdef __cplusplus

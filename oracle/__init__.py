@@ -266,3 +266,92 @@ def tpq(spec, psi0, K: int, l: float, Ns: float | None = None, want_state: bool 
     out = np.zeros(d, dtype=np.complex128) if want_state else None
     _check(lib().or_tpq(om.ref, _ptr(pc), K, l, Ns, _ptr(u), _ptr(h2), _ptr(nrm), _ptr(out)), "tpq")
     return (u, h2, nrm, out) if want_state else (u, h2, nrm)
+
+
+def _popcount(a: np.ndarray) -> np.ndarray:
+    a = np.asarray(a, dtype=np.uint64)
+    out = np.zeros(a.shape, dtype=np.int64)
+    for b in range(64):
+        out += ((a >> np.uint64(b)) & np.uint64(1)).astype(np.int64)
+    return out
+
+
+def basis_configurations(spec):
+    """Configuration of every basis index (section 3.1's ordering): spin -> s [dim];
+    Hubbard -> (up [dim], dn [dim]) with index = dn_index * dim_up + up_index."""
+    n = spec.n_sites
+    if spec.kind == 0:
+        if spec.basis == 0:
+            return np.arange(1 << n, dtype=np.uint64)
+        return sector_list(n, spec.n_a)
+    if spec.basis == 0:
+        lu = ld = np.arange(1 << n, dtype=np.uint64)
+    else:
+        lu, ld = sector_list(n, spec.n_a), sector_list(n, spec.n_b)
+    up = np.tile(lu, len(ld))
+    dn = np.repeat(ld, len(lu))
+    return up, dn
+
+
+def diag_observables(spec, psi):
+    """Section 3.5's local estimate <psi|A|psi> / (<psi|psi> N_s) for the diagonal operators
+    A = sum_i n_i,up n_i,dn (doubly occupied sites; 0 for spins), S^z_total and (S^z_total)^2.
+    psi [dim] or [dim][nvec]; returns three arrays [nvec] (or scalars)."""
+    p = np.asarray(psi)
+    w = np.abs(p) ** 2
+    if spec.kind == 0:
+        s = basis_configurations(spec)
+        dbl = np.zeros(len(s))
+        m2 = 2 * _popcount(s) - spec.n_sites
+    else:
+        up, dn = basis_configurations(spec)
+        dbl = _popcount(up & dn).astype(np.float64)
+        m2 = _popcount(up) - _popcount(dn)
+    m2 = m2.astype(np.float64)
+    ww = w.sum(axis=0)
+    ns = spec.n_sites
+    if w.ndim == 2:
+        dbl, m2 = dbl[:, None], m2[:, None]
+    return ((w * dbl).sum(axis=0) / ww / ns, (w * m2).sum(axis=0) / 2 / ww / ns,
+            (w * m2 * m2).sum(axis=0) / 4 / ww / ns)
+
+
+def tpq_states(spec, psi0, K: int, l: float, Ns: float | None = None):
+    """The normalised mTPQ states psi_0 .. psi_{K-1} of section 3.5, one multiplication by
+    (l - H / N_s) and one normalisation per step; returns [K][dim]."""
+    d = dim(spec)
+    Ns = float(spec.n_sites if Ns is None else Ns)
+    x = _as_c128(psi0, d)[:, 0].copy()
+    x /= np.linalg.norm(x)
+    out = np.zeros((K, d), dtype=np.complex128)
+    for k in range(K):
+        out[k] = x
+        y = l * x - apply_H(spec, x) / Ns
+        x = y / np.linalg.norm(y)
+    return out
+
+
+def inverse_iteration(spec, x0, E: float, delta: float, outer: int):
+    """Section 3.4.1: y_{k+1} = (H - E + delta)^{-1} y_k, normalised, from y_0 = x0 (each
+    solve by LAPACK on the dense matrix of the oracle's H)."""
+    H = dense_H(spec)
+    A = H - (E - delta) * np.eye(H.shape[0])
+    y = np.asarray(x0, dtype=np.complex128).copy()
+    y /= np.linalg.norm(y)
+    for _ in range(outer):
+        y = np.linalg.solve(A, y)
+        y /= np.linalg.norm(y)
+    return y
+
+
+def lanczos_convergence_step(alpha, beta, eps: float, first: int = 5, every: int = 2):
+    """Appendix C's stopping rule on a recurrence's alpha / beta: the first n (n = first,
+    first + every, ...) at which T_n's first excited eigenvalue agrees with its value at the
+    previous test to eps relative; None if no n within the data does."""
+    prev = None
+    for n in range(first, len(alpha) + 1, every):
+        e1 = ritz_values(alpha[:n], beta[:n])[1]
+        if prev is not None and abs(e1 - prev) <= eps * abs(e1):
+            return n
+        prev = e1
+    return None

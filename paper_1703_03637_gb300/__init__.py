@@ -30,7 +30,7 @@ EXPORTS = [
     "hphi_build_sector", "hphi_dim", "hphi_is_complex", "hphi_basis_states", "hphi_basis_ranks", "hphi_apply_H",
     "hphi_random_vector", "hphi_philox4x32_10", "hphi_lanczos_run", "hphi_tpq_run", "hphi_apply_H_noalloc",
     "hphi_lanczos_run_sectors", "hphi_autotune", "hphi_set_window_bits", "hphi_set_sector_split",
-    "hphi_release_workspace",
+    "hphi_release_workspace", "hphi_inverse_iteration",
 ]
 
 
@@ -43,14 +43,25 @@ class LibraryError(RuntimeError):
 class LanczosParams(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("v0", ctypes.c_void_p),
                 ("n_eig", ctypes.c_int), ("refine", ctypes.c_int), ("breakdown", ctypes.c_double),
-                ("profile", ctypes.c_int), ("keep_basis", ctypes.c_int), ("v0_on_host", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("keep_basis", ctypes.c_int), ("v0_on_host", ctypes.c_int),
+                ("eps", ctypes.c_double), ("ritz_out", ctypes.c_void_p)]
 
 
 class LanczosResult(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_int), ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p),
                 ("eig", ctypes.c_double * 8), ("e_refined", ctypes.c_double), ("residual", ctypes.c_double),
                 ("variance", ctypes.c_double), ("device_ms", ctypes.c_float), ("hv_ms", ctypes.c_float),
-                ("hv_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+                ("hv_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int), ("converged", ctypes.c_int)]
+
+
+class InvitParams(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("shift", ctypes.c_double), ("outer", ctypes.c_int),
+                ("max_cg", ctypes.c_int), ("cg_tol", ctypes.c_double)]
+
+
+class InvitResult(ctypes.Structure):
+    _fields_ = [("e", ctypes.c_double), ("residual", ctypes.c_double), ("variance", ctypes.c_double),
+                ("cg_steps", ctypes.c_int), ("device_ms", ctypes.c_float), ("kernel_launches", ctypes.c_int)]
 
 
 class TuneResult(ctypes.Structure):
@@ -62,13 +73,14 @@ class TuneResult(ctypes.Structure):
 class TpqParams(ctypes.Structure):
     _fields_ = [("n_starts", ctypes.c_int), ("steps", ctypes.c_int), ("l", ctypes.c_double), ("n_s", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("psi0", ctypes.c_void_p), ("prec", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("obs_every", ctypes.c_int)]
 
 
 class TpqResult(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("h2", ctypes.c_void_p), ("norm", ctypes.c_void_p), ("device_ms", ctypes.c_float),
                 ("kernel_launches", ctypes.c_int), ("hv_ms", ctypes.c_float), ("hv_launches", ctypes.c_int),
-                ("beta", ctypes.c_void_p)]
+                ("beta", ctypes.c_void_p), ("spec_heat", ctypes.c_void_p), ("doublon", ctypes.c_void_p),
+                ("sz", ctypes.c_void_p), ("sz2", ctypes.c_void_p)]
 
 
 _lib = None
@@ -118,6 +130,7 @@ def load(build_if_missing: bool = True):
         L.hphi_set_window_bits.argtypes = [P, I]
         L.hphi_set_sector_split.argtypes = [P, I, I, I, P]
         L.hphi_release_workspace.argtypes = [P]
+        L.hphi_inverse_iteration.argtypes = [P, ctypes.POINTER(InvitParams), P, ctypes.POINTER(InvitResult), P]
         L.hphi_lanczos_run_sectors.argtypes = [P, P, I, ctypes.POINTER(LanczosParams), ctypes.POINTER(LanczosResult), P]
         _lib = L
         return L
@@ -311,8 +324,11 @@ class Model:
         return out
 
     def lanczos(self, steps: int, prec=FP64, seed: int = 123432, v0=None, n_eig: int = 1, refine: bool = False,
-                breakdown: float = 0.0, profile: bool = False, keep_basis: int = 0, v0_on_host: bool = False):
-        """Section 3.4 Lanczos; returns dict(alpha, beta, steps, eig, e_refined, residual, variance, ms).
+                breakdown: float = 0.0, profile: bool = False, keep_basis: int = 0, v0_on_host: bool = False,
+                eps: float = 0.0, ritz_out=None):
+        """Section 3.4 Lanczos; returns dict(alpha, beta, steps, eig, e_refined, residual, variance, ms,
+        converged).  eps > 0: appendix C's convergence test, steps is then the limit.  ritz_out: a CUDA
+        fp64 (complex128) tensor of length dim that receives the refined Ritz vector (refine=True).
         v0: start vector (a CUDA tensor, or any tensor moved to the device here); with v0_on_host
         it must be a host tensor, which the library copies in itself (hphi_lanczos_params.v0_on_host)."""
         torch = _torch()
@@ -331,8 +347,13 @@ class Model:
             vptr = None
         a = np.zeros(steps)
         b = np.zeros(steps)
+        if ritz_out is not None:
+            want = torch.complex128 if self.is_complex else torch.float64
+            if not (ritz_out.is_cuda and ritz_out.dtype == want and ritz_out.is_contiguous()
+                    and ritz_out.numel() == self.dim):
+                raise LibraryError(-1, f"ritz_out must be a contiguous CUDA {want} tensor of length dim")
         p = LanczosParams(steps, prec, seed, vptr, n_eig, int(refine), breakdown, int(profile), int(keep_basis),
-                          int(on_host))
+                          int(on_host), float(eps), _dptr(ritz_out) if ritz_out is not None else None)
         r = LanczosResult()
         r.alpha = a.ctypes.data
         r.beta = b.ctypes.data
@@ -340,10 +361,10 @@ class Model:
         n = r.steps_done
         return dict(alpha=a[:n], beta=b[:n], steps=n, eig=np.array(r.eig[:n_eig]), e_refined=r.e_refined,
                     residual=r.residual, variance=r.variance, ms=r.device_ms, hv_ms=r.hv_ms,
-                    hv_launches=r.hv_launches, launches=r.kernel_launches)
+                    hv_launches=r.hv_launches, launches=r.kernel_launches, converged=bool(r.converged))
 
     def lanczos_sectors(self, n_up_list, steps: int, prec=FP64, seed: int = 123432, n_eig: int = 1,
-                        refine: bool = False, breakdown: float = 0.0, keep_basis: int = 0):
+                        refine: bool = False, breakdown: float = 0.0, keep_basis: int = 0, eps: float = 0.0):
         """Lanczos in several S^z sectors captured as one CUDA graph; one result dict per sector."""
         _torch()
         nu = np.ascontiguousarray(n_up_list, dtype=np.int32)
@@ -354,32 +375,46 @@ class Model:
         for i in range(ns):
             res[i].alpha = al[i].ctypes.data
             res[i].beta = be[i].ctypes.data
-        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0, int(keep_basis), 0)
+        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0, int(keep_basis), 0, float(eps))
         self._check(self._L.hphi_lanczos_run_sectors(self._h, nu.ctypes.data, ns, ctypes.byref(p), res, _stream()))
         out = []
         for i in range(ns):
             n = res[i].steps_done
             out.append(dict(n_up=int(nu[i]), alpha=al[i][:n], beta=be[i][:n], steps=n, eig=np.array(res[i].eig[:n_eig]),
                             e_refined=res[i].e_refined, residual=res[i].residual, variance=res[i].variance,
-                            ms=res[i].device_ms, launches=res[i].kernel_launches))
+                            ms=res[i].device_ms, launches=res[i].kernel_launches, converged=bool(res[i].converged)))
         return out
 
+    def inverse_iteration(self, x, energy: float, shift: float = 0.0, outer: int = 2, max_cg: int = 1000,
+                          cg_tol: float = 0.0):
+        """Section 3.4.1 inverse iteration by CG on the CUDA fp64 (complex128) tensor x, in place; returns
+        dict(e, residual, variance, cg_steps, ms, launches)."""
+        torch = _torch()
+        want = torch.complex128 if self.is_complex else torch.float64
+        if not (x.is_cuda and x.dtype == want and x.is_contiguous() and x.numel() == self.dim):
+            raise LibraryError(-1, f"x must be a contiguous CUDA {want} tensor of length dim")
+        p = InvitParams(float(energy), float(shift), int(outer), int(max_cg), float(cg_tol))
+        r = InvitResult()
+        self._check(self._L.hphi_inverse_iteration(self._h, ctypes.byref(p), _dptr(x), ctypes.byref(r), _stream()))
+        return dict(e=r.e, residual=r.residual, variance=r.variance, cg_steps=r.cg_steps, ms=r.device_ms,
+                    launches=r.kernel_launches)
+
     def tpq(self, n_starts: int, steps: int, l: float = 1.0, n_s: float = 0.0, prec=FP64, seed: int = 123432,
-            psi0=None, profile: bool = False):
-        """Section 3.5 mTPQ for n_starts interleaved starts; returns dict(u, h2, norm, beta, ms, ...), arrays
-        [steps, n_starts]."""
+            psi0=None, profile: bool = False, obs_every: int = 0):
+        """Section 3.5 mTPQ for n_starts interleaved starts; returns dict(u, h2, norm, beta, spec_heat, doublon,
+        sz, sz2, ms, ...), arrays [steps, n_starts] (observables NaN where not measured)."""
         torch = _torch()
         if psi0 is not None:
             psi0 = psi0.to(device="cuda", dtype=torch.complex128 if self.is_complex else torch.float64).contiguous()
-        u = np.zeros((steps, n_starts))
-        h2 = np.zeros((steps, n_starts))
-        nr = np.zeros((steps, n_starts))
-        bt = np.zeros((steps, n_starts))
-        p = TpqParams(n_starts, steps, l, n_s, seed, _dptr(psi0) if psi0 is not None else None, prec, int(profile))
-        r = TpqResult(u.ctypes.data, h2.ctypes.data, nr.ctypes.data, 0.0, 0, 0.0, 0, bt.ctypes.data)
+        out = {k: np.zeros((steps, n_starts)) for k in ("u", "h2", "norm", "beta", "spec_heat", "doublon", "sz", "sz2")}
+        p = TpqParams(n_starts, steps, l, n_s, seed, _dptr(psi0) if psi0 is not None else None, prec, int(profile),
+                      int(obs_every))
+        r = TpqResult(out["u"].ctypes.data, out["h2"].ctypes.data, out["norm"].ctypes.data, 0.0, 0, 0.0, 0,
+                      out["beta"].ctypes.data, out["spec_heat"].ctypes.data, out["doublon"].ctypes.data,
+                      out["sz"].ctypes.data, out["sz2"].ctypes.data)
         self._check(self._L.hphi_tpq_run(self._h, ctypes.byref(p), ctypes.byref(r), _stream()))
-        return dict(u=u, h2=h2, norm=nr, beta=bt, ms=r.device_ms, launches=r.kernel_launches, hv_ms=r.hv_ms,
-                    hv_launches=r.hv_launches)
+        out.update(ms=r.device_ms, launches=r.kernel_launches, hv_ms=r.hv_ms, hv_launches=r.hv_launches)
+        return out
 
 
 def philox4x32_10(ctr, key):

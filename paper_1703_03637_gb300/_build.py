@@ -16,7 +16,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 INC_DIR = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libhphi_gpu.so")
-SOURCES = ["api.cu", "k_basis.cu", "k_hv.cu", "k_hub.cu", "k_solver.cu", "k_batch.cu", "k_sector.cu"]
+SOURCES = ["api.cu", "k_basis.cu", "k_hv.cu", "k_hub.cu", "k_solver.cu", "k_batch.cu", "k_sector.cu", "k_cg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC_DIR, "-I", SRC_DIR]
 

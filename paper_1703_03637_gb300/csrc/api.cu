@@ -94,6 +94,7 @@ cplx site_el(int a, int b, int* kb) {
 
 struct Workspace {
   DBuf vecA, vecB, x, partials, scal, work, basis;
+  DBuf cgp, cgq;  // inverse iteration: CG direction and A p
 };
 
 }  // namespace
@@ -1047,7 +1048,8 @@ int hphi_release_workspace(hphi_model* m) {
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(m, HPHI_ERR_CUDA, std::string("release_workspace: ") + cudaGetErrorString(e));
   Workspace& ws = m->ws;
-  for (DBuf* b : {&ws.vecA, &ws.vecB, &ws.x, &ws.partials, &ws.scal, &ws.work, &ws.basis}) b->release();
+  for (DBuf* b : {&ws.vecA, &ws.vecB, &ws.x, &ws.partials, &ws.scal, &ws.work, &ws.basis, &ws.cgp, &ws.cgq})
+    b->release();
   return HPHI_OK;
 }
 
@@ -1235,6 +1237,8 @@ struct LzPlan {
   size_t nsc = 0;
   int* flags = nullptr;
   double brk = 1e-13;
+  double eps = 0.0;  // convergence test of appendix C (0: off)
+  void* ritz_out = nullptr;
   const double* v0 = nullptr;
   const double* v0_host = nullptr;  // start vector in host memory (copied in by start())
   uint64_t seed = 0;
@@ -1261,6 +1265,8 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   }
   L.seed = p->seed;
   L.brk = p->breakdown > 0 ? p->breakdown : 1e-13;
+  L.eps = p->eps > 0 ? p->eps : 0.0;
+  L.ritz_out = p->ritz_out;
   const int steps = L.steps, prec = L.prec;
   const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (L.cplx ? 2 : 1);
   L.n_real = m->dim * (L.cplx ? 2 : 1);
@@ -1408,6 +1414,11 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
                                      L.partials, L.vgrid, emax, st)).code)
         return q;
       if ((q = hphi::launch_lz_fin2(L.lz, k, L.brk, L.partials, L.vgrid, with_x, st)).code) return q;
+      // appendix C: after five steps, then every two, unless the run already stopped
+      if (!with_x && L.eps > 0.0 && k + 1 >= 5 && (k + 1 - 5) % 2 == 0 && k + 1 < steps) {
+        ++L.launches;
+        if ((q = hphi::launch_lz_conv(L.lz, L.eps, st)).code) return q;
+      }
       if (!L.store) std::swap(C, P);
     }
     return {};
@@ -1440,7 +1451,10 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
   if ((s = hphi::launch_refine_fin(L.lz, L.partials, L.rgrid, 0, st)).code) return s;
   if ((s = hphi::launch_refine_resid(cplx, ws.x.as<double>(), hx, L.n_real, L.lz, L.partials, L.vgrid, st)).code)
     return s;
-  return hphi::launch_refine_fin(L.lz, L.partials, L.vgrid, 1, st);
+  if ((s = hphi::launch_refine_fin(L.lz, L.partials, L.vgrid, 1, st)).code) return s;
+  if (L.ritz_out)
+    HPHI_CUDA_TRY(cudaMemcpyAsync(L.ritz_out, ws.x.p, 8 * (size_t)L.n_real, cudaMemcpyDeviceToDevice, st));
+  return {};
 }
 
 hphi::Status lz_collect(LzPlan& L, hphi_lanczos_result* r, cudaStream_t st) {
@@ -1449,6 +1463,7 @@ hphi::Status lz_collect(LzPlan& L, hphi_lanczos_result* r, cudaStream_t st) {
   HPHI_CUDA_TRY(cudaStreamSynchronize(st));
   const int* hf = reinterpret_cast<const int*>(host.data() + (reinterpret_cast<double*>(L.flags) - L.base));
   r->steps_done = hf[1];
+  r->converged = host[(L.lz.s - L.base) + 8] > 0.0 ? 1 : 0;
   if (r->alpha) memcpy(r->alpha, host.data() + (L.lz.alpha - L.base), sizeof(double) * L.steps);
   if (r->beta) memcpy(r->beta, host.data() + (L.lz.beta - L.base), sizeof(double) * L.steps);
   for (int k = 0; k < 8; ++k) r->eig[k] = (k < L.n_eig) ? host[(L.lz.tri - L.base) + k] : 0.0;
@@ -1630,7 +1645,8 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   const int vgrid = launch_grid(m->dim * nvec);
   const int pgrid = std::max(grid, vgrid);
   if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * nvec * hphi::kMaxRedQ)).code) return s;
-  const size_t nsc = 2 * (size_t)nvec + 3 * (size_t)K * nvec;
+  const int obs_every = p->obs_every;
+  const size_t nsc = 2 * (size_t)nvec + 6 * (size_t)K * nvec;
   if ((s = ws.scal.ensure(sizeof(double) * nsc)).code) return s;
   hphi::TpqDev tq;
   tq.n2 = ws.scal.as<double>();
@@ -1638,6 +1654,21 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   tq.u = tq.inv + nvec;
   tq.h2 = tq.u + (size_t)K * nvec;
   tq.nrm = tq.h2 + (size_t)K * nvec;
+  tq.doub = tq.nrm + (size_t)K * nvec;
+  tq.sz = tq.doub + (size_t)K * nvec;
+  tq.sz2 = tq.sz + (size_t)K * nvec;
+  hphi::ObsDev od{};
+  od.n_sites = m->n_sites;
+  od.dim = m->dim;
+  if (m->kind == HPHI_SPIN_HALF) {
+    od.kind = m->basis == HPHI_BASIS_FULL ? 0 : 1;
+    od.n_ones = m->a;
+  } else {
+    od.kind = 2;
+    od.dim_up = m->hdev.dim_up;
+    od.list_up = m->hdev.sector ? m->hdev.list_up : nullptr;
+    od.list_dn = m->hdev.sector ? m->hdev.list_dn : nullptr;
+  }
   double* partials = ws.partials.as<double>();
   const double ns = p->n_s > 0 ? p->n_s : (double)m->n_sites;
   const double inv_ns = 1.0 / ns;
@@ -1692,6 +1723,10 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
       if ((q = hv_launch(m, prec, X, nullptr, nvec, hphi::Epi::kTpq, fa, grid, tscratch, cap)).code) return q;
       if (prof) HPHI_CUDA_TRY(cudaEventRecord(ev[2 * (size_t)k + 1], cap));
       if ((q = hphi::launch_tpq_fin(tq, k, nvec, inv_ns, p->l, partials, grid, cap)).code) return q;
+      if (obs_every > 0 && k % obs_every == 0) {  // observables of psi_k, still held in X
+        if ((q = hphi::launch_tpq_obs(prec, cplx, od, X, nvec, partials, vgrid, cap)).code) return q;
+        if ((q = hphi::launch_tpq_obs_fin(tq, k, nvec, inv_ns, partials, vgrid, cap)).code) return q;
+      }
       std::swap(X, Xn);
     }
     return {};
@@ -1714,7 +1749,7 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
   }
   if (s.code) return s;
   HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
-  std::vector<double> host(3 * (size_t)K * nvec);
+  std::vector<double> host((obs_every > 0 ? 6 : 3) * (size_t)K * nvec);
   HPHI_CUDA_TRY(cudaMemcpyAsync(host.data(), tq.u, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, st));
   HPHI_CUDA_TRY(cudaStreamSynchronize(st));
   float ms = 0.f;
@@ -1730,8 +1765,27 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
         r->beta[o] = (2.0 * k / ns) / (p->l - host[o]);  // host[o] = u_k of start c
       }
   }
+  if (r->spec_heat) {  // C / N_s = beta^2 (<H^2> - <H>^2) / N_s = beta^2 N_s (h2_k - u_k^2)
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < nvec; ++c) {
+        const size_t o = (size_t)k * nvec + c;
+        const double b = (2.0 * k / ns) / (p->l - host[o]);
+        r->spec_heat[o] = b * b * ns * (host[kn + o] - host[o] * host[o]);
+      }
+  }
+  int n_obs = 0;
+  for (double* dst : {r->doublon, r->sz, r->sz2}) {
+    const size_t src = (3 + (size_t)n_obs++) * kn;
+    if (!dst) continue;
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < nvec; ++c) {
+        const size_t o = (size_t)k * nvec + c;
+        dst[o] = (obs_every > 0 && k % obs_every == 0) ? host[src + o] : NAN;
+      }
+  }
   r->device_ms = ms;
-  r->kernel_launches = (p->psi0 ? 0 : 1) + 2 + (1 + hv_kernels(m, prec, nvec, hphi::Epi::kTpq)) * K;
+  const int n_meas = obs_every > 0 ? (K + obs_every - 1) / obs_every : 0;
+  r->kernel_launches = (p->psi0 ? 0 : 1) + 2 + (1 + hv_kernels(m, prec, nvec, hphi::Epi::kTpq)) * K + 2 * n_meas;
   r->hv_ms = 0.f;
   r->hv_launches = prof ? K : 0;
   for (int k = 0; prof && k < K; ++k) {
@@ -1739,6 +1793,106 @@ hphi::Status tpq_impl(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* 
     HPHI_CUDA_TRY(cudaEventElapsedTime(&t, ev[2 * (size_t)k], ev[2 * (size_t)k + 1]));
     r->hv_ms += t;
   }
+  return {};
+}
+
+// Inverse iteration of section 3.4.1 by CG, fp64.  x (the caller's vector) is b of the
+// first solve and receives every normalised iterate; y, r, p, q are the four extra vectors.
+hphi::Status invit_impl(hphi_model* m, const hphi_invit_params* p, void* xv, hphi_invit_result* r, cudaStream_t st) {
+  const bool cplx = m->cplx_model;
+  const int64_t n = m->dim * (cplx ? 2 : 1);
+  const size_t vb = sizeof(double) * (size_t)n;
+  Workspace& ws = m->ws;
+  hphi::Status s;
+  for (DBuf* b : {&ws.vecA, &ws.vecB, &ws.cgp, &ws.cgq})
+    if ((s = b->ensure(vb)).code) return s;
+  void* scratch = nullptr;
+  const size_t need = hv_scratch_bytes(m, HPHI_FP64, 1, hphi::Epi::kStore);
+  if (need && m->kind == HPHI_SPIN_HALF) {
+    scratch = optional_scratch(m, need);
+  } else if (need) {
+    if ((s = ws.work.ensure(need)).code) return s;
+    scratch = ws.work.p;
+  }
+  const int grid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kStore);
+  const int vgrid = launch_grid(n);
+  if ((s = ws.partials.ensure(sizeof(double) * (size_t)vgrid * hphi::kMaxRedQ)).code) return s;
+  if ((s = ws.scal.ensure(sizeof(double) * 18)).code) return s;
+  hphi::CgDev cg;
+  cg.s = ws.scal.as<double>();
+  cg.done = reinterpret_cast<int*>(cg.s + 16);
+  cg.steps = cg.done + 1;
+  double* x = static_cast<double*>(xv);
+  double* y = ws.vecA.as<double>();
+  double* rr = ws.vecB.as<double>();
+  double* pp = ws.cgp.as<double>();
+  double* q = ws.cgq.as<double>();
+  double* partials = ws.partials.as<double>();
+  const double delta = p->shift > 0 ? p->shift : 1e-4 * std::max(1.0, std::fabs(p->energy));
+  const double tol = p->cg_tol > 0 ? p->cg_tol : 1e-12;
+  double host_s[18] = {0.0};
+  host_s[4] = delta - p->energy;
+  host_s[5] = tol * tol;
+  Timer tm;
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
+  HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
+  HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
+  HPHI_CUDA_TRY(cudaMemcpyAsync(cg.s, host_s, sizeof(host_s), cudaMemcpyHostToDevice, st));
+  int launches = 0;
+  hphi::FusedArgs plain;  // H v without a flag
+  hphi::FusedArgs flagged;
+  flagged.done = cg.done;  // H p of a solve that has converged is skipped
+  const int hvk = hv_kernels(m, HPHI_FP64, 1, hphi::Epi::kStore);
+  int done_h = 0;
+  for (int outer = 0; outer < p->outer; ++outer) {
+    HPHI_CUDA_TRY(cudaMemsetAsync(cg.done, 0, sizeof(int), st));
+    // start: y = b, r = b - A b, p = r
+    plain.out = q;
+    if ((s = hv_launch(m, HPHI_FP64, x, q, 1, hphi::Epi::kStore, plain, grid, scratch, st)).code) return s;
+    if ((s = hphi::launch_cg_shift(cg, x, q, n, partials, vgrid, st)).code) return s;
+    if ((s = hphi::launch_cg_update(cg, 0, x, y, rr, pp, q, n, partials, vgrid, st)).code) return s;
+    if ((s = hphi::launch_cg_fin(cg, 0, partials, vgrid, st)).code) return s;
+    launches += hvk + 3;
+    for (int it = 0; it < p->max_cg; ++it) {
+      flagged.out = q;
+      if ((s = hv_launch(m, HPHI_FP64, pp, q, 1, hphi::Epi::kStore, flagged, grid, scratch, st)).code) return s;
+      if ((s = hphi::launch_cg_shift(cg, pp, q, n, partials, vgrid, st)).code) return s;
+      if ((s = hphi::launch_cg_fin(cg, 1, partials, vgrid, st)).code) return s;
+      if ((s = hphi::launch_cg_update(cg, 1, nullptr, y, rr, pp, q, n, partials, vgrid, st)).code) return s;
+      if ((s = hphi::launch_cg_fin(cg, 2, partials, vgrid, st)).code) return s;
+      if ((s = hphi::launch_cg_dir(cg, rr, pp, n, vgrid, st)).code) return s;
+      launches += hvk + 5;
+      if (it % 16 == 15) {  // look at the flag now and then; the kernels skip work once it is set
+        HPHI_CUDA_TRY(cudaMemcpyAsync(&done_h, cg.done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HPHI_CUDA_TRY(cudaStreamSynchronize(st));
+        if (done_h) break;
+      }
+    }
+    // x = y / |y|
+    if ((s = hphi::launch_cg_norm(cg, 0, y, x, n, partials, vgrid, st)).code) return s;
+    if ((s = hphi::launch_cg_fin(cg, 3, partials, vgrid, st)).code) return s;
+    if ((s = hphi::launch_cg_norm(cg, 1, y, x, n, partials, vgrid, st)).code) return s;
+    launches += 3;
+  }
+  // Rayleigh quotient, variance and residual of the final unit vector
+  plain.out = q;
+  if ((s = hv_launch(m, HPHI_FP64, x, q, 1, hphi::Epi::kStore, plain, grid, scratch, st)).code) return s;
+  if ((s = hphi::launch_cg_rq(cg, 0, x, q, n, partials, vgrid, st)).code) return s;
+  if ((s = hphi::launch_cg_fin(cg, 4, partials, vgrid, st)).code) return s;
+  if ((s = hphi::launch_cg_rq(cg, 1, x, q, n, partials, vgrid, st)).code) return s;
+  if ((s = hphi::launch_cg_fin(cg, 5, partials, vgrid, st)).code) return s;
+  launches += hvk + 4;
+  HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
+  HPHI_CUDA_TRY(cudaMemcpyAsync(host_s, cg.s, sizeof(host_s), cudaMemcpyDeviceToHost, st));
+  HPHI_CUDA_TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  HPHI_CUDA_TRY(cudaEventElapsedTime(&ms, tm.a, tm.b));
+  r->e = host_s[6];
+  r->residual = host_s[7];
+  r->variance = host_s[8];
+  r->cg_steps = reinterpret_cast<const int*>(host_s + 16)[1];
+  r->device_ms = ms;
+  r->kernel_launches = launches;
   return {};
 }
 
@@ -1775,6 +1929,17 @@ int hphi_lanczos_run_sectors(hphi_model* m, const int* n_up_list, int n_sectors,
   return s.code ? fail(m, s) : HPHI_OK;
 }
 
+int hphi_inverse_iteration(hphi_model* m, const hphi_invit_params* p, void* x, hphi_invit_result* r, void* stream) {
+  int rc = check_built(m);
+  if (rc) return rc;
+  if (!p || !r || !x) return fail(m, HPHI_ERR_INVALID_ARG, "inverse_iteration: params, result and x must be non-NULL");
+  if (p->outer < 1 || p->outer > 64 || p->max_cg < 1 || p->max_cg > 100000 || !isfinite(p->energy) ||
+      !(p->shift >= 0.0) || !(p->cg_tol >= 0.0))
+    return fail(m, HPHI_ERR_INVALID_ARG, "inverse_iteration: outer 1..64, max_cg 1..100000, finite energy, shift and tol >= 0");
+  hphi::Status s = invit_impl(m, p, x, r, (cudaStream_t)stream);
+  return s.code ? fail(m, s) : HPHI_OK;
+}
+
 int hphi_tpq_run(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* r, void* stream) {
   int rc = check_built(m);
   if (rc) return rc;
@@ -1782,8 +1947,8 @@ int hphi_tpq_run(hphi_model* m, const hphi_tpq_params* p, hphi_tpq_result* r, vo
   const int nv = p->n_starts;
   if (nv < 1 || nv > hphi::kMaxNvec || (nv & (nv - 1)) != 0)
     return fail(m, HPHI_ERR_INVALID_ARG, "tpq: n_starts must be a power of two in 1..256");
-  if (p->steps < 1 || (p->prec != HPHI_FP64 && p->prec != HPHI_FP32) || !isfinite(p->l))
-    return fail(m, HPHI_ERR_INVALID_ARG, "tpq: bad steps, precision or l");
+  if (p->steps < 1 || (p->prec != HPHI_FP64 && p->prec != HPHI_FP32) || !isfinite(p->l) || p->obs_every < 0)
+    return fail(m, HPHI_ERR_INVALID_ARG, "tpq: bad steps, precision, l or obs_every");
   hphi::Status s = tpq_impl(m, p, r, (cudaStream_t)stream);
   return s.code ? fail(m, s) : HPHI_OK;
 }

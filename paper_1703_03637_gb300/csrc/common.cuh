@@ -365,6 +365,9 @@ Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* 
 // coefficient, keeps the first pass's step count)
 Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, bool replay,
                       cudaStream_t st);
+// appendix C's test after a step: stop when T_n's first excited eigenvalue agrees with the
+// previous test's to eps (relative)
+Status launch_lz_conv(const LzDev& lz, double eps, cudaStream_t st);
 // tail_tol: Ritz-coefficient weight below which the replayed second pass may stop
 Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, double tail_tol, cudaStream_t st);
 Status launch_refine_fin(const LzDev& lz, const double* partials, int grid, int which, cudaStream_t st);
@@ -380,7 +383,42 @@ struct TpqDev {
   double* u;             // [K][nvec]
   double* h2;            // [K][nvec]
   double* nrm;           // [K][nvec]
+  double* doub;          // [K][nvec] doubly occupied sites per site (observables on)
+  double* sz;            // [K][nvec] S^z_total per site
+  double* sz2;           // [K][nvec] (S^z_total)^2 per site
 };
+
+// device scalars of an inverse-iteration (CG) solve: s[0] |r|^2, s[1] alpha, s[2] beta,
+// s[3] |b|^2, s[4] delta - E, s[5] tol^2, s[6] e, s[7] residual, s[8] variance, s[9] 1/|y|
+struct CgDev {
+  double* s;             // [16]
+  int* done;             // [1] the current solve has converged
+  int* steps;            // [1] CG iterations so far
+};
+Status launch_cg_shift(const CgDev& cg, const double* p, double* q, int64_t n, double* partials, int grid,
+                       cudaStream_t st);
+Status launch_cg_update(const CgDev& cg, int mode, const double* b, double* y, double* r, double* p, const double* q,
+                        int64_t n, double* partials, int grid, cudaStream_t st);
+Status launch_cg_dir(const CgDev& cg, const double* r, double* p, int64_t n, int grid, cudaStream_t st);
+Status launch_cg_norm(const CgDev& cg, int mode, const double* y, double* x, int64_t n, double* partials, int grid,
+                      cudaStream_t st);
+Status launch_cg_rq(const CgDev& cg, int mode, const double* x, const double* hx, int64_t n, double* partials,
+                    int grid, cudaStream_t st);
+Status launch_cg_fin(const CgDev& cg, int mode, const double* partials, int grid, cudaStream_t st);
+
+// what the diagonal-observable kernel needs to know of a row's configuration
+struct ObsDev {
+  int kind;                  // 0 spin (all 2^N), 1 spin (fixed popcount), 2 Hubbard
+  int n_sites, n_ones;
+  int64_t dim;
+  int64_t dim_up;            // Hubbard: row = d * dim_up + u
+  const uint32_t* list_up;   // Hubbard sector species lists (null: all 2^N)
+  const uint32_t* list_dn;
+};
+Status launch_tpq_obs(int prec, bool cplx, const ObsDev& od, const void* X, int nvec, double* partials, int grid,
+                      cudaStream_t st);
+Status launch_tpq_obs_fin(const TpqDev& tq, int k, int nvec, double inv_ns, const double* partials, int grid,
+                          cudaStream_t st);
 Status launch_tpq_init(int prec, bool cplx, const void* psi0_f64, void* X, int64_t n_rows, int nvec,
                        double* partials, int grid, cudaStream_t st);
 Status launch_tpq_init_fin(const TpqDev& tq, int nvec, const double* partials, int grid, cudaStream_t st);

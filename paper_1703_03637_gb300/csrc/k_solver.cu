@@ -165,15 +165,11 @@ __device__ int sturm_count(const double* __restrict__ a, const double* __restric
   return cnt;
 }
 
-// One warp per wanted eigenvalue: 33-section of the Gershgorin interval until the bracket is
-// a few ulps wide.  Then (warp 0, lane 0, if asked) inverse iteration for the lowest
-// eigenvector of T with partial-pivoting tridiagonal LU.
-__global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double tail_tol, double* __restrict__ work) {
-  const int n = *lz.steps_done;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double* a = lz.alpha;
-  const double* b = lz.beta;
-  if (n <= 0) return;
+// Gershgorin interval of T_n (widened by a few ulps) and the pivot floor of the Sturm count
+struct TriBounds {
+  double lo, hi, scale, pivmin;
+};
+__device__ TriBounds tri_bounds(const double* a, const double* b, int n) {
   double lo = a[0], hi = a[0], bmax = 0.0;
   for (int i = 0; i < n; ++i) {
     const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
@@ -181,32 +177,73 @@ __global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double tail_tol, do
     hi = fmax(hi, a[i] + r);
     if (i + 1 < n) bmax = fmax(bmax, fabs(b[i]));
   }
-  const double scale = fmax(fabs(lo), fabs(hi));
-  const double pivmin = fmax(1e-300, 2.2250738585072014e-308 * fmax(1.0, bmax * bmax));
-  lo -= 2.2e-16 * scale + 1e-300;
-  hi += 2.2e-16 * scale + 1e-300;
+  TriBounds t;
+  t.scale = fmax(fabs(lo), fabs(hi));
+  t.pivmin = fmax(1e-300, 2.2250738585072014e-308 * fmax(1.0, bmax * bmax));
+  t.lo = lo - (2.2e-16 * t.scale + 1e-300);
+  t.hi = hi + (2.2e-16 * t.scale + 1e-300);
+  return t;
+}
+
+// eigenvalue j (ascending, j < n) of T_n by one warp: 33-section of the bracket until it is a
+// few ulps wide; every lane returns it
+__device__ double tri_eigenvalue(const double* a, const double* b, int n, int j, const TriBounds& t, int lane) {
+  double x0 = t.lo, x1 = t.hi;
+  for (int it = 0; it < 64; ++it) {
+    if (x1 - x0 <= 4.0 * 2.2204460492503131e-16 * fmax(fabs(x0), fabs(x1)) + 1e-300) break;
+    const double x = x0 + (x1 - x0) * (double)(lane + 1) / 33.0;
+    const int cnt = sturm_count(a, b, n, x, t.pivmin);
+    // points with cnt <= j lie left of eigenvalue j
+    const unsigned left = __ballot_sync(0xffffffffu, cnt <= j);
+    const int nl = __popc(left);  // points are increasing in lane order
+    double nx0 = x0, nx1 = x1;
+    const double xl = __shfl_sync(0xffffffffu, x, nl > 0 ? nl - 1 : 0);
+    const double xr = __shfl_sync(0xffffffffu, x, nl < 32 ? nl : 31);
+    if (nl > 0) nx0 = xl;
+    if (nl < 32) nx1 = xr;
+    x0 = nx0;
+    x1 = nx1;
+  }
+  return 0.5 * (x0 + x1);
+}
+
+// Convergence test of appendix C, one warp, after the fused step that made T_n: the first
+// excited eigenvalue of T_n against its value at the previous test; when they agree to eps
+// (relative) the run is done (the remaining steps' kernels return at once).  s[6] previous
+// value, s[7] tests so far, s[8] 1 when the test stopped the run.
+__global__ void k_lz_conv(LzDev lz, double eps) {
+  if (*lz.done) return;
+  const int n = *lz.steps_done;
+  const int lane = threadIdx.x & 31;
+  if (n < 2) return;
+  const TriBounds t = tri_bounds(lz.alpha, lz.beta, n);
+  const double e1 = tri_eigenvalue(lz.alpha, lz.beta, n, 1, t, lane);
+  if (lane != 0) return;
+  if (lz.s[7] > 0.0 && fabs(e1 - lz.s[6]) <= eps * fabs(e1)) {
+    *lz.done = 1;
+    lz.s[8] = 1.0;
+  }
+  lz.s[6] = e1;
+  lz.s[7] += 1.0;
+}
+
+// One warp per wanted eigenvalue (tri_eigenvalue).  Then (warp 0, lane 0, if asked) inverse
+// iteration for the lowest eigenvector of T with partial-pivoting tridiagonal LU.
+__global__ void k_tridiag(LzDev lz, int n_eig, int want_vec, double tail_tol, double* __restrict__ work) {
+  const int n = *lz.steps_done;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* a = lz.alpha;
+  const double* b = lz.beta;
+  if (n <= 0) return;
+  const TriBounds tb = tri_bounds(a, b, n);
+  const double scale = tb.scale;
   if (warp < n_eig) {
     const int j = warp;
     if (j >= n) {
       if (lane == 0) lz.tri[j] = nan("");
     } else {
-      double x0 = lo, x1 = hi;
-      for (int it = 0; it < 64; ++it) {
-        if (x1 - x0 <= 4.0 * 2.2204460492503131e-16 * fmax(fabs(x0), fabs(x1)) + 1e-300) break;
-        const double x = x0 + (x1 - x0) * (double)(lane + 1) / 33.0;
-        const int cnt = sturm_count(a, b, n, x, pivmin);
-        // points with cnt <= j lie left of eigenvalue j
-        const unsigned left = __ballot_sync(0xffffffffu, cnt <= j);
-        const int nl = __popc(left);  // points are increasing in lane order
-        double nx0 = x0, nx1 = x1;
-        const double xl = __shfl_sync(0xffffffffu, x, nl > 0 ? nl - 1 : 0);
-        const double xr = __shfl_sync(0xffffffffu, x, nl < 32 ? nl : 31);
-        if (nl > 0) nx0 = xl;
-        if (nl < 32) nx1 = xr;
-        x0 = nx0;
-        x1 = nx1;
-      }
-      if (lane == 0) lz.tri[j] = 0.5 * (x0 + x1);
+      const double e = tri_eigenvalue(a, b, n, j, tb, lane);
+      if (lane == 0) lz.tri[j] = e;
     }
   }
   if (!want_vec) return;
@@ -400,6 +437,81 @@ __global__ void __launch_bounds__(kThreads) k_tpq_fin(TpqDev tq, int mode, int k
   }
 }
 
+// Diagonal observables of the TPQ state (section 3.5: a local quantity at beta_k is its
+// expectation in psi_k per site).  Per column: S0 = sum |x|^2, S1 = sum |x|^2 D(s),
+// S2 = sum |x|^2 M(s), S3 = sum |x|^2 M(s)^2 with D the number of doubly occupied sites and
+// M = 2 S^z_total (an integer) of configuration s.  nvec divides kThreads.
+template <class R, bool CPLX>
+__global__ void __launch_bounds__(kThreads) k_tpq_obs(const ObsDev od, const R* __restrict__ X, int lg_nvec,
+                                                       double* __restrict__ partials) {
+  __shared__ double sm[kThreads];
+  const int nvec = 1 << lg_nvec;
+  const int64_t n_elem = od.dim << lg_nvec;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int c = threadIdx.x & (nvec - 1);
+  for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * kThreads) {
+    const int64_t row = e >> lg_nvec;
+    double w;
+    if constexpr (CPLX) {
+      const double xr = (double)X[2 * e], xi = (double)X[2 * e + 1];
+      w = fma(xr, xr, xi * xi);
+    } else {
+      const double x = (double)X[e];
+      w = x * x;
+    }
+    int dbl = 0, m2 = 0;
+    switch (od.kind) {
+      case 0:  // spin, all 2^N configurations: s = row
+        m2 = 2 * __popcll((unsigned long long)row) - od.n_sites;
+        break;
+      case 1:  // spin, fixed popcount
+        m2 = 2 * od.n_ones - od.n_sites;
+        break;
+      default: {  // Hubbard: row = d * dim_up + u
+        const int64_t d = row / od.dim_up;
+        const int64_t u = row - d * od.dim_up;
+        const uint32_t up = od.list_up ? __ldg(od.list_up + u) : (uint32_t)u;
+        const uint32_t dn = od.list_dn ? __ldg(od.list_dn + d) : (uint32_t)d;
+        dbl = __popc(up & dn);
+        m2 = __popc(up) - __popc(dn);
+      }
+    }
+    a0 += w;
+    a1 = fma(w, (double)dbl, a1);
+    a2 = fma(w, (double)m2, a2);
+    a3 = fma(w, (double)(m2 * m2), a3);
+  }
+  const double acc[4] = {a0, a1, a2, a3};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __syncthreads();
+    sm[threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int off = kThreads / 2; off >= nvec; off >>= 1) {
+      if (threadIdx.x < off) sm[threadIdx.x] += sm[threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x < nvec) partials[((size_t)blockIdx.x * nvec + c) * kMaxRedQ + q] = sm[threadIdx.x];
+  }
+}
+
+// one CTA per column: the per-site observables of record k
+__global__ void __launch_bounds__(kThreads) k_tpq_obs_fin(TpqDev tq, int k, int nvec, double inv_ns,
+                                                           const double* __restrict__ partials, int grid) {
+  __shared__ double sm[kThreads];
+  const int c = blockIdx.x;
+  const double s0 = sum_partials(partials, grid, nvec, c, 0, sm);
+  const double s1 = sum_partials(partials, grid, nvec, c, 1, sm);
+  const double s2 = sum_partials(partials, grid, nvec, c, 2, sm);
+  const double s3 = sum_partials(partials, grid, nvec, c, 3, sm);
+  if (threadIdx.x == 0) {
+    const size_t o = (size_t)k * nvec + c;
+    tq.doub[o] = s1 / s0 * inv_ns;
+    tq.sz[o] = 0.5 * s2 / s0 * inv_ns;
+    tq.sz2[o] = 0.25 * s3 / s0 * inv_ns;
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -458,6 +570,12 @@ Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials
   return {};
 }
 
+Status launch_lz_conv(const LzDev& lz, double eps, cudaStream_t st) {
+  k_lz_conv<<<1, 32, 0, st>>>(lz, eps);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
 Status launch_tridiag(const LzDev& lz, int m_max, int n_eig, bool want_vec, double tail_tol, cudaStream_t st) {
   (void)m_max;
   k_tridiag<<<1, 32 * 8, 0, st>>>(lz, n_eig, want_vec ? 1 : 0, tail_tol, lz.tri + 16);
@@ -512,6 +630,29 @@ Status launch_tpq_init_fin(const TpqDev& tq, int nvec, const double* partials, i
 Status launch_tpq_fin(const TpqDev& tq, int k, int nvec, double inv_ns, double l, const double* partials, int grid,
                       cudaStream_t st) {
   k_tpq_fin<<<nvec, kThreads, 0, st>>>(tq, 1, k, nvec, inv_ns, l, partials, grid);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_tpq_obs(int prec, bool cplx, const ObsDev& od, const void* X, int nvec, double* partials, int grid,
+                      cudaStream_t st) {
+  int lg = 0;
+  while ((1 << lg) < nvec) ++lg;
+  if ((1 << lg) != nvec || nvec > kThreads) return {HPHI_ERR_INVALID_ARG, "tpq observables: nvec a power of two <= 256"};
+  if (prec == HPHI_FP64) {
+    if (cplx) k_tpq_obs<double, true><<<grid, kThreads, 0, st>>>(od, reinterpret_cast<const double*>(X), lg, partials);
+    else k_tpq_obs<double, false><<<grid, kThreads, 0, st>>>(od, reinterpret_cast<const double*>(X), lg, partials);
+  } else {
+    if (cplx) k_tpq_obs<float, true><<<grid, kThreads, 0, st>>>(od, reinterpret_cast<const float*>(X), lg, partials);
+    else k_tpq_obs<float, false><<<grid, kThreads, 0, st>>>(od, reinterpret_cast<const float*>(X), lg, partials);
+  }
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+Status launch_tpq_obs_fin(const TpqDev& tq, int k, int nvec, double inv_ns, const double* partials, int grid,
+                          cudaStream_t st) {
+  k_tpq_obs_fin<<<nvec, kThreads, 0, st>>>(tq, k, nvec, inv_ns, partials, grid);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }

@@ -79,6 +79,7 @@ def _header_struct_fields(name):
 @pytest.mark.parametrize("cname,pyname", [
     ("hphi_lanczos_params", "LanczosParams"), ("hphi_lanczos_result", "LanczosResult"),
     ("hphi_tpq_params", "TpqParams"), ("hphi_tpq_result", "TpqResult"), ("hphi_tune_result", "TuneResult"),
+    ("hphi_invit_params", "InvitParams"), ("hphi_invit_result", "InvitResult"),
 ])
 def test_binding_structs_follow_header(cname, pyname):
     """The ctypes structures list the header's fields in the header's order."""

@@ -838,3 +838,137 @@ def test_lanczos_start_vector_from_host(name, mk):
         host = m.lanczos(30, prec=prec, v0=v0, v0_on_host=True, refine=True, keep_basis=-1)
         assert np.array_equal(dev["alpha"], host["alpha"]) and np.array_equal(dev["beta"], host["beta"])
         assert dev["e_refined"] == host["e_refined"]
+
+
+# ----------------------------------------------------------------------------- TPQ observables
+OBS_CASES = [
+    ("hubbard_tilted8_22", lambda: wl.hubbard_tilted8(U=8.0).with_basis(wl.BASIS_NUMBER, 2, 2), 4, 5.0),
+    ("hubbard_ring4_full_cplx", lambda: wl.random_hubbard_model(4, 6, seed=3), 2, 8.0),
+    ("heisenberg_ring10_full", lambda: wl.heisenberg_ring(10), 1, 1.0),
+    ("kitaev_2x2", lambda: wl.kitaev_honeycomb(2, 2), 4, 1.0),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,mk,nv,l", OBS_CASES, ids=[c[0] for c in OBS_CASES])
+def test_tpq_observables_parity(name, mk, nv, l, prec):
+    """Doubly occupied sites, S^z_total and its square per site of psi_k (section 3.5's local
+    estimate), every third record, against the oracle's states; the specific heat per site
+    beta_k^2 N_s (h2_k - u_k^2) from the records."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    K, every = 12, 3
+    psi0 = wl.gaussian_vector(61, m.dim, nv, complex_=m.is_complex)
+    p = hp.FP64 if prec == "fp64" else hp.FP32
+    res = m.tpq(nv, K, l=l, prec=p, psi0=torch.as_tensor(psi0), obs_every=every)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    for c in range(nv):
+        st = oracle.tpq_states(spec, psi0[:, c], K, l)
+        d, sz, sz2 = oracle.diag_observables(spec, st.T)
+        u, h2, _ = oracle.tpq(spec, psi0[:, c], K, l)
+        for k in range(K):
+            if k % every:
+                assert np.isnan(res["doublon"][k, c]) and np.isnan(res["sz"][k, c])
+                continue
+            scale = max(abs(d[k]), abs(sz2[k]), 1e-3)
+            assert abs(res["doublon"][k, c] - d[k]) <= tol * scale
+            assert abs(res["sz"][k, c] - sz[k]) <= tol * scale
+            assert abs(res["sz2"][k, c] - sz2[k]) <= tol * scale
+        beta = 2.0 * np.arange(K) / spec.n_sites / (l - u)
+        ch = beta ** 2 * spec.n_sites * (h2 - u ** 2)
+        assert np.max(np.abs(res["spec_heat"][:, c] - ch)) <= (1e-9 if prec == "fp64" else 1e-3) * max(1.0, np.max(np.abs(ch)))
+
+
+def test_tpq_observables_off_by_default():
+    m = hp.Model.from_spec(wl.heisenberg_ring(8))
+    res = m.tpq(2, 4, l=1.0)
+    assert np.all(np.isnan(res["doublon"])) and np.all(np.isnan(res["sz2"]))
+    assert np.all(np.isfinite(res["spec_heat"]))
+
+
+def test_tpq_doublon_vs_canonical_8site_hubbard():
+    """Section 5.1's validation: the 8-site periodic cluster (a0 = (2, 2), a1 = (-2, 2)), U/t = 8,
+    half filling with S^z = 0; the doublon density and energy per site of independent TPQ runs
+    against the canonical ensemble of the full spectrum (oracle Hamiltonian, LAPACK), at the
+    TPQ runs' mean inverse temperature."""
+    spec = wl.hubbard_tilted8(U=8.0).with_basis(wl.BASIS_NUMBER, 4, 4)
+    Ns = spec.n_sites
+    m = hp.Model.from_spec(spec)
+    R, K, l = 32, 400, 5.0
+    res = m.tpq(R, K, l=l, seed=2024, obs_every=25)
+    H = oracle.dense_H(spec).real
+    ev, V = np.linalg.eigh(H)
+    dn = oracle.diag_observables(spec, V)[0]  # doublon per site of every eigenstate
+    checked = 0
+    for k in range(25, K, 25):
+        bk = res["beta"][k]
+        b = float(np.mean(bk))
+        w = np.exp(-b * (ev - ev[0]))
+        e_can = float(np.sum(w * ev) / np.sum(w) / Ns)
+        d_can = float(np.sum(w * dn) / np.sum(w))
+        uk, dk = res["u"][k], res["doublon"][k]
+        assert abs(np.mean(uk) - e_can) < 4 * np.std(uk) + 2e-3, (k, b)
+        assert abs(np.mean(dk) - d_can) < 4 * np.std(dk) + 2e-3, (k, b)
+        checked += 1
+    assert checked == 15
+    # low temperature: the doublon density approaches the ground state's
+    assert float(np.mean(res["beta"][K - 1])) > 4.0
+    assert abs(np.mean(res["doublon"][K - 25]) - dn[0]) < 0.02
+
+
+# ----------------------------------------------------------------------------- convergence loop, CG
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_lanczos_convergence_test_appendix_c(prec):
+    """The device stops where appendix C's rule, applied to its own alpha / beta with LAPACK,
+    says it should, and the steps it ran are the steps of a run without the test."""
+    spec = wl.heisenberg_ring(16).with_basis(wl.BASIS_SZ, 8)
+    m = hp.Model.from_spec(spec)
+    p = hp.FP64 if prec == "fp64" else hp.FP32
+    eps = 1e-10 if prec == "fp64" else 1e-6
+    r = m.lanczos(300, prec=p, seed=9, n_eig=2, eps=eps)
+    n = r["steps"]
+    assert r["converged"] and 7 <= n < 300 and (n - 5) % 2 == 0
+    want = oracle.lanczos_convergence_step(r["alpha"], r["beta"], eps)
+    if want != n:  # only a test within rounding of the threshold may flip
+        e_n = oracle.ritz_values(r["alpha"][:n], r["beta"][:n])[1]
+        e_p = oracle.ritz_values(r["alpha"][:n - 2], r["beta"][:n - 2])[1]
+        assert abs(abs(e_n - e_p) / (eps * abs(e_n)) - 1.0) < 1e-3, (n, want)
+    full = m.lanczos(n, prec=p, seed=9, n_eig=2)
+    assert not full["converged"] and full["steps"] == n
+    assert np.array_equal(full["alpha"], r["alpha"]) and np.array_equal(full["beta"], r["beta"])
+    assert np.array_equal(full["eig"], r["eig"])
+    if prec == "fp64":
+        a, _ = oracle.lanczos(spec, oracle.gauss_at(9, np.arange(m.dim, dtype=np.uint64), False), n)
+        assert _rel(r["alpha"][:12], a[:12]) < 1e-11
+    # eps = 0: no test, all steps
+    assert m.lanczos(40, prec=p, seed=9)["steps"] == 40
+
+
+@pytest.mark.parametrize("name,mk", [
+    ("heisenberg_ring16_sz8", lambda: wl.heisenberg_ring(16).with_basis(wl.BASIS_SZ, 8)),
+    ("hubbard_tilted8_44", lambda: wl.hubbard_tilted8(U=8.0).with_basis(wl.BASIS_NUMBER, 4, 4)),
+    ("kitaev_2x2", lambda: wl.kitaev_honeycomb(2, 2)),
+])
+def test_inverse_iteration_cg(name, mk):
+    """Section 3.4.1: from a rough Lanczos eigenvector (12 steps) CG inverse iteration reaches
+    the oracle's shifted solves and a residual near fp64 rounding."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    x = torch.zeros(m.dim, dtype=torch.complex128 if m.is_complex else torch.float64, device="cuda")
+    r = m.lanczos(30, seed=5, refine=True, ritz_out=x)
+    x0 = x.cpu().numpy().copy()
+    assert abs(np.linalg.norm(x0) - 1.0) < 1e-6 and r["residual"] > 1e-6
+    # the Rayleigh quotient lies within the residual of an eigenvalue: a shift of twice the
+    # residual keeps H - E + delta positive definite
+    E = float(r["e_refined"])
+    delta = 2.0 * float(r["residual"])
+    out = m.inverse_iteration(x, E, shift=delta, outer=4, max_cg=20000, cg_tol=1e-13)
+    y = oracle.inverse_iteration(spec, x0, E, delta, outer=4)
+    xg = x.cpu().numpy()
+    assert abs(np.linalg.norm(xg) - 1.0) < 1e-12
+    assert abs(abs(np.vdot(y, xg)) - 1.0) < 1e-10
+    H = oracle.dense_H(spec)
+    e0 = np.linalg.eigvalsh(H)[0]
+    assert abs(out["e"] - e0) < 1e-10 * max(1.0, abs(e0))
+    assert out["residual"] < 1e-7 and out["cg_steps"] > 0
+    assert abs(out["e"] - np.vdot(xg, H @ xg).real) < 1e-11 * max(1.0, abs(e0))

@@ -404,3 +404,138 @@ def test_apply_H_rows_philox_matches_full_product(name, mk, nvec):
         assert np.max(np.abs(got - full[rows])) <= 1e-13 * np.max(np.abs(full))
         if not cplx:
             assert np.max(np.abs(got.imag)) == 0.0
+
+
+# ----------------------------------------------------------------------------- TPQ observables
+def _num_ops(n):
+    c = _indep.fermion_ops(2 * n)
+    return [x.conj().T @ x for x in c]
+
+
+@pytest.mark.parametrize("basis", ["full", "sector"])
+def test_diag_observables_hubbard_match_fermion_operators(basis):
+    """Doubly occupied sites and S^z_total of a Hubbard state against the Jordan-Wigner
+    number operators (mode i + n s, full-basis index up + 2^n dn)."""
+    n = 4
+    spec = wl.hubbard(n, [], U=1.0)
+    num = _num_ops(n)
+    Dop = sum(num[i] @ num[i + n] for i in range(n)).real
+    Sz = sum(num[i] - num[i + n] for i in range(n)).real / 2
+    if basis == "full":
+        idx = np.arange(4 ** n)
+    else:
+        spec = spec.with_basis(wl.BASIS_NUMBER, 3, 1)
+        idx = _indep.hubbard_sector_indices(n, 3, 1)
+    psi = wl.gaussian_vector(5, len(idx), nvec=3, complex_=True)
+    d, sz, sz2 = oracle.diag_observables(spec, psi)
+    full = np.zeros((4 ** n, 3), dtype=complex)
+    full[idx] = psi
+    for c in range(3):
+        x = full[:, c]
+        nn = np.vdot(x, x).real
+        assert abs(d[c] - np.vdot(x, Dop @ x).real / nn / n) < 1e-13
+        assert abs(sz[c] - np.vdot(x, Sz @ x).real / nn / n) < 1e-13
+        assert abs(sz2[c] - np.vdot(x, Sz @ Sz @ x).real / nn / n) < 1e-13
+    if basis == "sector":
+        assert np.allclose(sz, (3 - 1) / 2 / n, atol=1e-15) and np.allclose(sz2, 1.0 / n, atol=1e-15)
+    # the oracle's own U term is the doublon operator
+    HU = oracle.dense_H(spec)
+    x = psi[:, 0]
+    assert abs(d[0] - np.vdot(x, HU @ x).real / np.vdot(x, x).real / n) < 1e-13
+
+
+def test_diag_observables_spin_match_pauli_operators():
+    n = 7
+    spec = wl.heisenberg_ring(n)
+    Sz = sum(_indep.site_op(_indep.SPIN_OPS[2], k, n) for k in range(n)).real
+    psi = wl.gaussian_vector(9, 2 ** n, nvec=2, complex_=True)
+    d, sz, sz2 = oracle.diag_observables(spec, psi)
+    assert np.all(d == 0)
+    for c in range(2):
+        x = psi[:, c]
+        nn = np.vdot(x, x).real
+        assert abs(sz[c] - np.vdot(x, Sz @ x).real / nn / n) < 1e-13
+        assert abs(sz2[c] - np.vdot(x, Sz @ Sz @ x).real / nn / n) < 1e-13
+    sec = spec.with_basis(wl.BASIS_SZ, 2)
+    d, sz, sz2 = oracle.diag_observables(sec, wl.gaussian_vector(1, oracle.dim(sec)))
+    assert abs(sz - (2 - n / 2) / n) < 1e-15 and abs(sz2 - (2 - n / 2) ** 2 / n) < 1e-15
+
+
+def test_tpq_states_are_normalised_matrix_powers():
+    spec = wl.hubbard_tilted8(U=8.0).with_basis(wl.BASIS_NUMBER, 2, 2)
+    D = oracle.dim(spec)
+    psi0 = wl.gaussian_vector(3, D)[:, 0]
+    K, l = 6, 5.0
+    st = oracle.tpq_states(spec, psi0, K, l)
+    A = l * np.eye(D) - oracle.dense_H(spec) / spec.n_sites
+    ref = psi0.astype(complex)
+    for k in range(K):
+        r = ref / np.linalg.norm(ref)
+        assert np.max(np.abs(st[k] - r)) < 1e-13
+        ref = A @ ref
+    u, _, _ = oracle.tpq(spec, psi0, K, l)
+    H = oracle.dense_H(spec)
+    for k in range(K):
+        assert abs(u[k] - np.vdot(st[k], H @ st[k]).real / spec.n_sites) < 1e-12
+
+
+def test_tilted8_cluster_geometry():
+    """Section 5.1's cluster: 8 sites, every site 4 distinct neighbours, 16 bonds; the
+    periodic 4x4 cluster from the same construction has the square lattice's 32 bonds."""
+    n, bonds = wl.tilted_square_bonds((2, 2), (-2, 2))
+    assert n == 8 and len(bonds) == 16
+    deg = np.zeros(n, dtype=int)
+    for i, j in bonds:
+        deg[i] += 1
+        deg[j] += 1
+    assert np.all(deg == 4)
+    n16, b16 = wl.tilted_square_bonds((4, 0), (0, 4))
+    assert n16 == 16 and len(b16) == 32
+    # the 8-site cluster's free-fermion levels: -2t (cos kx + cos ky) over its 8 momenta
+    spec = wl.hubbard_tilted8(U=0.0).with_basis(wl.BASIS_NUMBER, 1, 0)
+    ev = np.sort(np.linalg.eigvalsh(oracle.dense_H(spec)))
+    ks = [(kx, ky) for kx in range(4) for ky in range(4) if (2 * kx + 2 * ky) % 4 == 0 and (-2 * kx + 2 * ky) % 4 == 0]
+    want = np.sort([-2 * (math.cos(math.pi * kx / 2) + math.cos(math.pi * ky / 2)) for kx, ky in ks])
+    assert len(ks) == 8 and np.allclose(ev, want, atol=1e-12)
+
+
+def test_inverse_iteration_converges_to_the_eigenvector():
+    """Section 3.4.1 on a small sector: from a rough vector and an energy just above E_0, a few
+    shifted solves reach numpy's ground state; E = E_0 + delta/2 keeps the operator definite."""
+    spec = wl.heisenberg_ring(12).with_basis(wl.BASIS_SZ, 6)
+    H = oracle.dense_H(spec).real
+    ev, V = np.linalg.eigh(H)
+    assert ev[1] - ev[0] > 0.1  # a non-degenerate ground state
+    x0 = V[:, 0] + 0.3 * wl.gaussian_vector(4, len(ev))[:, 0] / math.sqrt(len(ev))
+    y = oracle.inverse_iteration(spec, x0, ev[0] + 1e-3, 1e-2, outer=4)
+    assert abs(abs(np.vdot(y, V[:, 0])) - 1.0) < 1e-12
+    # the error shrinks by (E0 - E + delta) / (E1 - E + delta) per step
+    y1 = oracle.inverse_iteration(spec, x0, ev[0] + 1e-3, 1e-2, outer=1)
+    err0 = 1 - abs(np.vdot(x0 / np.linalg.norm(x0), V[:, 0])) ** 2
+    err1 = 1 - abs(np.vdot(y1, V[:, 0])) ** 2
+    assert err1 < err0 * ((1e-2 - 1e-3) / (ev[1] - ev[0] - 1e-3 + 1e-2)) ** 2 * 10
+
+
+def test_lanczos_convergence_step_rule():
+    """Appendix C's rule on a recurrence with a known answer: T from a diagonal matrix with
+    well separated low levels converges; the rule returns an odd n >= 7 at which the first
+    excited Ritz value has settled, and None when eps is unreachable."""
+    d = np.concatenate([[-3.0, -2.0], np.linspace(0, 1, 200)])
+    v0 = np.ones(len(d)) / math.sqrt(len(d))
+    # Lanczos on diag(d) in plain numpy (the oracle's recurrence is pinned elsewhere)
+    a, b = [], []
+    q_prev, q, bk = np.zeros_like(v0), v0, 0.0
+    for _ in range(40):
+        w = d * q - bk * q_prev
+        ak = q @ w
+        w -= ak * q
+        w -= (w @ q) * q
+        bk = np.linalg.norm(w)
+        a.append(ak)
+        b.append(bk)
+        q_prev, q = q, w / bk
+    n = oracle.lanczos_convergence_step(a, b, 1e-10)
+    assert n is not None and n >= 7 and (n - 5) % 2 == 0
+    e1n = oracle.ritz_values(a[:n], b[:n])[1]
+    assert abs(e1n - (-2.0)) < 1e-8
+    assert oracle.lanczos_convergence_step(a[:9], b[:9], 1e-300) is None

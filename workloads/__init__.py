@@ -102,6 +102,37 @@ def square_bonds(lx: int, ly: int) -> List[Tuple[int, int]]:
     return out
 
 
+def tilted_square_bonds(a0: Tuple[int, int], a1: Tuple[int, int]) -> Tuple[int, List[Tuple[int, int]]]:
+    """Square-lattice cluster with periodic boundaries along the superlattice vectors a0, a1
+    (section 2.4's a0W/a0L, a1W/a1L); returns (number of sites, nearest-neighbour bonds).
+    Points are identified modulo the superlattice; sites are numbered in the order their
+    classes are first met scanning x, then y, over a box that covers every class."""
+    det = a0[0] * a1[1] - a0[1] * a1[0]
+    n = abs(det)
+
+    def cls(x, y):  # superlattice coordinates times det, reduced modulo det
+        return ((x * a1[1] - y * a1[0]) % n, (a0[0] * y - a0[1] * x) % n)
+
+    site, rep = {}, []
+    r = abs(a0[0]) + abs(a0[1]) + abs(a1[0]) + abs(a1[1])
+    for y in range(-r, r + 1):
+        for x in range(-r, r + 1):
+            c = cls(x, y)
+            if c not in site:
+                site[c] = len(rep)
+                rep.append((x, y))
+    assert len(rep) == n
+    out, seen = [], set()
+    for i, (x, y) in enumerate(rep):
+        for dx, dy in ((1, 0), (0, 1)):
+            j = site[cls(x + dx, y + dy)]
+            key = (min(i, j), max(i, j))
+            if i != j and key not in seen:
+                seen.add(key)
+                out.append(key)
+    return n, out
+
+
 def honeycomb_bonds(cx: int, cy: int) -> List[Tuple[int, int, str]]:
     """Periodic honeycomb of cx x cy two-site cells: A = 2(x + cx*y), B = A + 1.
 
@@ -168,6 +199,12 @@ def hubbard(n_sites: int, bonds: Sequence[Tuple[int, int]], t: complex = 1.0, U:
 
 def hubbard_square(lx: int, ly: int, t: float = 1.0, U: float = 8.0) -> ModelSpec:
     return hubbard(lx * ly, square_bonds(lx, ly), t, U, name=f"hubbard_square_{lx}x{ly}")
+
+
+def hubbard_tilted8(t: float = 1.0, U: float = 8.0) -> ModelSpec:
+    """The 8-site periodic square cluster of section 5.1 (a0 = (2, 2), a1 = (-2, 2))."""
+    n, bonds = tilted_square_bonds((2, 2), (-2, 2))
+    return hubbard(n, bonds, t, U, name="hubbard_tilted8")
 
 
 def hubbard_ring(n: int, t: float = 1.0, U: float = 8.0) -> ModelSpec:
