@@ -42,10 +42,8 @@ FALLBACK_HBM_GBS = 6800.0
 # kernels, with where they come from; absent where no capture of the current kernels exists
 MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): (10_560_000_000, "ncu capture of the 4x4 Hubbard sector, "
                                                                    "quantise + pass D + pass U of one step"),
-                    ("heisenberg_6x5_sz15", "fp64"): (18_407_000_000, "ncu capture of this sector, k_quant + "
-                                                      "k_sec_hi + k_sec_lo at split (15, 2), one step"),
-                    ("heisenberg_6x6_sz0", "fp64"): (1_077_200_000_000, "scaled by rows (118.7 B/row) from the ncu "
-                                                     "capture of the 6x5 S^z=0 sector, same kernels and split")}
+                    ("heisenberg_6x5_sz15", "fp64"): (12_814_000_000, "ncu capture of this sector, k_quant + "
+                                                      "k_sec_hi + k_sec_lo at split (15, 2), one step")}
 # fp64 FMA throughput of this machine's GB300 from a throughput probe (thread-level T op/s); the
 # chip issues fp64 at 1/64 of its fp32 rate
 FP64_PEAK_TOPS = 0.50
