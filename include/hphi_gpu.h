@@ -97,8 +97,8 @@ int hphi_set_basis(hphi_model* m, int basis, int a, int b);
 /* Compiles the term list (section 3.3: diagonal folded into integer bit counts per
  * coefficient class; off-diagonal terms as XOR masks with phase tables), checks that
  * every term conserves the sector (HPHI_ERR_BASIS_MISMATCH otherwise), and builds the
- * two-dimensional rank tables of the restricted space on the device (section 3.1, the
- * split-half "two-dimensional search").  *dim_out (may be NULL) receives the dimension. */
+ * split-half rank tables of the restricted space on the device (section 3.1).  *dim_out
+ * (may be NULL) receives the dimension. */
 int hphi_build_sector(hphi_model* m, int64_t* dim_out, void* stream);
 
 /* Dimension of the built basis, or a negative status. */
@@ -136,9 +136,11 @@ int hphi_apply_H(hphi_model* m, const void* v, void* w, int nvec, int prec, void
  * scratch (16 bytes per basis row + 256 bytes) is a fixed 64 MiB device array inside the
  * library, so the basis may have at most 4,194,288 rows; larger bases return
  * HPHI_ERR_INVALID_ARG with the limit in the message, other models HPHI_ERR_UNSUPPORTED.
- * v and w are caller-owned device buffers [dim] of double and must not overlap.  The first
- * call on each device looks up the array's device address with that device current; make
- * that first call before any stream capture.  Every call on a device shares the one array,
+ * v and w are caller-owned device buffers [dim] of double and must not overlap.  A call on a
+ * stream that is not being captured looks up the array's device address afresh (after a
+ * device reset or a context switch it is the current one); a call on a capturing stream uses
+ * the address of the device's last uncaptured call, so make one uncaptured call on the device
+ * before any stream capture.  Every call on a device shares the one array,
  * so calls whose GPU work overlaps (different streams or threads without ordering between
  * them) race and give wrong results; calls ordered on one stream are safe.  The array is
  * held by every GPU that loads the library until the process exits. */
@@ -211,16 +213,15 @@ int hphi_set_window_bits(hphi_model* m, int bits);
 
 /* ---------------------------------------------------------------- start vectors */
 
-/* Fills v (device, [dim][nvec], precision prec) with standard-normal numbers from the
- * counter-based generator Philox4x32-10 (Salmon et al., SC'11) and the Box-Muller
- * transform: element e = r * nvec + c uses counter (e mod 2^32, e >> 32, 0, 0) and key
- * (seed mod 2^32, seed >> 32); the four output words give two 53-bit uniforms
- * u_a = ((w0 << 21) | (w1 >> 11)) + 0.5) / 2^53 and u_b likewise from w2, w3; the real part
- * is sqrt(-2 ln u_a) cos(2 pi u_b) and the imaginary part (complex models) the sine, in fp64
- * for prec = HPHI_FP64.  For prec = HPHI_FP32 the same two uniforms are rounded to fp32 and
- * the transform runs in fp32 arithmetic (values within a few fp32 ulps of the fp64 numbers).
- * This replaces the paper's dSFMT draws (appendix A.2 / A.4), whose stream depends on the
- * process count. */
+/* Fills v (device, [dim][nvec], precision prec) with uniform random numbers in [-1, 1) from
+ * the counter-based generator Philox4x32-10 (Salmon et al., SC'11): element e = r * nvec + c
+ * uses counter (e mod 2^32, e >> 32, 0, 0) and key (seed mod 2^32, seed >> 32); output words
+ * w0, w1 give the 53-bit integer m_a = ((w0 << 32) | w1) >> 11 and the real part
+ * (m_a - 2^52) 2^-52, words w2, w3 the imaginary part (complex models) likewise.  prec =
+ * HPHI_FP64 holds these values exactly; HPHI_FP32 holds their round-to-nearest fp32 values.
+ * Appendix A.2 / A.4 draw every coefficient of the initial vector from a random number
+ * generator (dSFMT, whose stream depends on the process count); this generator depends on
+ * the seed and the element index only. */
 int hphi_random_vector(hphi_model* m, void* v, int nvec, int prec, uint64_t seed, void* stream);
 
 /* Raw Philox4x32-10 on the device: for k < n, out[4k..4k+3] = Philox(ctr[4k..4k+3],

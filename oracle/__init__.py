@@ -65,8 +65,8 @@ def lib():
             L.or_apply_H.argtypes = [P, P, P, i32]
             L.or_apply_H_slice.argtypes = [P, P, P, i32, u64, u64]
             L.or_philox4x32_10.argtypes = [P, P, P]
-            L.or_gauss_pair.argtypes = [u64, u64, P]
-            L.or_gauss_at.argtypes = [u64, P, i64, i32, P]
+            L.or_uniform_pair.argtypes = [u64, u64, P]
+            L.or_random_at.argtypes = [u64, P, i64, i32, P]
             L.or_apply_H_rows_philox.argtypes = [P, P, i64, u64, i32, i32, i32, P]
             L.or_lanczos.argtypes = [P, P, i32, f64, P, P]
             L.or_lanczos_vector.argtypes = [P, P, i32, P, P, P, P]
@@ -180,7 +180,7 @@ def apply_H_slice(spec, v, r0: int, nrows: int) -> np.ndarray:
 
 
 def apply_H_rows_philox(spec, rows, seed: int, complex_: bool, nvec: int = 1, col: int = 0) -> np.ndarray:
-    """Rows of H v where v [dim][nvec] is the Philox-Gaussian vector of `seed` (column `col`)."""
+    """Rows of H v where v [dim][nvec] is the Philox start vector of `seed` (column `col`)."""
     om = OracleModel(spec)
     rows = np.ascontiguousarray(rows, dtype=np.uint64)
     out = np.zeros(len(rows), dtype=np.complex128)
@@ -203,10 +203,11 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return out
 
 
-def gauss_at(seed: int, idx, complex_: bool) -> np.ndarray:
+def random_at(seed: int, idx, complex_: bool) -> np.ndarray:
+    """Elements idx of the Philox start vector of `seed` (uniform in [-1, 1), appendix A.2 / A.4)."""
     idx = np.ascontiguousarray(idx, dtype=np.uint64)
     out = np.zeros(len(idx), dtype=np.complex128)
-    lib().or_gauss_at(seed, _ptr(idx), len(idx), int(complex_), _ptr(out))
+    lib().or_random_at(seed, _ptr(idx), len(idx), int(complex_), _ptr(out))
     return out if complex_ else out.real.copy()
 
 

@@ -1239,6 +1239,7 @@ struct LzPlan {
   double brk = 1e-13;
   double eps = 0.0;  // convergence test of appendix C (0: off)
   void* ritz_out = nullptr;
+  bool cta = false;  // the whole recurrence in one CTA (small real spin models)
   const double* v0 = nullptr;
   const double* v0_host = nullptr;  // start vector in host memory (copied in by start())
   uint64_t seed = 0;
@@ -1314,6 +1315,9 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
       L.scratch = optional_scratch(m, gen);
     }
   }
+  // small real spin models: both vectors in one CTA's shared memory, one kernel for all steps
+  L.cta = m->kind == HPHI_SPIN_HALF && !L.cplx && prec == HPHI_FP64 && !L.refine && !L.profile && L.eps == 0.0 &&
+          hphi::lz_cta_smem(m->sdev) <= 200 * 1024;
   // grids after the scratch: the split-row kernels run only when it holds what they need
   L.grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
   L.rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);
@@ -1424,7 +1428,14 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
     return {};
   };
   if ((s = start()).code) return s;
-  if ((s = run_pass(false)).code) return s;
+  if (L.cta) {
+    L.launches += 3;
+    if ((s = hphi::launch_lz_init(prec, cplx, v0_dev, c0, p0, L.n_real, L.partials, L.vgrid, st)).code) return s;
+    if ((s = hphi::launch_lz_init_fin(L.lz, L.partials, L.vgrid, st)).code) return s;
+    if ((s = hphi::launch_lz_cta(m->sdev, L.lz, steps, L.brk, static_cast<const double*>(c0), st)).code) return s;
+  } else if ((s = run_pass(false)).code) {
+    return s;
+  }
   ++L.launches;
   // the replayed pass may skip steps whose Ritz coefficients change the unit Ritz vector by
   // less than the storage precision's rounding (fp64: 1e-15, fp32: 1e-8)

@@ -5,7 +5,7 @@
 //     rank(s) = hi_off[hi] + lo_rank[lo],
 // where hi_off[hi] counts the sector states whose high part is smaller than hi and
 // lo_rank[lo] is the rank of lo among the L-bit strings with the same popcount: the
-// two-dimensional search of Lin / TITPACK that the paper uses for its reverse lookup.
+// split-half lookup of Lin / TITPACK that the paper uses for its reverse lookup.
 // Row -> configuration goes the other way: hi is the largest value with hi_off[hi] <= r
 // (binary search; a non-empty block always wins ties) and lo is entry r - hi_off[hi] of
 // the ascending list of L-bit strings with popcount n_ones - popcount(hi).

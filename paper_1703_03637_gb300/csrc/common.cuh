@@ -365,6 +365,10 @@ Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* 
 // coefficient, keeps the first pass's step count)
 Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, bool replay,
                       cudaStream_t st);
+// the whole Lanczos recurrence in one CTA (real spin models whose two vectors fit in shared
+// memory): C0 holds C_0 (after k_lz_init / its finaliser); fills alpha, beta, sig, steps_done
+size_t lz_cta_smem(const SpinDev& md);
+Status launch_lz_cta(const SpinDev& md, const LzDev& lz, int steps, double brk, const double* C0, cudaStream_t st);
 // appendix C's test after a step: stop when T_n's first excited eigenvalue agrees with the
 // previous test's to eps (relative)
 Status launch_lz_conv(const LzDev& lz, double eps, cudaStream_t st);

@@ -738,17 +738,21 @@ int up_grid_r(const HubDev& md, Epi epi) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * occ));
 }
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device
-// (with that device current) and cached.
+// Device address of g_noalloc_scratch on the current device.  Looked up again on every call
+// whose stream is not being captured (the lookup allocates nothing), so a device reset or
+// another current context cannot leave a stale address behind; a capturing stream takes the
+// address cached by the last such lookup on the device (a graph replays that address anyway).
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {};
 
-Status noalloc_scratch(void** out) {
+Status noalloc_scratch(void** out, cudaStream_t st) {
   int dev = 0;
   HPHI_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return {HPHI_ERR_UNSUPPORTED, "allocation-free path: device ordinal above 63"};
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HPHI_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
+  if (cs == cudaStreamCaptureStatusNone || g_noalloc_ptr[dev] == nullptr) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -775,7 +779,7 @@ Status launch_hub_store_noalloc(const HubDev& md0, const void* v, void* w, cudaS
                                       " bytes of scratch, above the fixed " + std::to_string(kNoAllocScratchBytes) +
                                       " (at most " + std::to_string((kNoAllocScratchBytes - 256) / 16) + " rows)"};
   void* scratch = nullptr;
-  Status s = noalloc_scratch(&scratch);
+  Status s = noalloc_scratch(&scratch, st);
   if (s.code) return s;
   FusedArgs fa;  // plain H v: no reductions, no breakdown flag
   return launch_q<Epi::kStore>(md, v, w, scratch, fa, upq_grid(md, Epi::kStore), st);

@@ -578,4 +578,125 @@ Status launch_hv(bool hubbard, const void* md, int prec, bool cplx, const void* 
   return {HPHI_ERR_INVALID_ARG, "unknown epilogue"};
 }
 
+// ------------------------------------------------------------------ one-CTA Lanczos
+// The whole recurrence of section 3.4 in one CTA when both Lanczos vectors fit in shared
+// memory (real spin models up to 12,800 rows): no launch per step, no trip through HBM.
+// Each thread owns rows tid, tid + kCta, ...; a step computes (H C)[r] from the staged C
+// (diagonal from the bit counts, exchange terms gathered from shared memory), P = c1 H C -
+// c2 P and the partial (C, H C) in one sweep, reduces alpha across the CTA, then P -= gamma C
+// and |P|^2, reduces beta, and swaps the roles of C and P.  Scalars follow k_lz_fin's
+// conventions (C unnormalised, sigma = 1 / |C|), so k_tridiag reads the same arrays.
+namespace {
+constexpr int kCta = 1024;
+
+__device__ double cta_sum(double x, double* s_w) {
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // the previous sum has been read
+  if (lane == 0) s_w[wid] = x;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < kCta / 32; ++k) t += s_w[k];  // same order in every thread
+  return t;
+}
+
+__global__ void __launch_bounds__(kCta, 1) k_lz_cta(const SpinDev md, LzDev lz, int steps, double brk,
+                                                     const double* __restrict__ C0, double* __restrict__ Cout) {
+  extern __shared__ __align__(16) double sm_v[];
+  __shared__ double s_w[kCta / 32];
+  __shared__ SpinEntry s_ent[kMaxSpinEntries];
+  __shared__ double s_cls[kMaxClasses];
+  __shared__ LinGroup s_lin[kMaxLin];
+  __shared__ PairEntry s_pair[kMaxPairs];
+  __shared__ double s_pcoef[kMaxPairGroups];
+  const int tid = threadIdx.x;
+  const int64_t n = md.dim;
+  double* C = sm_v;
+  double* P = sm_v + n;
+  for (int64_t r = tid; r < n; r += kCta) {
+    C[r] = C0[r];
+    P[r] = 0.0;
+  }
+  for (int k = tid; k < md.n_entries; k += kCta) s_ent[k] = md.entries[k];
+  for (int k = tid; k < md.n_classes; k += kCta) s_cls[k] = md.cls_coef[k].x;
+  for (int k = tid; k < md.n_lin; k += kCta) s_lin[k] = md.lin[k];
+  for (int k = tid; k < md.n_pairs; k += kCta) s_pair[k] = md.pairs[k];
+  for (int k = tid; k < md.n_pair_groups; k += kCta) s_pcoef[k] = md.pair_coef[k];
+  // k_lz_init / k_lz_fin mode 0 have set sigma_0, c1, c2 and the flags
+  double sg = lz.sig[0];
+  double c1 = lz.s[0], c2 = lz.s[1];
+  int done = *lz.done;
+  int k = 0;
+  for (; k < steps && !done; ++k) {
+    __syncthreads();  // C complete
+    double xh = 0.0;
+    for (int64_t r = tid; r < n; r += kCta) {
+      const uint64_t s = md.sector ? sector_state(md.t, (uint64_t)r) : (uint64_t)r;
+      double d = md.c0;
+      for (int g = 0; g < md.n_lin; ++g) d += s_lin[g].coef * (double)__popcll(s & s_lin[g].mask);
+      for (int q = 0; q < md.n_pairs; ++q) {
+        const PairEntry pe = s_pair[q];
+        d += s_pcoef[pe.grp] * (double)((s >> pe.i) & (s >> pe.j) & 1ull);
+      }
+      const double x = C[r];
+      double hv = d * x;
+      for (int e = 0; e < md.n_entries; ++e) {
+        const SpinEntry en = s_ent[e];
+        const int sel = (int)((s >> en.i) & 1ull) | ((int)((s >> en.j) & 1ull) << 1);
+        const int code = (en.phases >> (3 * sel)) & 7;
+        if (!code) continue;
+        const uint64_t s2 = s ^ en.mask;
+        const int64_t r2 = md.sector ? (int64_t)sector_rank(md.t, s2) : (int64_t)s2;
+        const double y = s_cls[en.cls] * C[r2];
+        hv += code == 1 ? y : -y;  // real models: codes +1 / -1 only
+      }
+      xh = fma(x, hv, xh);
+      P[r] = c1 * hv - c2 * P[r];
+    }
+    const double a = cta_sum(xh, s_w) * sg * sg;  // alpha_k = (H v_k, v_k)
+    const double gm = a * sg;
+    double pp = 0.0;
+    for (int64_t r = tid; r < n; r += kCta) {
+      const double p = fma(-gm, C[r], P[r]);
+      P[r] = p;
+      pp = fma(p, p, pp);
+    }
+    const double b = sqrt(cta_sum(pp, s_w));
+    if (tid == 0) {
+      lz.alpha[k] = a;
+      lz.beta[k] = b;
+    }
+    if (!(b > brk * fmax(1.0, fabs(a)))) {
+      done = 1;
+    } else {
+      const double sn = 1.0 / b;
+      c1 = sn;
+      c2 = b * sg;
+      sg = sn;
+      if (tid == 0) lz.sig[k + 1] = sn;
+      double* t = C;
+      C = P;
+      P = t;
+    }
+  }
+  if (tid == 0) {
+    *lz.steps_done = k;
+    *lz.done = 1;
+  }
+  (void)Cout;
+}
+
+}  // namespace
+
+// dynamic shared memory of k_lz_cta: both vectors (its term tables are static, about 22 KB)
+size_t lz_cta_smem(const SpinDev& md) { return 2 * sizeof(double) * (size_t)md.dim; }
+
+Status launch_lz_cta(const SpinDev& md, const LzDev& lz, int steps, double brk, const double* C0, cudaStream_t st) {
+  const size_t smem = lz_cta_smem(md);
+  HPHI_CUDA_TRY(cudaFuncSetAttribute(k_lz_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_lz_cta<<<1, kCta, smem, st>>>(md, lz, steps, brk, C0, nullptr);
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
 }  // namespace hphi

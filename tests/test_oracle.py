@@ -359,12 +359,33 @@ def test_philox_known_answers():
         assert oracle.philox4x32_10(ctr, key).tolist() == want, name
 
 
-def test_gaussian_moments():
+def test_start_vector_numbers():
+    """Start-vector numbers (appendix A.2 / A.4: random coefficients): uniform in [-1, 1) on the
+    2^-52 grid, with the uniform distribution's moments; and the mapping from Philox words,
+    pinned on the published known-answer blocks whose counter has the form (e, 0, 0, 0)."""
     idx = np.arange(200000, dtype=np.uint64)
-    g = oracle.gauss_at(123432, idx, complex_=True)
+    g = oracle.random_at(123432, idx, complex_=True)
     for part in (g.real, g.imag):
-        assert abs(part.mean()) < 0.01 and abs(part.var() - 1.0) < 0.01
-        assert abs(np.mean(part ** 4) - 3.0) < 0.05
+        assert np.all(part >= -1.0) and np.all(part < 1.0)
+        assert np.all(part * 2.0 ** 52 == np.round(part * 2.0 ** 52))
+        assert abs(part.mean()) < 0.005 and abs(part.var() - 1.0 / 3.0) < 0.005
+        assert abs(np.mean(part ** 4) - 0.2) < 0.005
+    assert np.array_equal(oracle.random_at(123432, idx[:100], complex_=False), g[:100].real)
+    kat = _golden("philox4x32_10_kat.txt")
+    used = 0
+    for name, vals in kat.items():
+        v = [int(x, 16) for x in vals]
+        ctr, key, w = v[0:4], v[4:6], v[6:10]
+        if ctr[2] or ctr[3]:
+            continue
+        e = ctr[0] | (ctr[1] << 32)
+        seed = key[0] | (key[1] << 32)
+        want_re = ((((w[0] << 32) | w[1]) >> 11) - 2 ** 52) / 2.0 ** 52
+        want_im = ((((w[2] << 32) | w[3]) >> 11) - 2 ** 52) / 2.0 ** 52
+        got = oracle.random_at(seed, np.array([e], dtype=np.uint64), complex_=True)[0]
+        assert got.real == want_re and got.imag == want_im, name
+        used += 1
+    assert used >= 1
 
 
 def test_tpq_deferred_norm_identity():
@@ -398,7 +419,7 @@ def test_apply_H_rows_philox_matches_full_product(name, mk, nvec):
     seed = 4711 + nvec
     rows = np.unique(np.concatenate([[0, D - 1], np.random.default_rng(3).integers(0, D, size=200)]))
     for c in sorted({0, nvec - 1}):
-        v = oracle.gauss_at(seed, np.arange(D, dtype=np.uint64) * nvec + c, cplx)
+        v = oracle.random_at(seed, np.arange(D, dtype=np.uint64) * nvec + c, cplx)
         full = oracle.apply_H(spec, v)
         got = oracle.apply_H_rows_philox(spec, rows.astype(np.uint64), seed, cplx, nvec, c)
         assert np.max(np.abs(got - full[rows])) <= 1e-13 * np.max(np.abs(full))
