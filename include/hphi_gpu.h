@@ -260,6 +260,12 @@ typedef struct {
   void* ritz_out;      /* optional device fp64 [dim] (complex128 for complex models): with
                           refine = 1 receives the fp64 Ritz vector x of the lowest eigenvalue
                           (the start of hphi_inverse_iteration); NULL: not copied out     */
+  int reorth;          /* 1: full reorthogonalisation: after every step the new vector is
+                          orthogonalised against all kept Lanczos vectors (classical Gram-
+                          Schmidt, every inner product and update in fp64); keeps the m + 1
+                          vectors in device memory (HPHI_ERR_OUT_OF_MEMORY if they do not
+                          fit) and costs (k + 1) extra vector reads at step k.  The paper's
+                          recurrence (section 3.4) has none: 0, the default               */
 } hphi_lanczos_params;
 
 typedef struct {

@@ -356,3 +356,30 @@ def lanczos_convergence_step(alpha, beta, eps: float, first: int = 5, every: int
             return n
         prev = e1
     return None
+
+
+def lanczos_reorth(spec, v0, m: int, brk: float = 1e-13, want_vectors: bool = False):
+    """Section 3.4's recurrence with full reorthogonalisation: after w = H v_k - beta_k v_{k-1}
+    - alpha_k v_k, the components of w along every earlier v_j are removed (classical
+    Gram-Schmidt, numpy inner products) before beta_{k+1} = |w|.  Returns (alpha, beta[, V])."""
+    d = dim(spec)
+    v = _as_c128(v0, d)[:, 0].copy()
+    v /= np.linalg.norm(v)
+    V = [v]
+    a, b = [], []
+    v_prev, b_prev = np.zeros_like(v), 0.0
+    for _ in range(m):
+        w = apply_H(spec, v) - b_prev * v_prev
+        al = np.vdot(v, w).real
+        w = w - al * v
+        Vm = np.array(V)
+        w = w - Vm.T @ (Vm.conj() @ w)
+        be = np.linalg.norm(w)
+        a.append(al)
+        b.append(be)
+        if not be > brk * max(1.0, abs(al)):
+            break
+        v_prev, v, b_prev = v, w / be, be
+        V.append(v)
+    out = (np.array(a), np.array(b))
+    return out + (np.array(V),) if want_vectors else out

@@ -44,7 +44,7 @@ class LanczosParams(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("v0", ctypes.c_void_p),
                 ("n_eig", ctypes.c_int), ("refine", ctypes.c_int), ("breakdown", ctypes.c_double),
                 ("profile", ctypes.c_int), ("keep_basis", ctypes.c_int), ("v0_on_host", ctypes.c_int),
-                ("eps", ctypes.c_double), ("ritz_out", ctypes.c_void_p)]
+                ("eps", ctypes.c_double), ("ritz_out", ctypes.c_void_p), ("reorth", ctypes.c_int)]
 
 
 class LanczosResult(ctypes.Structure):
@@ -325,10 +325,11 @@ class Model:
 
     def lanczos(self, steps: int, prec=FP64, seed: int = 123432, v0=None, n_eig: int = 1, refine: bool = False,
                 breakdown: float = 0.0, profile: bool = False, keep_basis: int = 0, v0_on_host: bool = False,
-                eps: float = 0.0, ritz_out=None):
+                eps: float = 0.0, ritz_out=None, reorth: bool = False):
         """Section 3.4 Lanczos; returns dict(alpha, beta, steps, eig, e_refined, residual, variance, ms,
         converged).  eps > 0: appendix C's convergence test, steps is then the limit.  ritz_out: a CUDA
         fp64 (complex128) tensor of length dim that receives the refined Ritz vector (refine=True).
+        reorth: full reorthogonalisation against the kept Lanczos vectors (fp64 inner products).
         v0: start vector (a CUDA tensor, or any tensor moved to the device here); with v0_on_host
         it must be a host tensor, which the library copies in itself (hphi_lanczos_params.v0_on_host)."""
         torch = _torch()
@@ -353,7 +354,7 @@ class Model:
                     and ritz_out.numel() == self.dim):
                 raise LibraryError(-1, f"ritz_out must be a contiguous CUDA {want} tensor of length dim")
         p = LanczosParams(steps, prec, seed, vptr, n_eig, int(refine), breakdown, int(profile), int(keep_basis),
-                          int(on_host), float(eps), _dptr(ritz_out) if ritz_out is not None else None)
+                          int(on_host), float(eps), _dptr(ritz_out) if ritz_out is not None else None, int(reorth))
         r = LanczosResult()
         r.alpha = a.ctypes.data
         r.beta = b.ctypes.data
@@ -375,7 +376,8 @@ class Model:
         for i in range(ns):
             res[i].alpha = al[i].ctypes.data
             res[i].beta = be[i].ctypes.data
-        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0, int(keep_basis), 0, float(eps))
+        p = LanczosParams(steps, prec, seed, None, n_eig, int(refine), breakdown, 0, int(keep_basis), 0, float(eps),
+                          None, 0)
         self._check(self._L.hphi_lanczos_run_sectors(self._h, nu.ctypes.data, ns, ctypes.byref(p), res, _stream()))
         out = []
         for i in range(ns):

@@ -1240,6 +1240,7 @@ struct LzPlan {
   double eps = 0.0;  // convergence test of appendix C (0: off)
   void* ritz_out = nullptr;
   bool cta = false;  // the whole recurrence in one CTA (small real spin models)
+  bool reorth = false;  // full reorthogonalisation against the kept basis
   const double* v0 = nullptr;
   const double* v0_host = nullptr;  // start vector in host memory (copied in by start())
   uint64_t seed = 0;
@@ -1268,6 +1269,7 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   L.brk = p->breakdown > 0 ? p->breakdown : 1e-13;
   L.eps = p->eps > 0 ? p->eps : 0.0;
   L.ritz_out = p->ritz_out;
+  L.reorth = p->reorth != 0;
   const int steps = L.steps, prec = L.prec;
   const size_t esz = (prec == HPHI_FP64 ? 8 : 4) * (L.cplx ? 2 : 1);
   L.n_real = m->dim * (L.cplx ? 2 : 1);
@@ -1279,9 +1281,9 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   L.vbytes = vbytes;
   // keep the whole basis when asked, or when it fits comfortably (the refinement then needs
   // one streaming pass over it instead of a second Lanczos run)
-  if (L.refine && p->keep_basis >= 0) {
+  if (L.reorth || (L.refine && p->keep_basis >= 0)) {
     const size_t need = (size_t)(steps + 1) * vbytes;
-    if (p->keep_basis == 1) {
+    if (p->keep_basis == 1 || L.reorth) {
       L.store = true;
     } else {
       size_t free_b = 0, total_b = 0;
@@ -1317,16 +1319,19 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   }
   // small real spin models: both vectors in one CTA's shared memory, one kernel for all steps
   L.cta = m->kind == HPHI_SPIN_HALF && !L.cplx && prec == HPHI_FP64 && !L.refine && !L.profile && L.eps == 0.0 &&
-          hphi::lz_cta_smem(m->sdev) <= 200 * 1024;
+          !L.reorth && hphi::lz_cta_smem(m->sdev) <= 200 * 1024;
   // grids after the scratch: the split-row kernels run only when it holds what they need
   L.grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
   L.rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);
   L.vgrid = launch_grid(L.n_real);
   const int pgrid = std::max(std::max(L.grid, L.rgrid), L.vgrid);
-  if ((s = ws.partials.ensure(sizeof(double) * (size_t)pgrid * hphi::kMaxRedQ)).code) return s;
+  size_t pdoubles = (size_t)pgrid * hphi::kMaxRedQ;
+  if (L.reorth) pdoubles = std::max(pdoubles, hphi::ro_part_doubles(L.vgrid));
+  if ((s = ws.partials.ensure(sizeof(double) * pdoubles)).code) return s;
   L.partials = ws.partials.as<double>();
-  // scalars: alpha[m], beta[m], sig[m+1], coef[m], s[16], tri[16 + 5m], done, steps_done
-  L.nsc = 3 * (size_t)steps + 1 + steps + 16 + 16 + 5 * (size_t)steps + 4;
+  // scalars: alpha[m], beta[m], sig[m+1], coef[m], s[16], tri[16 + 5m], done, steps_done,
+  // then ro[2 (m + 1)]
+  L.nsc = 3 * (size_t)steps + 1 + steps + 16 + 16 + 5 * (size_t)steps + 4 + 2 * ((size_t)steps + 1);
   if ((s = ws.scal.ensure(sizeof(double) * L.nsc)).code) return s;
   L.base = ws.scal.as<double>();
   L.lz.alpha = L.base;
@@ -1338,6 +1343,7 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
   L.flags = reinterpret_cast<int*>(L.lz.tri + 16 + 5 * (size_t)steps);
   L.lz.done = L.flags;
   L.lz.steps_done = L.flags + 1;
+  L.lz.ro = reinterpret_cast<double*>(L.flags + 4);  // after the flags' two doubles of room
   if (L.profile) {
     L.ev.assign(2 * (size_t)steps, nullptr);
     for (auto& e : L.ev) {
@@ -1417,6 +1423,13 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
       if ((q = hphi::launch_lz_pass2(prec, cplx, L.lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, L.n_real,
                                      L.partials, L.vgrid, emax, st)).code)
         return q;
+      if (L.reorth && !with_x) {  // P is slot k + 1 of the kept basis; its norm replaces pass 2's
+        L.launches += hphi::reorth_launches(k);
+        if ((q = hphi::launch_reorth(prec, cplx, L.lz, k, slot(0), L.n_real,
+                                     (int64_t)(L.vbytes / (prec == HPHI_FP64 ? 8 : 4)), P, L.partials, L.partials,
+                                     L.vgrid, st)).code)
+          return q;
+      }
       if ((q = hphi::launch_lz_fin2(L.lz, k, L.brk, L.partials, L.vgrid, with_x, st)).code) return q;
       // appendix C: after five steps, then every two, unless the run already stopped
       if (!with_x && L.eps > 0.0 && k + 1 >= 5 && (k + 1 - 5) % 2 == 0 && k + 1 < steps) {

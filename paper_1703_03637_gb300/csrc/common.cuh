@@ -352,6 +352,7 @@ struct LzDev {           // device scalars of one Lanczos run
   int* done;             // [1]   breakdown flag
   int* steps_done;       // [1]
   double* tri;           // [8 + 3]  eigenvalues and refinement results
+  double* ro;            // [2 (m + 1)] reorthogonalisation coefficients (re, im) of C_0 .. C_k
 };
 
 Status launch_lz_init(int prec, bool cplx, const void* v0_f64, void* C, void* P, int64_t n_real, double* partials,
@@ -369,6 +370,12 @@ Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials
 // memory): C0 holds C_0 (after k_lz_init / its finaliser); fills alpha, beta, sig, steps_done
 size_t lz_cta_smem(const SpinDev& md);
 Status launch_lz_cta(const SpinDev& md, const LzDev& lz, int steps, double brk, const double* C0, cudaStream_t st);
+// full reorthogonalisation of the new P (slot k + 1 of the kept basis) against C_0 .. C_k,
+// then the partial |P|^2 that launch_lz_fin2 reads; part holds ro_part_doubles(grid) doubles
+size_t ro_part_doubles(int grid);
+Status launch_reorth(int prec, bool cplx, const LzDev& lz, int k, const void* V, int64_t n_real, int64_t stride_real,
+                     void* P, double* part, double* partials, int grid, cudaStream_t st);
+int reorth_launches(int k);
 // appendix C's test after a step: stop when T_n's first excited eigenvalue agrees with the
 // previous test's to eps (relative)
 Status launch_lz_conv(const LzDev& lz, double eps, cudaStream_t st);

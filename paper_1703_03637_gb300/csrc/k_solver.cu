@@ -6,6 +6,8 @@
 // Every reduction ends in a fixed-order fp64 sum over per-CTA partials.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "reduce.cuh"
 
@@ -344,6 +346,113 @@ __global__ void __launch_bounds__(kThreads) k_lz_combine(LzDev lz, const R* __re
   }
 }
 
+// ------------------------------------------------------------------ full reorthogonalisation
+// After pass 2 of step k (kept basis: slot j holds C_j, v_j = sigma_j C_j; slot k + 1 holds the
+// new P): P <- P - sum_{j <= k} <v_j, P> v_j = P - sum_j sigma_j^2 <C_j, P> C_j, every inner
+// product and every update accumulated in fp64 (classical Gram-Schmidt against the whole kept
+// basis), then |P|^2 for beta_{k+1}.  Inner products run kRoChunk vectors per pass over P.
+constexpr int kRoChunk = 16;
+
+template <class R, bool CPLX>
+__global__ void __launch_bounds__(kThreads) k_ro_dots(LzDev lz, const R* __restrict__ V, int64_t stride_real,
+                                                       int64_t n_elem, int j0, int nj, const R* __restrict__ P,
+                                                       double* __restrict__ part) {
+  constexpr int W = CPLX ? 2 : 1;
+  constexpr int NQ = W * kRoChunk;
+  __shared__ double s_part[kThreads / 32][NQ];
+  if (*lz.done) return;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_elem; i += (int64_t)gridDim.x * kThreads) {
+    const double pr = (double)P[W * i], pi = CPLX ? (double)P[W * i + 1] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kRoChunk; ++j) {
+      if (j < nj) {
+        const R* c = V + (int64_t)(j0 + j) * stride_real + W * i;
+        const double cr = (double)c[0];
+        if constexpr (CPLX) {
+          const double ci = (double)c[1];
+          acc[2 * j] = fma(cr, pr, fma(ci, pi, acc[2 * j]));        // Re conj(c) p
+          acc[2 * j + 1] = fma(cr, pi, fma(-ci, pr, acc[2 * j + 1]));  // Im conj(c) p
+        } else {
+          acc[j] = fma(cr, pr, acc[j]);
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double x = acc[q];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) s_part[wid][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += s_part[w][threadIdx.x];
+    part[(size_t)blockIdx.x * NQ + threadIdx.x] = t;
+  }
+}
+
+// coefficient of C_j: sigma_j^2 <C_j, P> (re, im)
+__global__ void __launch_bounds__(kThreads) k_ro_fin(LzDev lz, int j0, int nj, int nq_per_vec,
+                                                      const double* __restrict__ part, int grid) {
+  __shared__ double sm[kThreads];
+  if (*lz.done) return;
+  const int NQ = nq_per_vec * kRoChunk;
+  for (int q = 0; q < nj * nq_per_vec; ++q) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < grid; b += kThreads) t += part[(size_t)b * NQ + q];
+    t = block_sum(t, sm);
+    if (threadIdx.x == 0) {
+      const int j = j0 + q / nq_per_vec;
+      const double sg = lz.sig[j];
+      lz.ro[2 * j + (q % nq_per_vec)] = sg * sg * t;
+      if (nq_per_vec == 1) lz.ro[2 * j + 1] = 0.0;
+    }
+  }
+}
+
+template <class R, bool CPLX>
+__global__ void __launch_bounds__(kThreads) k_ro_update(LzDev lz, const R* __restrict__ V, int64_t stride_real,
+                                                         int64_t n_elem, int k, R* __restrict__ P,
+                                                         double* __restrict__ partials) {
+  constexpr int W = CPLX ? 2 : 1;
+  extern __shared__ double s_ro[];  // [2 (k + 1)]
+  __shared__ double sm[kThreads];
+  if (*lz.done) return;
+  for (int j = threadIdx.x; j < 2 * (k + 1); j += kThreads) s_ro[j] = lz.ro[j];
+  __syncthreads();
+  double pp = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_elem; i += (int64_t)gridDim.x * kThreads) {
+    double pr = (double)P[W * i], pi = CPLX ? (double)P[W * i + 1] : 0.0;
+    for (int j = 0; j <= k; ++j) {
+      const R* c = V + (int64_t)j * stride_real + W * i;
+      const double cr = (double)c[0];
+      if constexpr (CPLX) {
+        const double ci = (double)c[1];
+        const double ar = s_ro[2 * j], ai = s_ro[2 * j + 1];
+        pr = fma(-ar, cr, fma(ai, ci, pr));
+        pi = fma(-ar, ci, fma(-ai, cr, pi));
+      } else {
+        pr = fma(-s_ro[2 * j], cr, pr);
+      }
+    }
+    const R qr = (R)pr;
+    P[W * i] = qr;
+    pp = fma((double)qr, (double)qr, pp);
+    if constexpr (CPLX) {
+      const R qi = (R)pi;
+      P[W * i + 1] = qi;
+      pp = fma((double)qi, (double)qi, pp);
+    }
+  }
+  const double t = block_sum(pp, sm);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kMaxRedQ] = t;
+}
+
 // ------------------------------------------------------------------ refinement
 __global__ void k_refine_fin(LzDev lz, const double* __restrict__ partials, int grid, int which) {
   __shared__ double sm[kThreads];
@@ -592,6 +701,35 @@ Status launch_lz_combine(int prec, const LzDev& lz, const void* V, int64_t n_rea
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
+
+size_t ro_part_doubles(int grid) { return (size_t)grid * 2 * kRoChunk; }
+
+Status launch_reorth(int prec, bool cplx, const LzDev& lz, int k, const void* V, int64_t n_real, int64_t stride_real,
+                     void* P, double* part, double* partials, int grid, cudaStream_t st) {
+  const int64_t n_elem = cplx ? n_real / 2 : n_real;
+  const int nqv = cplx ? 2 : 1;
+  const size_t smem = sizeof(double) * 2 * (size_t)(k + 1);
+#define HPHI_RO(RR, CC)                                                                                              \
+  for (int j0 = 0; j0 <= k; j0 += kRoChunk) {                                                                        \
+    const int nj = std::min(kRoChunk, k + 1 - j0);                                                                   \
+    k_ro_dots<RR, CC><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const RR*>(V), stride_real, n_elem, j0, nj,    \
+                                                 reinterpret_cast<const RR*>(P), part);                             \
+    k_ro_fin<<<1, kThreads, 0, st>>>(lz, j0, nj, nqv, part, grid);                                                   \
+  }                                                                                                                  \
+  HPHI_CUDA_TRY(cudaFuncSetAttribute(k_ro_update<RR, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));  \
+  k_ro_update<RR, CC><<<grid, kThreads, smem, st>>>(lz, reinterpret_cast<const RR*>(V), stride_real, n_elem, k,      \
+                                                    reinterpret_cast<RR*>(P), partials);
+  if (prec == HPHI_FP64) {
+    if (cplx) { HPHI_RO(double, true) } else { HPHI_RO(double, false) }
+  } else {
+    if (cplx) { HPHI_RO(float, true) } else { HPHI_RO(float, false) }
+  }
+#undef HPHI_RO
+  HPHI_CUDA_TRY(cudaGetLastError());
+  return {};
+}
+
+int reorth_launches(int k) { return 2 * ((k + kRoChunk) / kRoChunk) + 1; }
 
 Status launch_refine_fin(const LzDev& lz, const double* partials, int grid, int which, cudaStream_t st) {
   k_refine_fin<<<1, kThreads, 0, st>>>(lz, partials, grid, which);

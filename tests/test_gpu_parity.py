@@ -946,26 +946,26 @@ def test_lanczos_convergence_test_appendix_c(prec):
     assert m.lanczos(40, prec=p, seed=9)["steps"] == 40
 
 
-@pytest.mark.parametrize("name,mk", [
-    ("heisenberg_ring16_sz8", lambda: wl.heisenberg_ring(16).with_basis(wl.BASIS_SZ, 8)),
-    ("hubbard_tilted8_44", lambda: wl.hubbard_tilted8(U=8.0).with_basis(wl.BASIS_NUMBER, 4, 4)),
-    ("kitaev_2x2", lambda: wl.kitaev_honeycomb(2, 2)),
+@pytest.mark.parametrize("name,mk,steps,outer", [
+    ("heisenberg_ring16_sz8", lambda: wl.heisenberg_ring(16).with_basis(wl.BASIS_SZ, 8), 30, 6),
+    ("hubbard_tilted8_44", lambda: wl.hubbard_tilted8(U=8.0).with_basis(wl.BASIS_NUMBER, 4, 4), 60, 6),
+    ("kitaev_2x2", lambda: wl.kitaev_honeycomb(2, 2), 30, 8),
 ])
-def test_inverse_iteration_cg(name, mk):
-    """Section 3.4.1: from a Lanczos eigenvector of 60 steps (residual above 1e-6) CG inverse
+def test_inverse_iteration_cg(name, mk, steps, outer):
+    """Section 3.4.1: from an unconverged Lanczos eigenvector (residual 1e-5 .. 1e-3) CG inverse
     iteration reaches the oracle's shifted solves and a residual near fp64 rounding."""
     spec = mk()
     m = hp.Model.from_spec(spec)
     x = torch.zeros(m.dim, dtype=torch.complex128 if m.is_complex else torch.float64, device="cuda")
-    r = m.lanczos(60, seed=5, refine=True, ritz_out=x)
+    r = m.lanczos(steps, seed=5, refine=True, ritz_out=x)
     x0 = x.cpu().numpy().copy()
     assert abs(np.linalg.norm(x0) - 1.0) < 1e-6 and r["residual"] > 1e-6
     # the Rayleigh quotient lies within the residual of an eigenvalue: a shift of twice the
     # residual keeps H - E + delta positive definite
     E = float(r["e_refined"])
     delta = 2.0 * float(r["residual"])
-    out = m.inverse_iteration(x, E, shift=delta, outer=6, max_cg=20000, cg_tol=1e-13)
-    y = oracle.inverse_iteration(spec, x0, E, delta, outer=6)
+    out = m.inverse_iteration(x, E, shift=delta, outer=outer, max_cg=20000, cg_tol=1e-13)
+    y = oracle.inverse_iteration(spec, x0, E, delta, outer=outer)
     xg = x.cpu().numpy()
     assert abs(np.linalg.norm(xg) - 1.0) < 1e-12
     assert abs(abs(np.vdot(y, xg)) - 1.0) < 1e-10
@@ -1019,3 +1019,37 @@ def test_lanczos_one_cta_heisenberg_ring12_full():
     as_, _ = oracle.lanczos(sec, oracle.random_at(7, np.arange(ms.dim, dtype=np.uint64), False), 60)
     assert rs["launches"] <= 6 and _rel(rs["alpha"][:20], as_[:20]) < 1e-12
     assert abs(rs["eig"][0] - e0) < 1e-10 * abs(e0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,mk", [
+    ("heisenberg_ring10_full", lambda: wl.heisenberg_ring(10)),
+    ("xxz_complex_sector", lambda: wl.random_xxz_model(11, 20, seed=8).with_basis(wl.BASIS_SZ, 5)),
+])
+def test_lanczos_full_reorthogonalisation(name, mk, prec):
+    """reorth=True: the recurrence with every new vector orthogonalised against all kept
+    vectors in fp64 follows the oracle's reorthogonalised recurrence well past the point where
+    the plain one loses orthogonality, and its Ritz values carry no spurious copies."""
+    spec = mk()
+    m = hp.Model.from_spec(spec)
+    p = hp.FP64 if prec == "fp64" else hp.FP32
+    steps = 100
+    r = m.lanczos(steps, prec=p, seed=11, n_eig=6, reorth=True)
+    v0 = oracle.random_at(11, np.arange(m.dim, dtype=np.uint64), m.is_complex)
+    a, b = oracle.lanczos_reorth(spec, v0, steps)
+    # the first 30 steps: on the ring's symmetric Krylov space the recurrence turns sensitive to
+    # rounding after about 40 steps (the oracle against itself with a 1e-15 perturbation)
+    n = min(30, len(a), r["steps"])
+    if prec == "fp64":
+        assert _rel(r["alpha"][:n], a[:n]) < 1e-10 and _rel(r["beta"][:n], b[:n]) < 1e-10
+    else:
+        assert _rel(r["alpha"][:n], a[:n]) < 1e-5 and _rel(r["beta"][:n], b[:n]) < 1e-5
+    evs = np.linalg.eigvalsh(oracle.dense_H(spec))
+    mult = lambda e, vals, tol: int(np.sum(np.abs(vals - e) < tol))  # noqa: E731
+    tol = 1e-8 if prec == "fp64" else 1e-4
+    for e in r["eig"][:3]:
+        assert np.min(np.abs(evs - e)) < tol * max(1.0, abs(e))
+    assert mult(evs[0], r["eig"], 10 * tol) <= mult(evs[0], evs, 1e-7)
+    # the refinement path works from the kept basis
+    rr = m.lanczos(60, prec=p, seed=11, reorth=True, refine=True)
+    assert abs(rr["e_refined"] - evs[0]) < 1e-8 * max(1.0, abs(evs[0])) and rr["residual"] < 1e-3

@@ -560,3 +560,27 @@ def test_lanczos_convergence_step_rule():
     e1n = oracle.ritz_values(a[:n], b[:n])[1]
     assert abs(e1n - (-2.0)) < 1e-8
     assert oracle.lanczos_convergence_step(a[:9], b[:9], 1e-300) is None
+
+
+def test_lanczos_reorth_keeps_the_basis_orthonormal():
+    """Full reorthogonalisation: the Lanczos vectors stay orthonormal to rounding long after the
+    plain recurrence has lost orthogonality, the first steps equal the plain recurrence's, and
+    the Ritz values show no spurious copies of converged eigenvalues (each lowest Ritz value is
+    a distinct eigenvalue of H)."""
+    spec = wl.heisenberg_ring(10)
+    D = oracle.dim(spec)
+    v0 = oracle.random_at(11, np.arange(D, dtype=np.uint64), False)
+    a, b, V = oracle.lanczos_reorth(spec, v0, 120, want_vectors=True)
+    G = V.conj() @ V.T
+    assert np.max(np.abs(G - np.eye(len(V)))) < 1e-12
+    ap, bp = oracle.lanczos(spec, v0, 120)
+    assert np.max(np.abs(a[:10] - ap[:10])) < 1e-12 and np.max(np.abs(b[:10] - bp[:10])) < 1e-12
+    evs = np.linalg.eigvalsh(oracle.dense_H(spec).real)
+    mult = lambda e, vals: int(np.sum(np.abs(vals - e) < 1e-7))  # noqa: E731
+    rv = oracle.ritz_values(a, b)[:6]
+    for e in rv:  # every low Ritz value is an eigenvalue, at most as often as its multiplicity
+        assert np.min(np.abs(evs - e)) < 1e-9 and mult(e, rv) <= mult(e, evs)
+    assert mult(evs[0], evs) == 1 and mult(evs[0], rv) == 1
+    # the plain recurrence has spurious copies of the (non-degenerate) ground state by now
+    rp = oracle.ritz_values(ap, bp)[:6]
+    assert mult(evs[0], rp) >= 2
