@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_sec_hi(const SecDev d, const T* __
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
         const int col = col0 + j * 32;
-        if (col < nq) W[o + col] = acc[j];
+        if (col < nq) __stcs(W + o + col, acc[j]);  // read once, by pass R
       }
     }
   }
@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
           const R dg = s_dtab[(c & 0xffu) + d.dstride * (c >> 8)];
           const int64_t idx = (int64_t)s_roff[m] + u;
           const T xq = tile[u * K + m];
-          const T wv = Wh[idx];
+          const T wv = __ldcs(Wh + idx);  // W and P stream: they must not evict the gathered rows
           if constexpr (!FIX) {
             const R hv = ONE ? dg * xq + coef0 * (acc[e][m] + wv) : dg * xq + (acc[e][m] + wv);
             epilogue<float, E, NQ>(idx, 0, xq, 0.f, hv, 0.f, reinterpret_cast<float*>(w), fa, es, s_inv, red);
@@ -949,7 +949,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
               } else if constexpr (E == Epi::kLanczos1) {
                 double* P = reinterpret_cast<double*>(fa.out);
                 const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
-                P[idx] = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+                __stcs(P + idx, fma(es.c1 * s_e2, hvu, -(es.c2 * __ldcs(Pin + idx))));
                 red.add(0, xr, hvu);
                 red.tick();
               }
@@ -1060,23 +1060,13 @@ Status launch_hi(const SecDev& d, const T* X, T* W, const int* done, unsigned lo
   HPHI_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   const int grid = num_sms() * 8;
   const bool one = d.one_cls != 0;
-  // stripes of 512 bytes per row, narrowed (down to one 32-element warp access) while one
-  // stripe of the largest class exceeds 48 MB: that stripe is the L2 working set
-  uint32_t rows = 0;
-  for (int i = 0; i < d.n_pc; ++i) rows = std::max(rows, d.pc_row0[i + 1] - d.pc_row0[i]);
-  int ept = sizeof(T) == 8 ? 2 : 4;
-  while (ept > 1 && (double)rows * 32.0 * ept * sizeof(T) > 48e6) ept /= 2;
-#define HPHI_SECHI(EE)                                                                     \
-  if (one) k_sec_hi<T, EE, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);       \
-  else k_sec_hi<T, EE, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
-  if (ept == 4) {
-    HPHI_SECHI(4)
-  } else if (ept == 2) {
-    HPHI_SECHI(2)
-  } else {
-    HPHI_SECHI(1)
-  }
-#undef HPHI_SECHI
+  // 512-byte row stripes per warp item.  On the 6x6 sector the largest class's stripe (180 MB
+  // for int64) exceeds L2, yet 256-byte stripes measured 1.5x slower (185 against 124 ms): the
+  // kernel is bound by L2 reads of the partner stripes, and halving the stripe doubles the items
+  // and their neighbour-list reads without removing a DRAM read that mattered.
+  constexpr int EPT = sizeof(T) == 8 ? 2 : 4;
+  if (one) k_sec_hi<T, EPT, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+  else k_sec_hi<T, EPT, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }

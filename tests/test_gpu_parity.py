@@ -1053,3 +1053,33 @@ def test_lanczos_full_reorthogonalisation(name, mk, prec):
     # the refinement path works from the kept basis
     rr = m.lanczos(60, prec=p, seed=11, reorth=True, refine=True)
     assert abs(rr["e_refined"] - evs[0]) < 1e-8 * max(1.0, abs(evs[0])) and rr["residual"] < 1e-3
+
+
+def test_hubbard_18_sz0_tpq_full_size():
+    """Section 5.2.1's workload on one GPU: the half-filled 18-site cluster in its S^z = 0 sector
+    (dim 2,363,904,400).  FP32 storage takes the two-pass path (a 48,620-entry up-spin row is
+    194 KB in FP32); sampled rows of its H v match the oracle, and the first mTPQ records of an
+    FP32 run match an FP64 run of the generic kernel."""
+    W = wl.workload("hubbard_18_sz0_tpq")
+    spec = W["model"]
+    m = hp.Model.from_spec(spec)
+    assert m.dim == 2_363_904_400
+    seed = 424242
+    v = m.random_vector(seed, prec=hp.FP32)
+    w = m.apply_H(v)
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([[0, m.dim - 1], rng.integers(0, m.dim, size=3000)])).astype(np.uint64)
+    got = w[torch.as_tensor(rows.astype(np.int64), device="cuda"), 0].double().cpu().numpy()
+    ref = oracle.apply_H_rows_philox(spec, rows, seed, False).real
+    assert np.max(np.abs(got - ref)) <= 2e-5 * np.max(np.abs(ref))
+    del v, w
+    m.release_workspace()
+    torch.cuda.empty_cache()
+    r32 = m.tpq(1, 3, l=W["l"], prec=hp.FP32, seed=seed)
+    m.release_workspace()
+    torch.cuda.empty_cache()
+    r64 = m.tpq(1, 2, l=W["l"], prec=hp.FP64, seed=seed)
+    assert _rel(r32["u"][:2, 0], r64["u"][:, 0]) < 1e-5 and _rel(r32["h2"][:2, 0], r64["h2"][:, 0]) < 1e-5
+    m.release_workspace()
+    m.close()
+    torch.cuda.empty_cache()

@@ -584,3 +584,21 @@ def test_lanczos_reorth_keeps_the_basis_orthonormal():
     # the plain recurrence has spurious copies of the (non-degenerate) ground state by now
     rp = oracle.ritz_values(ap, bp)[:6]
     assert mult(evs[0], rp) >= 2
+
+
+def test_tilted18_cluster_of_section_5_2_1():
+    """The 18-site cluster (a0 = (3, 3), a1 = (-3, 3)): 36 bonds, coordination 4, the sector
+    dimension (18 C 9)^2 quoted in section 5.2.1, and one-particle levels
+    -2t (cos kx + cos ky) over the cluster's 18 momenta."""
+    W = wl.workload("hubbard_18_sz0_tpq")
+    spec = W["model"]
+    assert spec.n_sites == 18 and oracle.dim(spec) == 2_363_904_400 == W["dim"]
+    n, bonds = wl.tilted_square_bonds((3, 3), (-3, 3))
+    assert len(bonds) == 36
+    deg = np.bincount(np.array(bonds).ravel(), minlength=n)
+    assert np.all(deg == 4)
+    one = wl.hubbard(n, bonds, 1.0, 0.0).with_basis(wl.BASIS_NUMBER, 1, 0)
+    ev = np.sort(np.linalg.eigvalsh(oracle.dense_H(one)))
+    ks = [(kx, ky) for kx in range(6) for ky in range(6) if (3 * kx + 3 * ky) % 6 == 0 and (-3 * kx + 3 * ky) % 6 == 0]
+    want = np.sort([-2 * (math.cos(math.pi * kx / 3) + math.cos(math.pi * ky / 3)) for kx, ky in ks])
+    assert len(ks) == 18 and np.allclose(ev, want, atol=1e-12)

@@ -303,6 +303,13 @@ def workload(name: str) -> dict:
         # the 6x6 sector at a size for kernel profiling (a 1.24 GB fp64 vector, above L2)
         m = heisenberg_square(6, 5).with_basis(BASIS_SZ, 15)
         return dict(model=m, steps=100, prec="fp64", dim=math.comb(30, 15))
+    if name == "hubbard_18_sz0_tpq":
+        # section 5.2.1: the half-filled 18-site cluster (a0 = (3, 3), a1 = (-3, 3)), t = 1, U = 8,
+        # S^z = 0 (N_up = N_dn = 9): dim (18 C 9)^2 = 2,363,904,400; one mTPQ start, l = 8 (the
+        # Gershgorin bound of H / N_s: U * 9 + 72 possible hops, over 18 sites)
+        n, bonds = tilted_square_bonds((3, 3), (-3, 3))
+        m = hubbard(n, bonds, 1.0, 8.0, name="hubbard_tilted18").with_basis(BASIS_NUMBER, 9, 9)
+        return dict(model=m, steps=1000, n_starts=1, l=8.0, prec="fp32", dim=math.comb(18, 9) ** 2)
     if name == "heisenberg_6x6_sz0":
         m = heisenberg_square(6, 6).with_basis(BASIS_SZ, 18)
         return dict(model=m, steps=100, prec="mixed", dim=math.comb(36, 18))
@@ -310,4 +317,4 @@ def workload(name: str) -> dict:
 
 
 WORKLOADS = ["heisenberg_ring12_full", "hubbard_4x4_8u8d", "kitaev_24_tpq64", "j1j2_ring28_all_sectors",
-             "heisenberg_6x6_sz0", "kitaev_18_tpq64", "heisenberg_6x5_sz15"]
+             "heisenberg_6x6_sz0", "kitaev_18_tpq64", "heisenberg_6x5_sz15", "hubbard_18_sz0_tpq"]
