@@ -51,34 +51,6 @@ __device__ __forceinline__ void st(S* __restrict__ p, int64_t i, typename Traits
   }
 }
 
-// streaming access (ld.global.cs / st.global.cs: evict first) for the vectors an epilogue
-// touches once per pass, so they do not push the gathered input out of L2
-template <class S>
-__device__ __forceinline__ void ld_cs(const S* __restrict__ p, int64_t i, typename Traits<S>::R& re,
-                                      typename Traits<S>::R& im) {
-  const S x = __ldcs(p + i);
-  if constexpr (Traits<S>::kCplx) {
-    re = x.x;
-    im = x.y;
-  } else {
-    re = x;
-    im = 0;
-  }
-}
-
-template <class S>
-__device__ __forceinline__ void st_cs(S* __restrict__ p, int64_t i, typename Traits<S>::R re,
-                                      typename Traits<S>::R im) {
-  if constexpr (Traits<S>::kCplx) {
-    S x;
-    x.x = re;
-    x.y = im;
-    __stcs(p + i, x);
-  } else {
-    __stcs(p + i, re);
-  }
-}
-
 // m * 2^eoff rounded to nearest even: the hardware int64 -> fp64 conversion (round to
 // nearest even) and an exact power-of-two scale.  Measured on GB300, this runs three
 // times faster than assembling the result's bits with 64-bit integer operations.
@@ -182,9 +154,9 @@ __device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>:
     S* P = reinterpret_cast<S*>(fa.out);
     const S* Pin = fa.in ? reinterpret_cast<const S*>(fa.in) : P;
     R pr, pi;
-    ld_cs<S>(Pin, idx, pr, pi);
+    ld<S>(Pin, idx, pr, pi);
     const R c1 = (R)es.c1, c2 = (R)es.c2;
-    st_cs<S>(P, idx, c1 * hr - c2 * pr, c1 * hi - c2 * pi);
+    st<S>(P, idx, c1 * hr - c2 * pr, c1 * hi - c2 * pi);
     red.add(0, sr, hr);
     if constexpr (C) red.add(0, si, hi);
     red.tick();
@@ -195,7 +167,7 @@ __device__ __forceinline__ void epilogue(int64_t idx, int c, typename Traits<S>:
     const R inv = (R)s_inv[c], l = (R)fa.l, ins = (R)fa.inv_ns;
     const R nr = inv * (l * sr - hr * ins);
     const R ni = inv * (l * si - hi * ins);
-    st_cs<S>(Xn, idx, nr, ni);
+    st<S>(Xn, idx, nr, ni);
     red.add(0, sr, hr);
     red.add(1, hr, hr);
     if constexpr (C) {

