@@ -560,6 +560,8 @@ def run_sectors(args, world, rank, local):
     refine = prec == hp.FP32
     m = hp.Model.from_spec(spec)
     seed = wl.START_SEED + rank
+    # untimed: the split-row shape of every sector of at least 2^20 rows
+    tune = m.autotune(prec) if args.autotune else None
     for _ in range(args.warmup):
         m.lanczos_sectors(sectors, steps, prec=prec, seed=seed, refine=refine)
     stream = torch.cuda.current_stream()
@@ -592,7 +594,7 @@ def run_sectors(args, world, rank, local):
     achieved = alg * args.steps / (ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-            "kernel": "whole sector graph (k_hv_spin Lanczos pass 1 + pass 2 + solvers); lower bound",
+            "kernel": "whole sector graph (split-row or one-CTA Lanczos per sector + pass 2 + solvers); lower bound",
             "algorithmic_bytes_per_launch": alg}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
@@ -601,7 +603,7 @@ def run_sectors(args, world, rank, local):
         "config": {"workload": args.workload, "dim_total": sum(dims), "sectors": len(sectors), "lanczos_steps": steps,
                    "model": spec.name, "start": "philox uniform [-1, 1), seed 123432+rank",
                    "l2": l2_note(max(dims) * (8 if prec == hp.FP64 else 4)), "parallelism": f"replicas{world}"},
-        "e0_min": min(e), "roofline": roof, "gpu_launches": launches, "clocks": clocks,
+        "e0_min": min(e), "roofline": roof, "gpu_launches": launches, "clocks": clocks, "autotune": tune,
     }
     if args.cpu_baseline:
         sub = spec.with_basis(wl.BASIS_SZ, spec.n_sites // 2)

@@ -169,13 +169,16 @@ typedef struct {
 
 /* Times the launch configurations of the model's H v at precision prec (HPHI_FP64 or
  * HPHI_FP32) on a seeded vector and keeps the fastest for every later hphi_apply_H /
- * hphi_lanczos_run / hphi_tpq_run on this model.  Today the two-pass Hubbard path is tuned
- * (columns per thread of the down-spin pass x rows per tile of the up-spin pass); other
- * models report n_candidates = 0.  Real spin models in an S^z sector that take the
- * split-row path (see hphi_set_sector_split) are tuned over the split: the default low part
- * and up to two bits fewer, each with every tile height that fits.  Uses the model's
- * workspace; synchronises the stream.  *out may be NULL.  No counterpart in the paper (its
- * CPU code has no launch shapes). */
+ * hphi_lanczos_run / hphi_tpq_run on this model.  The two-pass Hubbard path is tuned over
+ * columns per thread of the down-spin pass x rows per tile of the up-spin pass.  Real spin
+ * models in an S^z sector that take the split-row path (see hphi_set_sector_split) are tuned
+ * over the split: the default low part and up to two bits fewer, each with every tile height
+ * that fits.  A real spin model in its full basis has every S^z sector of at least 2^20 rows
+ * tuned that way: hphi_lanczos_run_sectors keeps those sectors' shapes; the result then
+ * counts the candidates of all of them and reports the timings of the largest.  Other models
+ * report n_candidates = 0.  Uses the model's workspace (and the sectors' own); synchronises
+ * the stream.  *out may be NULL.  No counterpart in the paper (its CPU code has no launch
+ * shapes). */
 int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream);
 
 /* Split-row H v of real spin models in an S^z sector, section 3.1's split of a configuration

@@ -1094,11 +1094,54 @@ int hphi_set_sector_split(hphi_model* m, int prec, int L, int K, void* stream) {
   return HPHI_OK;
 }
 
+}  // extern "C"
+
+namespace {
+hphi::Status sector_model(hphi_model* m, int n_up, cudaStream_t st, hphi_model** out);
+
+// A spin model in its full basis: tune the split-row shape of every S^z sector of at least
+// 2^20 rows, the sectors hphi_lanczos_run_sectors runs (their sub-models keep the shapes).
+// The result reports the candidates of all of them and the timings of the largest.
+hphi::Status tune_sectors(hphi_model* m, int prec, hphi_tune_result* res, cudaStream_t st) {
+  if (m->n_sites > 40) return {};
+  int n_cand = 0;
+  hphi_tune_result big{};
+  int64_t big_dim = 0;
+  for (int n_up = 0; n_up <= m->n_sites; ++n_up) {
+    const int64_t d = (int64_t)binom_host(m->n_sites, n_up);
+    if (d < ((int64_t)1 << 20)) continue;
+    hphi_model* sub = nullptr;
+    hphi::Status s = sector_model(m, n_up, st, &sub);
+    if (s.code) return s;
+    const int pi = prec == HPHI_FP64 ? 0 : 1;
+    if (!sub->sec_ok[pi] || sub->sec_L[pi] < 0 || sub->cplx_model) continue;
+    hphi_tune_result r{};
+    if ((s = sec_autotune(sub, prec, &r, st)).code) return s;
+    n_cand += r.n_candidates;
+    if (d > big_dim) {
+      big_dim = d;
+      big = r;
+    }
+  }
+  *res = big;
+  res->n_candidates = n_cand;
+  return {};
+}
+}  // namespace
+
+extern "C" {
+
 int hphi_autotune(hphi_model* m, int prec, hphi_tune_result* out, void* stream) {
   int rc = check_built(m);
   if (rc) return rc;
   if (prec != HPHI_FP64 && prec != HPHI_FP32) return fail(m, HPHI_ERR_INVALID_ARG, "autotune: prec FP64 or FP32");
   hphi_tune_result res{};
+  if (m->kind == HPHI_SPIN_HALF && m->basis == HPHI_BASIS_FULL && !m->cplx_model) {
+    hphi::Status s = tune_sectors(m, prec, &res, (cudaStream_t)stream);
+    if (s.code) return fail(m, s);
+    if (out) *out = res;
+    return HPHI_OK;
+  }
   if (m->kind == HPHI_SPIN_HALF && m->sec_ok[prec == HPHI_FP64 ? 0 : 1] && m->sec_L[prec == HPHI_FP64 ? 0 : 1] >= 0 &&
       !m->cplx_model) {
     hphi::Status s = sec_autotune(m, prec, &res, (cudaStream_t)stream);
