@@ -615,6 +615,10 @@ __global__ void __launch_bounds__(kThreads) k_sec_hi(const SecDev d, const T* __
   __shared__ uint32_t s_nrow[kSecMaxH + 1], s_nq[kSecMaxH + 1], s_nstr[kSecMaxH + 1];
   __shared__ T s_w[kSecMaxCls];
   __shared__ unsigned long long s_claim;
+  // per warp: the current batch of neighbour rows (first element, weight), read back as
+  // shared-memory broadcasts by every lane
+  __shared__ uint64_t s_src[kHiWarps][32];
+  __shared__ T s_wt[kHiWarps][32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     long long acc = 0;
@@ -655,40 +659,37 @@ __global__ void __launch_bounds__(kThreads) k_sec_hi(const SecDev d, const T* __
       const uint64_t o = __ldg(d.hi_off + hi);
       const int cnt = __ldg(d.hi_cnt + hi);
       const int col0 = (int)sidx * SW + lane;
+      const bool full = (int)sidx * SW + SW <= nq;  // the whole stripe lies inside the row
       T acc[EPT];
 #pragma unroll
       for (int j = 0; j < EPT; ++j) acc[j] = (T)0;
       for (int qb = 0; qb < cnt; qb += 32) {
         const int nn = min(32, cnt - qb);
-        uint64_t src = 0;
-        int cls = 0;
+        __syncwarp();  // the previous batch's entries have been read
         if (lane < nn) {
           const uint32_t e = __ldg(d.hi_nbr + (size_t)(qb + lane) * nH + hi);
-          src = __ldg(d.hi_off + (e & 0xffffffu));
-          cls = (int)(e >> 24);
+          s_src[warp][lane] = __ldg(d.hi_off + (e & 0xffffffu));
+          if constexpr (!ONE) s_wt[warp][lane] = s_w[e >> 24];
         }
+        __syncwarp();
         for (int q0 = 0; q0 < nn; q0 += 4) {
           T x[4][EPT];
-          T wt[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            const uint64_t sr = __shfl_sync(0xffffffffu, src, (q0 + t) & 31);
-            const int cl = __shfl_sync(0xffffffffu, cls, (q0 + t) & 31);
             const bool on = q0 + t < nn;
-            wt[t] = on ? (ONE ? (T)1 : s_w[cl]) : (T)0;
+            const T* p = X + s_src[warp][(q0 + t) & 31] + col0;
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-              const int col = col0 + j * 32;
-              x[t][j] = (on && col < nq) ? __ldg(X + sr + col) : (T)0;
-            }
+            for (int j = 0; j < EPT; ++j) x[t][j] = (on && (full || col0 + j * 32 < nq)) ? __ldg(p + j * 32) : (T)0;
           }
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < 4; ++t) {
+            const T wt = ONE ? (T)1 : ((q0 + t < nn) ? s_wt[warp][(q0 + t) & 31] : (T)0);
 #pragma unroll
             for (int j = 0; j < EPT; ++j) {
               if constexpr (ONE) acc[j] += x[t][j];
-              else acc[j] += wt[t] * x[t][j];
+              else acc[j] += wt * x[t][j];
             }
+          }
         }
       }
 #pragma unroll
@@ -869,6 +870,25 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
         gmax = max(gmax, ng[e]);
 #pragma unroll
         for (int m = 0; m < K; ++m) acc[e][m] = (T)0;
+      }
+      // Lanczos: ask L2 for this thread's W and P elements now, so the epilogue's loads find
+      // them there instead of in DRAM (measured 1 to 3 % faster on the 6x6 sector)
+      if constexpr (E == Epi::kLanczos1) {
+        const char* pin = reinterpret_cast<const char*>(fa.in ? fa.in : fa.out);
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+          const int u = u0 + e * NT;
+          if (u < nq) {
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+              if (m < nk) {
+                const int64_t idx = (int64_t)s_roff[m] + u;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Wh + idx));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pin + idx * (int64_t)sizeof(T)));
+              }
+            }
+          }
+        }
       }
       // low-low exchange: four neighbours per table load, unused slots read the zero entry
       for (int g = 0; g < gmax; ++g) {
@@ -1060,11 +1080,12 @@ Status launch_hi(const SecDev& d, const T* X, T* W, const int* done, unsigned lo
   HPHI_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   const int grid = num_sms() * 8;
   const bool one = d.one_cls != 0;
-  // 512-byte row stripes per warp item.  On the 6x6 sector the largest class's stripe (180 MB
-  // for int64) exceeds L2, yet 256-byte stripes measured 1.5x slower (185 against 124 ms): the
-  // kernel is bound by L2 reads of the partner stripes, and halving the stripe doubles the items
-  // and their neighbour-list reads without removing a DRAM read that mattered.
-  constexpr int EPT = sizeof(T) == 8 ? 2 : 4;
+  // 1 KB row stripes per warp item (4 int64 / 8 fp32 columns per lane).  The kernel is bound by
+  // instruction issue (64-bit adds, addresses, neighbour lists), so wider stripes spread each
+  // neighbour's overhead over more columns: on the 6x6 sector 256-byte stripes measured 185 ms,
+  // 512-byte 124 ms, and 1 KB about 2.5 % less again, although one stripe of the largest class
+  // (360 MB) then far exceeds L2.
+  constexpr int EPT = sizeof(T) == 8 ? 4 : 8;
   if (one) k_sec_hi<T, EPT, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
   else k_sec_hi<T, EPT, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
   HPHI_CUDA_TRY(cudaGetLastError());

@@ -1087,8 +1087,9 @@ def test_hubbard_18_sz0_tpq_full_size():
 
 def test_autotune_full_basis_spin_model_tunes_its_sectors():
     """hphi_autotune on a full-basis spin model tunes the split-row shape of every S^z sector of
-    at least 2^20 rows; hphi_lanczos_run_sectors then runs those shapes with bit-identical FP64
-    results (the sums are exact integers whatever the shape)."""
+    at least 2^20 rows; hphi_lanczos_run_sectors then runs those shapes.  The products are exact
+    integer sums whatever the shape; the Lanczos inner products are summed in another order
+    (rows reach other threads), so alpha / beta agree to rounding."""
     spec = wl.j1j2_ring(24, 1.0, 0.5)
     m = hp.Model.from_spec(spec)
     before = m.lanczos_sectors([12, 10, 3], 12, seed=3)
@@ -1096,4 +1097,4 @@ def test_autotune_full_basis_spin_model_tunes_its_sectors():
     assert t["n_candidates"] >= 7 and t["split_L"] > 0
     after = m.lanczos_sectors([12, 10, 3], 12, seed=3)
     for a, b in zip(before, after):
-        assert np.array_equal(a["alpha"], b["alpha"]) and np.array_equal(a["beta"], b["beta"])
+        assert _rel(a["alpha"], b["alpha"]) < 1e-13 and _rel(a["beta"], b["beta"]) < 1e-13
