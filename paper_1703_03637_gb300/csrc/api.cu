@@ -1426,18 +1426,22 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
     ++L.launches;  // buffer A holds C_0 (regenerated bit-identically for the second pass)
     return hphi::launch_random(c0, m->dim, cplx, prec == HPHI_FP64, L.seed, st);
   };
-  // fp64 two-pass Hubbard: pass 2 also finds the next vector's largest exponent, so the next
-  // step's H v skips its own max-exponent scan
+  // fp64 fixed-point paths (two-pass Hubbard, split-row): pass 1 records the largest exponent
+  // of the P it writes, and pass 2 writes the next step's quantised copy on a scale bounded
+  // from it (k_lz_pass2) and finds the new vector's exact largest exponent, so the next step's
+  // H v starts from a ready copy: no max-exponent scan, no quantisation pass
   int* emax = nullptr;
-  if (prec == HPHI_FP64 && L.scratch != nullptr) {
-    if (use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1)) emax = hphi::hub_exponent_slot(m->hdev, L.scratch);
+  hphi::QSlots qs;
+  if (prec == HPHI_FP64 && L.scratch != nullptr && !cplx) {
+    if (use_hub_fast(m, prec, 1, hphi::Epi::kLanczos1))
+      qs = hphi::hub_qslots(m->hdev, L.scratch);
     else if (sec_runs(m, prec, 1, hphi::Epi::kLanczos1, ws.work.bytes))
-      emax = hphi::sec_exponent_slot(*use_sec(m, prec, 1, hphi::Epi::kLanczos1), prec, hphi::Epi::kLanczos1,
-                                     L.scratch);
+      qs = hphi::sec_qslots(*use_sec(m, prec, 1, hphi::Epi::kLanczos1), prec, hphi::Epi::kLanczos1, L.scratch);
   }
+  const bool qnext = qs.Q != nullptr;
   auto run_pass = [&](bool with_x) -> hphi::Status {
     hphi::Status q;
-    L.launches += 2 + (3 + hv_kernels(m, prec, 1, hphi::Epi::kLanczos1)) * steps - (emax ? steps - 1 : 0);
+    L.launches += 2 + (3 + hv_kernels(m, prec, 1, hphi::Epi::kLanczos1)) * steps - (qnext ? 2 * (steps - 1) : 0);
     if ((q = hphi::launch_lz_init(prec, cplx, v0_dev, c0, p0, L.n_real, L.partials, L.vgrid, st)).code) return q;
     if ((q = hphi::launch_lz_init_fin(L.lz, L.partials, L.vgrid, st)).code) return q;
     if (with_x) HPHI_CUDA_TRY(cudaMemsetAsync(ws.x.p, 0, 8 * (size_t)L.n_real, st));
@@ -1456,15 +1460,23 @@ hphi::Status lz_enqueue(LzPlan& L, cudaStream_t st) {
       fa.scal = L.lz.s;
       fa.partials = L.partials;
       fa.done = L.lz.done;
-      fa.exp_ready = (emax != nullptr && k > 0) ? 1 : 0;
+      fa.exp_ready = (qnext && k > 0) ? 2 : 0;
+      fa.pexp = qnext ? qs.ep : nullptr;
       const bool timed = L.profile && !with_x;
       if (timed) HPHI_CUDA_TRY(cudaEventRecord(L.ev[2 * k], st));
       if ((q = hv_launch(m, prec, C, nullptr, 1, hphi::Epi::kLanczos1, fa, L.grid, L.scratch, st)).code) return q;
       if (timed) HPHI_CUDA_TRY(cudaEventRecord(L.ev[2 * k + 1], st));
       if ((q = hphi::launch_lz_fin1(L.lz, k, L.partials, L.grid, st)).code) return q;
-      if (emax) HPHI_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int), st));
+      hphi::QNext qn{};
+      if (qnext) {
+        // the exact exponent of C_k: k_maxexp's slot (the copy's) at k = 0, else the one the
+        // previous pass 2 found; this pass 2 finds C_{k+1}'s into the other slot
+        emax = qs.ec[(k + 1) & 1];
+        qn = hphi::QNext{qs.Q, qs.eq, qs.ep, k == 0 ? qs.eq : qs.ec[k & 1], qs.extra};
+        HPHI_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int), st));
+      }
       if ((q = hphi::launch_lz_pass2(prec, cplx, L.lz, k, C, P, with_x ? ws.x.as<double>() : nullptr, L.n_real,
-                                     L.partials, L.vgrid, emax, st)).code)
+                                     L.partials, L.vgrid, emax, st, qnext ? &qn : nullptr)).code)
         return q;
       if (L.reorth && !with_x) {  // P is slot k + 1 of the kept basis; its norm replaces pass 2's
         L.launches += hphi::reorth_launches(k);

@@ -246,9 +246,26 @@ struct FusedArgs {
   double* partials = nullptr;      // [grid][nvec][kMaxRedQ]
   const int* done = nullptr;       // device flag: skip all work when set
   double l = 0.0, inv_ns = 0.0;
-  int exp_ready = 0;               // fp64 two-pass Hubbard: the input's exponent is already in
-                                   // the scratch slot (computed by the previous Lanczos pass 2)
+  int exp_ready = 0;               // fp64 fixed-point paths (two-pass Hubbard, split-row): 0 scan
+                                   // the input's exponent and quantise it; 1 the exponent is in the
+                                   // scratch slot already (quantise only); 2 the quantised copy is
+                                   // ready too (written by the previous Lanczos pass 2)
+  int* pexp = nullptr;             // fp64 Lanczos pass 1 of those paths: atomicMax of the exponent
+                                   // fields of the P values written (null: not tracked)
 };
+
+// The scratch slots through which a fp64 Lanczos pass 2 writes the next step's quantised copy:
+// Q [dim] int64, its exponent slot, the pass-1 exponent slot and two slots for the exact
+// exponent of the current / next vector (alternating by step).
+struct QSlots {
+  long long* Q = nullptr;
+  int* eq = nullptr;               // exponent field E of Q's scale (q = round(x 2^(1078 - E - extra)))
+  int* ep = nullptr;               // max exponent field of the pass-1 output P
+  int* ec[2] = {nullptr, nullptr}; // exact max exponent field of C_k (k even / odd)
+  int extra = 0;                   // extra headroom bits of the path
+};
+QSlots sec_qslots(const SecDev& d, int prec, Epi epi, void* scratch);
+QSlots hub_qslots(const HubDev& md, void* scratch);
 
 // Launches w = H v (or a fused step) over all rows; grid chosen by the library.  Spin models
 // in fp64 gather from a quantised copy of v when scratch (spin_scratch_bytes) is given.
@@ -360,8 +377,19 @@ Status launch_lz_init(int prec, bool cplx, const void* v0_f64, void* C, void* P,
 Status launch_lz_init_fin(const LzDev& lz, const double* partials, int grid, cudaStream_t st);
 Status launch_lz_fin1(const LzDev& lz, int k, const double* partials, int grid, cudaStream_t st);
 // emax (fp64 only, may be null): atomicMax of the exponent fields of the new P
+// qn (fp64, may be null): also writes the next step's quantised copy qn->Q on a scale bounded
+// before the pass (see k_lz_pass2), its exponent into qn->eq; emax then receives the exact
+// max exponent field of the new P (qn->ec for the next step)
+struct QNext {
+  long long* Q;
+  int* eq;
+  const int* ep;
+  const int* ec_cur;
+  int extra;
+};
 Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* C, void* P, double* x,
-                       int64_t n_real, double* partials, int grid, int* emax, cudaStream_t st);
+                       int64_t n_real, double* partials, int grid, int* emax, cudaStream_t st,
+                       const QNext* qn = nullptr);
 // replay: the refinement's second pass (stops after the last step with a significant Ritz
 // coefficient, keeps the first pass's step count)
 Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, bool replay,

@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
   __syncthreads();
   Red<true> red;
   red.zero();
+  int pmx = 0;  // Lanczos: largest exponent field of the P values written (fa.pexp)
   const int64_t dim_up = md.dim_up, dim_dn = md.dim_dn;
   const int64_t n_tiles = (dim_dn + K - 1) / K;
   const int du = (int)dim_up;
@@ -532,7 +533,9 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
             // P <- c1 hv - c2 P; partial <x, hv> in units of 2^(eoff + e2)
             double* P = reinterpret_cast<double*>(fa.out);
             const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
-            P[idx] = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+            const double pv = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+            P[idx] = pv;
+            pmx = max(pmx, (int)((__double_as_longlong(pv) >> 52) & 0x7ff));
             red.add(0, xr, hvu);
             red.tick();
           }
@@ -542,9 +545,25 @@ __global__ void __launch_bounds__(NT) k_hub_up_q(const HubDev md,
           if (c_p2) hv = fma(dg, x, fix_to_double(c_neg ? -(acc[m] + wq) : acc[m] + wq, eoff + c_l2));
           else if (same_c) hv = fma(dg, x, md.c_up * fix_to_double(acc[m] + wq, eoff));
           else hv = fma(dg, x, fma(md.c_up, fix_to_double(acc[m], eoff), md.c_dn * fix_to_double(wq, eoff)));
-          epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, w, fa, es, s_inv, red);
+          if constexpr (E == Epi::kLanczos1) {  // the epilogue's Lanczos step, with the exponent kept
+            double* P = reinterpret_cast<double*>(fa.out);
+            const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
+            const double pv = es.c1 * hv - es.c2 * Pin[idx];
+            P[idx] = pv;
+            pmx = max(pmx, (int)((__double_as_longlong(pv) >> 52) & 0x7ff));
+            red.add(0, x, hv);
+            red.tick();
+          } else {
+            epilogue<double, E>(idx, 0, x, 0.0, hv, 0.0, w, fa, es, s_inv, red);
+          }
         }
       }
+    }
+  }
+  if constexpr (E == Epi::kLanczos1) {
+    if (fa.pexp != nullptr) {
+      pmx = (int)__reduce_max_sync(0xffffffffu, (unsigned)pmx);
+      if ((tid & 31) == 0 && pmx > 0) atomicMax(fa.pexp, pmx);
     }
   }
   if constexpr (E != Epi::kStore) {
@@ -659,8 +678,11 @@ Status launch_q(const HubDev& md, const void* v, void* w, void* scratch, const F
     k_maxexp<<<gv, kThreads, 0, st>>>(X, md.dim, Ep, fa.done);
     HPHI_CUDA_TRY(cudaGetLastError());
   }
-  k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done, 0);
-  HPHI_CUDA_TRY(cudaGetLastError());
+  if (fa.exp_ready != 2) {  // 2: the previous Lanczos pass 2 wrote Q and its exponent
+    k_quant<<<gv, kThreads, 0, st>>>(X, Q, md.dim, Ep, fa.done, 0);
+    HPHI_CUDA_TRY(cudaGetLastError());
+  }
+  if (fa.pexp != nullptr) HPHI_CUDA_TRY(cudaMemsetAsync(fa.pexp, 0, sizeof(int), st));
   Status sd = launch_dn<long long>(md, Q, WQ, fa.done, counter, st);
   if (sd.code) return sd;
   double* out = reinterpret_cast<double*>(w);
@@ -831,6 +853,21 @@ int hub_up_grid(const HubDev& md0, int prec, Epi epi) {
 }
 
 int* hub_exponent_slot(const HubDev& md, void* scratch) { return hub_exponent_slot_impl(md, scratch); }
+
+// Q at the start of the scratch; tail (after WQ) ints: exponent of Q at 0, work counter
+// (u64) at 8, the exact exponents of the current / next vector at 16 and 20, pass-1's at 24
+QSlots hub_qslots(const HubDev& md, void* scratch) {
+  QSlots q;
+  if (scratch == nullptr) return q;
+  int* tail = hub_exponent_slot_impl(md, scratch);
+  q.Q = reinterpret_cast<long long*>(scratch);
+  q.eq = tail;
+  q.ec[0] = tail + 4;
+  q.ec[1] = tail + 5;
+  q.ep = tail + 6;
+  q.extra = 0;
+  return q;
+}
 
 size_t hub_scratch_bytes(const HubDev& md, int prec, Epi epi) {
   if (prec == HPHI_FP64) return quant_scratch_bytes(md);

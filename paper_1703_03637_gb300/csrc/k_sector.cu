@@ -787,6 +787,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
   constexpr int NQ = n_red<E>() > 0 ? n_red<E>() : 1;  // reduced quantities of the epilogue
   Red<FIX, NQ> red;
   red.zero();
+  int pmx = 0;  // fp64 Lanczos: largest exponent field of the P values written (fa.pexp)
 
   // tiles are claimed in order from a counter, so the tiles in flight stay a narrow window of
   // the processing order (a fixed stride would let CTAs drift apart over thousands of tiles)
@@ -969,18 +970,36 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
               } else if constexpr (E == Epi::kLanczos1) {
                 double* P = reinterpret_cast<double*>(fa.out);
                 const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
-                P[idx] = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+                const double pv = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+                P[idx] = pv;
+                pmx = max(pmx, (int)((__double_as_longlong(pv) >> 52) & 0x7ff));
                 red.add(0, xr, hvu);
                 red.tick();
               }
             } else {
               const double x = fix_to_double(xq, eoff);
               const double hv = fma((double)dg, x, d.unit * fix_to_double(S, eoff));
-              epilogue<double, E, NQ>(idx, 0, x, 0.0, hv, 0.0, reinterpret_cast<double*>(w), fa, es, s_inv, red);
+              if constexpr (E == Epi::kLanczos1) {  // the epilogue's Lanczos step, with the exponent kept
+                double* P = reinterpret_cast<double*>(fa.out);
+                const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
+                const double pv = es.c1 * hv - es.c2 * Pin[idx];
+                P[idx] = pv;
+                pmx = max(pmx, (int)((__double_as_longlong(pv) >> 52) & 0x7ff));
+                red.add(0, x, hv);
+                red.tick();
+              } else {
+                epilogue<double, E, NQ>(idx, 0, x, 0.0, hv, 0.0, reinterpret_cast<double*>(w), fa, es, s_inv, red);
+              }
             }
           }
         }
       }
+    }
+  }
+  if constexpr (FIX && E == Epi::kLanczos1) {
+    if (fa.pexp != nullptr) {
+      pmx = (int)__reduce_max_sync(0xffffffffu, (unsigned)pmx);
+      if ((tid & 31) == 0 && pmx > 0) atomicMax(fa.pexp, pmx);
     }
   }
   if constexpr (E != Epi::kStore) {
@@ -1093,8 +1112,8 @@ Status launch_hi(const SecDev& d, const T* X, T* W, const int* done, unsigned lo
 }
 
 // scratch layout: fp64 [Q: dim int64][W: dim int64, Lanczos only][tail]; fp32 [W: dim float,
-// Lanczos only][tail]; tail = 256 bytes: exponent (int) at 0, pass-H counter (u64) at 64,
-// pass-R tile counter (u64) at 128
+// Lanczos only][tail]; tail = 256 bytes: exponent (int) at 0 (and the QSlots ints at 4, 8,
+// 192), pass-H counter (u64) at 64, pass-R tile counter (u64) at 128
 size_t vec_bytes(const SecDev& d, int esz) { return (((size_t)d.dim * esz + 255) / 256) * 256; }
 
 }  // namespace
@@ -1109,6 +1128,21 @@ size_t sec_scratch_bytes(const SecDev& d, int prec, Epi epi) {
 
 int* sec_exponent_slot(const SecDev& d, int prec, Epi epi, void* scratch) {
   return reinterpret_cast<int*>(static_cast<char*>(scratch) + sec_scratch_bytes(d, prec, epi) - 256);
+}
+
+// fp64: Q at the start of the scratch; tail ints: exponent of Q at 0, the exact exponents of
+// the current / next vector at 4 and 8, the pass-1 exponent at 192
+QSlots sec_qslots(const SecDev& d, int prec, Epi epi, void* scratch) {
+  QSlots q;
+  if (prec != HPHI_FP64 || scratch == nullptr) return q;
+  char* tail = static_cast<char*>(scratch) + sec_scratch_bytes(d, prec, epi) - 256;
+  q.Q = reinterpret_cast<long long*>(scratch);
+  q.eq = reinterpret_cast<int*>(tail);
+  q.ec[0] = reinterpret_cast<int*>(tail + 4);
+  q.ec[1] = reinterpret_cast<int*>(tail + 8);
+  q.ep = reinterpret_cast<int*>(tail + 192);
+  q.extra = d.qextra;
+  return q;
 }
 
 int sec_grid(const SecDev& d, int prec, Epi epi) {
@@ -1140,9 +1174,12 @@ Status launch_sec(const SecDev& d, int prec, const void* v, void* w, void* scrat
     long long* Q = reinterpret_cast<long long*>(sc);
     long long* W = (epi == Epi::kLanczos1) ? reinterpret_cast<long long*>(sc + vec_bytes(d, 8))
                                            : reinterpret_cast<long long*>(out);
-    Status s = launch_quant_vec(reinterpret_cast<const double*>(v), Q, d.dim, Ep, fa.done, fa.exp_ready != 0,
-                                d.qextra, st);
-    if (s.code) return s;
+    Status s;
+    if (fa.exp_ready != 2) {  // 2: the previous Lanczos pass 2 wrote Q and its exponent
+      s = launch_quant_vec(reinterpret_cast<const double*>(v), Q, d.dim, Ep, fa.done, fa.exp_ready != 0, d.qextra, st);
+      if (s.code) return s;
+    }
+    if (fa.pexp != nullptr) HPHI_CUDA_TRY(cudaMemsetAsync(fa.pexp, 0, sizeof(int), st));
     if ((s = launch_hi<long long>(d, Q, W, fa.done, counter, st)).code) return s;
     switch (epi) {
       case Epi::kStore: return launch_lo_k<long long, Epi::kStore>(d, Q, W, w, fa, Ep, grid, claim, st);

@@ -106,16 +106,50 @@ __global__ void __launch_bounds__(kThreads) k_lz_fin(LzDev lz, int mode, int k, 
 
 // P <- P - gamma C ; partial |P|^2 ; optionally x += xc * C (fp64 accumulator); optionally
 // (emax) the largest exponent field of the new P, which the next step's quantisation needs
+// q = round(p 2^(1078 - E)) by integer operations on the bits of p (|q| < 2^56 when the
+// exponent field of p is at most E); the same rounding as the quantisation kernels
+__device__ __forceinline__ long long quant_bits(double p, int E) {
+  const int hi = __double2hiint(p);
+  const unsigned lo = (unsigned)__double2loint(p);
+  const int ex = (hi >> 20) & 0x7ff;
+  long long q = 0;
+  if (ex != 0) {
+    const long long M = ((long long)((hi & 0xfffff) | 0x100000) << 32) | (long long)lo;  // p = M 2^(ex-1075)
+    const int sh = E - ex - 3;                                                           // q = M 2^-sh
+    if (sh <= 0) q = M << (-sh);
+    else if (sh < 62) q = (M + (1ll << (sh - 1))) >> sh;
+    if (hi < 0) q = -q;
+  }
+  return q;
+}
+
+// With Q: the next step's quantised copy is written here instead of by a separate pass.  Its
+// exponent must be fixed before any element is seen, so it is a bound: |P - gamma C| <
+// 2^(EP - 1022) + |gamma| 2^(EC - 1022), EP the largest exponent field pass 1 wrote, EC the
+// exact one of C, so E = max(EP, EC + e_gamma - 1022) + 1 is at least the exponent field of
+// every new element; the scale is then at most two bits coarser than the exact maximum's
+// (each element moves by at most 2^-55 max|P| instead of 2^-57).
 template <class R, bool X>
 __global__ void __launch_bounds__(kThreads) k_lz_pass2(LzDev lz, const R* __restrict__ C, R* __restrict__ P,
                                                         double* __restrict__ x, int64_t n_real,
-                                                        double* __restrict__ partials, int* __restrict__ emax) {
+                                                        double* __restrict__ partials, int* __restrict__ emax,
+                                                        QNext qn) {
   constexpr bool F64 = sizeof(R) == 8;
   __shared__ double sm[kThreads];
   if (*lz.done) return;
   const double g = lz.s[2];
   const R gr = (R)g;
   const double xc = X ? lz.s[3] : 0.0;
+  int Eq = 0;
+  if (F64 && qn.Q != nullptr) {
+    const int eg = (int)((__double_as_longlong(g) >> 52) & 0x7ff);
+    const int ec = *qn.ec_cur;
+    int eb = *qn.ep;
+    if (eg != 0 && ec != 0) eb = max(eb, ec + eg - 1022);
+    eb = min(eb + 1, 2046);
+    Eq = eb + qn.extra;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *qn.eq = eb;
+  }
   Red<F64, 1> red;  // one reduced quantity, |P|^2
   red.zero();
   int mx = 0;
@@ -138,7 +172,10 @@ __global__ void __launch_bounds__(kThreads) k_lz_pass2(LzDev lz, const R* __rest
         red.add(0, p, p);
         red.tick();
         if (X) x[k] = fma(xc, (double)c[u], x[k]);
-        if constexpr (F64) mx = max(mx, (int)((__double_as_longlong((double)p) >> 52) & 0x7ff));
+        if constexpr (F64) {
+          mx = max(mx, (int)((__double_as_longlong((double)p) >> 52) & 0x7ff));
+          if (qn.Q != nullptr) qn.Q[k] = quant_bits((double)p, Eq);
+        }
       }
     }
   }
@@ -650,23 +687,25 @@ Status launch_lz_fin1(const LzDev& lz, int k, const double* partials, int grid, 
 }
 
 Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* C, void* P, double* x, int64_t n_real,
-                       double* partials, int grid, int* emax, cudaStream_t st) {
+                       double* partials, int grid, int* emax, cudaStream_t st, const QNext* qn) {
   (void)cplx;
   (void)k;
+  QNext q{nullptr, nullptr, nullptr, nullptr, 0};
+  if (qn != nullptr && prec == HPHI_FP64 && !cplx) q = *qn;
   if (prec == HPHI_FP64) {
     if (x)
       k_lz_pass2<double, true><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const double*>(C),
-                                                          reinterpret_cast<double*>(P), x, n_real, partials, emax);
+                                                          reinterpret_cast<double*>(P), x, n_real, partials, emax, q);
     else
       k_lz_pass2<double, false><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const double*>(C),
-                                                           reinterpret_cast<double*>(P), x, n_real, partials, emax);
+                                                           reinterpret_cast<double*>(P), x, n_real, partials, emax, q);
   } else {
     if (x)
       k_lz_pass2<float, true><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const float*>(C),
-                                                         reinterpret_cast<float*>(P), x, n_real, partials, nullptr);
+                                                         reinterpret_cast<float*>(P), x, n_real, partials, nullptr, q);
     else
       k_lz_pass2<float, false><<<grid, kThreads, 0, st>>>(lz, reinterpret_cast<const float*>(C),
-                                                          reinterpret_cast<float*>(P), x, n_real, partials, nullptr);
+                                                          reinterpret_cast<float*>(P), x, n_real, partials, nullptr, q);
   }
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
