@@ -339,9 +339,9 @@ def run_ours(args, world, rank, local):
         if args.mixed and prec == hp.FP64:
             tune["fp32"] = m.autotune(hp.FP32)
     m.release_workspace()
-    # a real spin model whose two FP64 vectors fit one CTA's shared memory runs the whole
-    # recurrence in one kernel (k_lz_cta), which only graph-launched (unprofiled) runs take
-    one_cta = prec == hp.FP64 and spec.kind == wl.SPIN and not m.is_complex and 16 * D <= 200 * 1024
+    # a real spin model of at most 32,768 rows runs the whole recurrence in one thread-block
+    # cluster (k_lz_cl), which only graph-launched (unprofiled) runs take
+    one_cta = prec == hp.FP64 and spec.kind == wl.SPIN and not m.is_complex and D <= 32768
     t = timed_lanczos(m, steps, prec, seed, args, world, local, rank, profile=not one_cta)
     t["one_cta"] = one_cta
     ms_step = t["ms"] / t["n"]
@@ -404,8 +404,8 @@ def assemble_lanczos_line(args, world, spec, D, steps, prec, esz, value, ms_step
             "kernel": hv_group_kernels(spec, hp_model_stub(spec), prec), "kernel_avg_ms": round(hv_avg_ms, 4),
             "algorithmic_bytes_per_launch": D * bytes_row}
     if t.get("one_cta"):
-        roof["kernel"] = ("k_lz_cta: the whole recurrence in one CTA, both vectors in shared memory (on chip); "
-                          "kernel_avg_ms is the run's device time per step")
+        roof["kernel"] = ("k_lz_cl: the whole recurrence in one 16-CTA cluster, both vectors in distributed "
+                          "shared memory (on chip); kernel_avg_ms is the run's device time per step")
     if prec == hp.FP64 and spec.kind == wl.SPIN and spec.basis == wl.BASIS_SZ:
         ops = SEC_FP64_OPS_PER_ROW * D
         roof["fp64_pipe"] = {"ops_per_row": SEC_FP64_OPS_PER_ROW, "achieved_tops": round(ops / (hv_avg_ms / 1e3) / 1e12, 4),

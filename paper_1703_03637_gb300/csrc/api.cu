@@ -1282,7 +1282,7 @@ struct LzPlan {
   double brk = 1e-13;
   double eps = 0.0;  // convergence test of appendix C (0: off)
   void* ritz_out = nullptr;
-  bool cta = false;  // the whole recurrence in one CTA (small real spin models)
+  bool cta = false;  // the whole recurrence in one thread-block cluster (small real spin models)
   bool reorth = false;  // full reorthogonalisation against the kept basis
   const double* v0 = nullptr;
   const double* v0_host = nullptr;  // start vector in host memory (copied in by start())
@@ -1360,9 +1360,10 @@ hphi::Status lz_prepare(hphi_model* m, const hphi_lanczos_params* p, LzPlan& L) 
       L.scratch = optional_scratch(m, gen);
     }
   }
-  // small real spin models: both vectors in one CTA's shared memory, one kernel for all steps
+  // small real spin models: both vectors in one thread-block cluster's shared memory, one
+  // kernel for all steps
   L.cta = m->kind == HPHI_SPIN_HALF && !L.cplx && prec == HPHI_FP64 && !L.refine && !L.profile && L.eps == 0.0 &&
-          !L.reorth && hphi::lz_cta_smem(m->sdev) <= 200 * 1024;
+          !L.reorth && hphi::lz_cta_smem(m->sdev) > 0;
   // grids after the scratch: the split-row kernels run only when it holds what they need
   L.grid = hv_grid_for(m, 1, prec, hphi::Epi::kLanczos1);
   L.rgrid = hv_grid_for(m, 1, HPHI_FP64, hphi::Epi::kRefine);

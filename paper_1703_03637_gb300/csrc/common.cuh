@@ -394,8 +394,10 @@ Status launch_lz_pass2(int prec, bool cplx, const LzDev& lz, int k, const void* 
 // coefficient, keeps the first pass's step count)
 Status launch_lz_fin2(const LzDev& lz, int k, double brk, const double* partials, int grid, bool replay,
                       cudaStream_t st);
-// the whole Lanczos recurrence in one CTA (real spin models whose two vectors fit in shared
-// memory): C0 holds C_0 (after k_lz_init / its finaliser); fills alpha, beta, sig, steps_done
+// the whole Lanczos recurrence in one thread-block cluster (real spin models of at most 32,768
+// rows, both vectors in the cluster's shared memory): C0 holds C_0 (after k_lz_init / its
+// finaliser); fills alpha, beta, sig, steps_done.  lz_cta_smem: bytes per CTA, 0 if the model
+// does not take the path
 size_t lz_cta_smem(const SpinDev& md);
 Status launch_lz_cta(const SpinDev& md, const LzDev& lz, int steps, double brk, const double* C0, cudaStream_t st);
 // full reorthogonalisation of the new P (slot k + 1 of the kept basis) against C_0 .. C_k,

@@ -578,67 +578,98 @@ Status launch_hv(bool hubbard, const void* md, int prec, bool cplx, const void* 
   return {HPHI_ERR_INVALID_ARG, "unknown epilogue"};
 }
 
-// ------------------------------------------------------------------ one-CTA Lanczos
-// The whole recurrence of section 3.4 in one CTA when both Lanczos vectors fit in shared
-// memory (real spin models up to 12,800 rows): no launch per step, no trip through HBM.
-// Each thread owns rows tid, tid + kCta, ...; a step computes (H C)[r] from the staged C
-// (diagonal from the bit counts, exchange terms gathered from shared memory), P = c1 H C -
-// c2 P and the partial (C, H C) in one sweep, reduces alpha across the CTA, then P -= gamma C
-// and |P|^2, reduces beta, and swaps the roles of C and P.  Scalars follow k_lz_fin's
-// conventions (C unnormalised, sigma = 1 / |C|), so k_tridiag reads the same arrays.
+// ------------------------------------------------------------------ one-cluster Lanczos
+// The whole recurrence of section 3.4 in one thread-block cluster when both Lanczos vectors fit
+// in the cluster's shared memory (real spin models up to kClMaxDim rows): no launch per step,
+// no trip through HBM.  CTA c of the cluster owns rows [c R, (c + 1) R) of C and P in its shared
+// memory; a thread owns rows of its CTA's slice.  H C gathers C[r'] from whichever CTA owns r'
+// through distributed shared memory.  GB300 issues fp64 at 1/64 of its fp32 rate, so one SM
+// alone would be bound by the fp64 work of the diagonal and exchange sums: the cluster spreads
+// it over kClCtas SMs.  Per step: P = c1 H C - c2 P with the partial (C, H C), cluster barrier,
+// alpha from the kClCtas partials (every CTA sums them in the same order), P -= gamma C with
+// |P|^2, cluster barrier, beta, swap C and P.  The two partial slots alternate, so each
+// barrier also ends the reads of the previous one.  Scalars follow k_lz_fin's conventions (C
+// unnormalised, sigma = 1 / |C|), so k_tridiag reads the same arrays.
 namespace {
-constexpr int kCta = 1024;
+constexpr int kClThreads = 256;
 
-__device__ double cta_sum(double x, double* s_w) {
+__device__ double cl_block_sum(double x, double* s_w) {
   for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();  // the previous sum has been read
   if (lane == 0) s_w[wid] = x;
   __syncthreads();
   double t = 0.0;
-  for (int k = 0; k < kCta / 32; ++k) t += s_w[k];  // same order in every thread
+  for (int k = 0; k < kClThreads / 32; ++k) t += s_w[k];  // same order in every thread
   return t;
 }
 
-__global__ void __launch_bounds__(kCta, 1) k_lz_cta(const SpinDev md, LzDev lz, int steps, double brk,
-                                                     const double* __restrict__ C0, double* __restrict__ Cout) {
-  extern __shared__ __align__(16) double sm_v[];
-  __shared__ double s_w[kCta / 32];
+// cluster barrier (all threads of all CTAs; shared-memory writes before it are visible after)
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// generic address of variable p of this CTA, as seen in CTA `rank` of the cluster
+template <class T>
+__device__ __forceinline__ T* cl_map(T* p, unsigned rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__global__ void __launch_bounds__(kClThreads, 1) k_lz_cl(const SpinDev md, LzDev lz, int steps, double brk,
+                                                         const double* __restrict__ C0, int R, int ncta) {
+  extern __shared__ __align__(16) double sm_v[];  // [2][R]: this CTA's slices of the two vectors
+  __shared__ double s_w[kClThreads / 32];
+  __shared__ double s_part[2];                   // this CTA's partial of each alternating slot
   __shared__ SpinEntry s_ent[kMaxSpinEntries];
   __shared__ double s_cls[kMaxClasses];
   __shared__ LinGroup s_lin[kMaxLin];
   __shared__ PairEntry s_pair[kMaxPairs];
   __shared__ double s_pcoef[kMaxPairGroups];
   const int tid = threadIdx.x;
+  const unsigned rank = cl_rank();
   const int64_t n = md.dim;
-  double* C = sm_v;
-  double* P = sm_v + n;
-  for (int64_t r = tid; r < n; r += kCta) {
-    C[r] = C0[r];
-    P[r] = 0.0;
+  const int64_t r0 = (int64_t)rank * R;
+  const int64_t left = n - r0;
+  const int nloc = left <= 0 ? 0 : (left < (int64_t)R ? (int)left : R);
+  double* A = sm_v;
+  double* B = sm_v + R;
+  for (int i = tid; i < nloc; i += kClThreads) {
+    A[i] = C0[r0 + i];
+    B[i] = 0.0;
   }
-  for (int k = tid; k < md.n_entries; k += kCta) s_ent[k] = md.entries[k];
-  for (int k = tid; k < md.n_classes; k += kCta) s_cls[k] = md.cls_coef[k].x;
-  for (int k = tid; k < md.n_lin; k += kCta) s_lin[k] = md.lin[k];
-  for (int k = tid; k < md.n_pairs; k += kCta) s_pair[k] = md.pairs[k];
-  for (int k = tid; k < md.n_pair_groups; k += kCta) s_pcoef[k] = md.pair_coef[k];
-  // k_lz_init / k_lz_fin mode 0 have set sigma_0, c1, c2 and the flags
+  for (int k = tid; k < md.n_entries; k += kClThreads) s_ent[k] = md.entries[k];
+  for (int k = tid; k < md.n_classes; k += kClThreads) s_cls[k] = md.cls_coef[k].x;
+  for (int k = tid; k < md.n_lin; k += kClThreads) s_lin[k] = md.lin[k];
+  for (int k = tid; k < md.n_pairs; k += kClThreads) s_pair[k] = md.pairs[k];
+  for (int k = tid; k < md.n_pair_groups; k += kClThreads) s_pcoef[k] = md.pair_coef[k];
+  // k_lz_init / its finaliser have set sigma_0, c1, c2 and the flags
   double sg = lz.sig[0];
   double c1 = lz.s[0], c2 = lz.s[1];
   int done = *lz.done;
+  bool cur_a = true;  // C is A (else B)
   int k = 0;
+  cl_sync();  // every CTA has staged its slice of C_0
   for (; k < steps && !done; ++k) {
-    __syncthreads();  // C complete
+    double* C = cur_a ? A : B;
+    double* P = cur_a ? B : A;
     double xh = 0.0;
-    for (int64_t r = tid; r < n; r += kCta) {
-      const uint64_t s = md.sector ? sector_state(md.t, (uint64_t)r) : (uint64_t)r;
+    for (int i = tid; i < nloc; i += kClThreads) {
+      const uint64_t s = md.sector ? sector_state(md.t, (uint64_t)(r0 + i)) : (uint64_t)(r0 + i);
       double d = md.c0;
       for (int g = 0; g < md.n_lin; ++g) d += s_lin[g].coef * (double)__popcll(s & s_lin[g].mask);
       for (int q = 0; q < md.n_pairs; ++q) {
         const PairEntry pe = s_pair[q];
         d += s_pcoef[pe.grp] * (double)((s >> pe.i) & (s >> pe.j) & 1ull);
       }
-      const double x = C[r];
+      const double x = C[i];
       double hv = d * x;
       for (int e = 0; e < md.n_entries; ++e) {
         const SpinEntry en = s_ent[e];
@@ -647,22 +678,33 @@ __global__ void __launch_bounds__(kCta, 1) k_lz_cta(const SpinDev md, LzDev lz, 
         if (!code) continue;
         const uint64_t s2 = s ^ en.mask;
         const int64_t r2 = md.sector ? (int64_t)sector_rank(md.t, s2) : (int64_t)s2;
-        const double y = s_cls[en.cls] * C[r2];
+        const unsigned owner = (unsigned)(r2 / R);
+        const double y = s_cls[en.cls] * cl_map(C, owner)[r2 - (int64_t)owner * R];
         hv += code == 1 ? y : -y;  // real models: codes +1 / -1 only
       }
       xh = fma(x, hv, xh);
-      P[r] = c1 * hv - c2 * P[r];
+      P[i] = c1 * hv - c2 * P[i];
     }
-    const double a = cta_sum(xh, s_w) * sg * sg;  // alpha_k = (H v_k, v_k)
+    double t = cl_block_sum(xh, s_w);
+    if (tid == 0) s_part[0] = t;
+    cl_sync();  // P written everywhere (so C is no longer read), partials of alpha ready
+    double xs = 0.0;
+    for (int c = 0; c < ncta; ++c) xs += *cl_map(&s_part[0], (unsigned)c);
+    const double a = xs * sg * sg;  // alpha_k = (H v_k, v_k)
     const double gm = a * sg;
     double pp = 0.0;
-    for (int64_t r = tid; r < n; r += kCta) {
-      const double p = fma(-gm, C[r], P[r]);
-      P[r] = p;
-      pp = fma(p, p, pp);
+    for (int i = tid; i < nloc; i += kClThreads) {
+      const double pv = fma(-gm, C[i], P[i]);
+      P[i] = pv;
+      pp = fma(pv, pv, pp);
     }
-    const double b = sqrt(cta_sum(pp, s_w));
-    if (tid == 0) {
+    t = cl_block_sum(pp, s_w);
+    if (tid == 0) s_part[1] = t;
+    cl_sync();  // the new vector complete everywhere, partials of beta ready
+    double ps = 0.0;
+    for (int c = 0; c < ncta; ++c) ps += *cl_map(&s_part[1], (unsigned)c);
+    const double b = sqrt(ps);
+    if (rank == 0 && tid == 0) {
       lz.alpha[k] = a;
       lz.beta[k] = b;
     }
@@ -673,30 +715,56 @@ __global__ void __launch_bounds__(kCta, 1) k_lz_cta(const SpinDev md, LzDev lz, 
       c1 = sn;
       c2 = b * sg;
       sg = sn;
-      if (tid == 0) lz.sig[k + 1] = sn;
-      double* t = C;
-      C = P;
-      P = t;
+      if (rank == 0 && tid == 0) lz.sig[k + 1] = sn;
+      cur_a = !cur_a;
     }
   }
-  if (tid == 0) {
+  if (rank == 0 && tid == 0) {
     *lz.steps_done = k;
     *lz.done = 1;
   }
-  (void)Cout;
+  cl_sync();  // no CTA leaves while another may still read its shared memory
 }
+
+constexpr int kClCtas = 16;       // CTAs per cluster (non-portable size; 8 if 16 cannot launch)
+constexpr int64_t kClMaxDim = 32768;
 
 }  // namespace
 
-// dynamic shared memory of k_lz_cta: both vectors (its term tables are static, about 22 KB)
-size_t lz_cta_smem(const SpinDev& md) { return 2 * sizeof(double) * (size_t)md.dim; }
+// dynamic shared memory of one cluster CTA, or 0 when the model does not take the path
+size_t lz_cta_smem(const SpinDev& md) {
+  if (md.dim > kClMaxDim) return 0;
+  const int64_t R = (md.dim + kClCtas - 1) / kClCtas;
+  return 2 * sizeof(double) * (size_t)R;
+}
 
 Status launch_lz_cta(const SpinDev& md, const LzDev& lz, int steps, double brk, const double* C0, cudaStream_t st) {
-  const size_t smem = lz_cta_smem(md);
-  HPHI_CUDA_TRY(cudaFuncSetAttribute(k_lz_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_lz_cta<<<1, kCta, smem, st>>>(md, lz, steps, brk, C0, nullptr);
-  HPHI_CUDA_TRY(cudaGetLastError());
-  return {};
+  for (int cs : {kClCtas, 8}) {
+    const int R = (int)((md.dim + cs - 1) / cs);
+    const size_t smem = 2 * sizeof(double) * (size_t)R;
+    HPHI_CUDA_TRY(cudaFuncSetAttribute(k_lz_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (cs > 8) HPHI_CUDA_TRY(cudaFuncSetAttribute(k_lz_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_lz_cl, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    HPHI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_lz_cl, md, lz, steps, brk, C0, R, cs));
+    return {};
+  }
+  return {HPHI_ERR_CUDA, "one-cluster Lanczos: no cluster of 16 or 8 CTAs can be scheduled"};
 }
 
 }  // namespace hphi

@@ -998,8 +998,8 @@ def test_tpq_c64_carried_norm_drift_1000_steps():
 
 def test_lanczos_one_cta_heisenberg_ring12_full():
     """The 12-site ring in its full basis (4096 rows, 64 KB for both vectors) runs the whole
-    100-step recurrence in one CTA: a handful of launches, the oracle's alpha / beta and the
-    ring's ground-state energy."""
+    100-step recurrence in one thread-block cluster (vectors in distributed shared memory): a
+    handful of launches, the oracle's alpha / beta and the ring's ground-state energy."""
     spec = wl.heisenberg_ring(12)
     m = hp.Model.from_spec(spec)
     r = m.lanczos(100, seed=123432, n_eig=2)
