@@ -663,25 +663,63 @@ __global__ void __launch_bounds__(kClThreads, 1) k_lz_cl(const SpinDev md, LzDev
     double xh = 0.0;
     for (int i = tid; i < nloc; i += kClThreads) {
       const uint64_t s = md.sector ? sector_state(md.t, (uint64_t)(r0 + i)) : (uint64_t)(r0 + i);
+      // diagonal: integer bit counts per coefficient group, one multiply-add per group
       double d = md.c0;
       for (int g = 0; g < md.n_lin; ++g) d += s_lin[g].coef * (double)__popcll(s & s_lin[g].mask);
-      for (int q = 0; q < md.n_pairs; ++q) {
-        const PairEntry pe = s_pair[q];
-        d += s_pcoef[pe.grp] * (double)((s >> pe.i) & (s >> pe.j) & 1ull);
+      if (md.n_pairs) {
+        int grp = s_pair[0].grp, cnt = 0;
+        for (int q = 0; q < md.n_pairs; ++q) {
+          const PairEntry pe = s_pair[q];
+          if (pe.grp != grp) {
+            d += s_pcoef[grp] * (double)cnt;
+            cnt = 0;
+            grp = pe.grp;
+          }
+          cnt += (int)((s >> pe.i) & (s >> pe.j) & 1ull);
+        }
+        d += s_pcoef[grp] * (double)cnt;
       }
       const double x = C[i];
       double hv = d * x;
-      for (int e = 0; e < md.n_entries; ++e) {
-        const SpinEntry en = s_ent[e];
-        const int sel = (int)((s >> en.i) & 1ull) | ((int)((s >> en.j) & 1ull) << 1);
-        const int code = (en.phases >> (3 * sel)) & 7;
-        if (!code) continue;
-        const uint64_t s2 = s ^ en.mask;
-        const int64_t r2 = md.sector ? (int64_t)sector_rank(md.t, s2) : (int64_t)s2;
-        const unsigned owner = (unsigned)(r2 / R);
-        const double y = s_cls[en.cls] * cl_map(C, owner)[r2 - (int64_t)owner * R];
-        hv += code == 1 ? y : -y;  // real models: codes +1 / -1 only
+      // exchange: signed sums per coefficient class (entries are sorted by class), gathers in
+      // batches of eight so their distributed-shared-memory loads overlap
+      double acc = 0.0;
+      int cur = md.n_entries ? s_ent[0].cls : 0;
+      for (int e0 = 0; e0 < md.n_entries; e0 += 8) {
+        double y[8];
+        int sg8[8], cl8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          y[j] = 0.0;
+          sg8[j] = 0;
+          cl8[j] = cur;
+          const int e = e0 + j;
+          if (e < md.n_entries) {
+            const SpinEntry en = s_ent[e];
+            cl8[j] = en.cls;
+            const int sel = (int)((s >> en.i) & 1ull) | ((int)((s >> en.j) & 1ull) << 1);
+            const int code = (en.phases >> (3 * sel)) & 7;
+            if (code) {
+              const uint64_t s2 = s ^ en.mask;
+              const int64_t r2 = md.sector ? (int64_t)sector_rank(md.t, s2) : (int64_t)s2;
+              const unsigned owner = (unsigned)(r2 / R);
+              y[j] = cl_map(C, owner)[r2 - (int64_t)owner * R];
+              sg8[j] = code == 1 ? 1 : -1;  // real models: codes +1 / -1 only
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (cl8[j] != cur) {
+            hv = fma(s_cls[cur], acc, hv);
+            acc = 0.0;
+            cur = cl8[j];
+          }
+          if (sg8[j] > 0) acc += y[j];
+          else if (sg8[j] < 0) acc -= y[j];
+        }
       }
+      if (md.n_entries) hv = fma(s_cls[cur], acc, hv);
       xh = fma(x, hv, xh);
       P[i] = c1 * hv - c2 * P[i];
     }

@@ -922,7 +922,7 @@ def test_tpq_doublon_vs_canonical_8site_hubbard():
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_lanczos_convergence_test_appendix_c(prec):
     """The device stops where appendix C's rule, applied to its own alpha / beta with LAPACK,
-    says it should, and the steps it ran are the steps of a run without the test."""
+    says it should, and the steps it ran are those of a run without the test."""
     spec = wl.heisenberg_ring(16).with_basis(wl.BASIS_SZ, 8)
     m = hp.Model.from_spec(spec)
     p = hp.FP64 if prec == "fp64" else hp.FP32
@@ -935,10 +935,13 @@ def test_lanczos_convergence_test_appendix_c(prec):
         e_n = oracle.ritz_values(r["alpha"][:n], r["beta"][:n])[1]
         e_p = oracle.ritz_values(r["alpha"][:n - 2], r["beta"][:n - 2])[1]
         assert abs(abs(e_n - e_p) / (eps * abs(e_n)) - 1.0) < 1e-3, (n, want)
+    # the same steps without the test (for this size in FP64 another kernel: the one-cluster
+    # recurrence, so agreement to rounding rather than bit for bit)
     full = m.lanczos(n, prec=p, seed=9, n_eig=2)
     assert not full["converged"] and full["steps"] == n
-    assert np.array_equal(full["alpha"], r["alpha"]) and np.array_equal(full["beta"], r["beta"])
-    assert np.array_equal(full["eig"], r["eig"])
+    tol = 1e-11 if prec == "fp64" else 0.0
+    assert _rel(full["alpha"], r["alpha"]) <= tol and _rel(full["beta"], r["beta"]) <= tol
+    assert _rel(full["eig"], r["eig"]) <= tol
     if prec == "fp64":
         a, _ = oracle.lanczos(spec, oracle.random_at(9, np.arange(m.dim, dtype=np.uint64), False), n)
         assert _rel(r["alpha"][:12], a[:12]) < 1e-11
