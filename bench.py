@@ -43,7 +43,10 @@ FALLBACK_HBM_GBS = 6800.0
 MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): (10_560_000_000, "ncu capture of the 4x4 Hubbard sector, "
                                                                    "quantise + pass D + pass U of one step"),
                     ("heisenberg_6x5_sz15", "fp64"): (12_814_000_000, "ncu capture of this sector, k_quant + "
-                                                      "k_sec_hi + k_sec_lo at split (15, 2), one step")}
+                                                      "k_sec_hi + k_sec_lo at split (15, 2), one step"),
+                    ("heisenberg_6x6_sz0", "fp64"): (999_900_000_000, "ncu capture at full size (1-pass DRAM "
+                                                     "counters): k_sec_hi + k_sec_lo of one step after the "
+                                                     "first, split (15, 2), 1 KB pass-H stripes")}
 # fp64 FMA throughput of this machine's GB300 from a throughput probe (thread-level T op/s); the
 # chip issues fp64 at 1/64 of its fp32 rate
 FP64_PEAK_TOPS = 0.50

@@ -165,6 +165,8 @@ typedef struct {
   float worst_ms;      /* H v time of the slowest candidate                                     */
   int best_split_L;    /* split-row spin path: chosen low-part length L (0: path not tuned)      */
   int best_split_K;    /* split-row spin path: chosen rows per shared-memory tile                */
+  int best_split_hi_cols; /* split-row spin path: chosen high-pass columns per lane (4 or 2 int64,
+                          8 or 4 fp32)                                                          */
 } hphi_tune_result;
 
 /* Times the launch configurations of the model's H v at precision prec (HPHI_FP64 or
@@ -173,7 +175,7 @@ typedef struct {
  * columns per thread of the down-spin pass x rows per tile of the up-spin pass.  Real spin
  * models in an S^z sector that take the split-row path (see hphi_set_sector_split) are tuned
  * over the split: the default low part and up to two bits fewer, each with every tile height
- * that fits.  A real spin model in its full basis has every S^z sector of at least 2^20 rows
+ * that fits, and then over the high pass's columns per lane on the chosen split.  A real spin model in its full basis has every S^z sector of at least 2^20 rows
  * tuned that way: hphi_lanczos_run_sectors keeps those sectors' shapes; the result then
  * counts the candidates of all of them and reports the timings of the largest.  Other models
  * report n_candidates = 0.  Uses the model's workspace (and the sectors' own); synchronises

@@ -67,7 +67,7 @@ class InvitResult(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int), ("best_dn_ept", ctypes.c_int), ("best_up_k", ctypes.c_int),
                 ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float), ("worst_ms", ctypes.c_float),
-                ("best_split_L", ctypes.c_int), ("best_split_K", ctypes.c_int)]
+                ("best_split_L", ctypes.c_int), ("best_split_K", ctypes.c_int), ("best_split_hi_cols", ctypes.c_int)]
 
 
 class TpqParams(ctypes.Structure):
@@ -277,7 +277,8 @@ class Model:
         r = TuneResult()
         self._check(self._L.hphi_autotune(self._h, prec, ctypes.byref(r), _stream()))
         return dict(n_candidates=r.n_candidates, dn_ept=r.best_dn_ept, up_k=r.best_up_k, best_ms=r.best_ms,
-                    default_ms=r.default_ms, worst_ms=r.worst_ms, split_L=r.best_split_L, split_K=r.best_split_K)
+                    default_ms=r.default_ms, worst_ms=r.worst_ms, split_L=r.best_split_L, split_K=r.best_split_K,
+                    split_hi_cols=r.best_split_hi_cols)
 
     def set_sector_split(self, prec=FP64, L: int = 0, K: int = 0):
         """Split-row spin path (see hphi_set_sector_split): L = -1 off, 0 default, else the low

@@ -138,6 +138,7 @@ struct hphi_model {
   bool sec_ok[2] = {false, false};
   std::string sec_why;
   int sec_L[2] = {0, 0}, sec_K[2] = {0, 0};
+  int sec_hi_cols[2] = {0, 0};  // pass H columns per lane per precision (0: built-in)
   std::map<std::pair<int, int>, std::unique_ptr<hphi::SecTables, hphi::SecTablesDeleter>> sec_tab;
 };
 
@@ -758,8 +759,11 @@ hphi::Status hv_launch(hphi_model* m, int prec, const void* v, void* w, int nvec
                        const hphi::FusedArgs& fa, int grid, void* scratch, cudaStream_t st) {
   if (use_hub_fast(m, prec, nvec, epi) && (hphi::hub_scratch_bytes(m->hdev, prec, epi) == 0 || scratch != nullptr))
     return hphi::launch_hub_fast(m->hdev, prec, v, w, scratch, epi, fa, grid, st);
-  if (scratch != nullptr && scratch == m->ws.work.p && sec_runs(m, prec, nvec, epi, m->ws.work.bytes))
-    return hphi::launch_sec(*use_sec(m, prec, nvec, epi), prec, v, w, scratch, epi, fa, grid, st);
+  if (scratch != nullptr && scratch == m->ws.work.p && sec_runs(m, prec, nvec, epi, m->ws.work.bytes)) {
+    hphi::SecDev dd = *use_sec(m, prec, nvec, epi);
+    dd.hi_cols = m->sec_hi_cols[prec == HPHI_FP64 ? 0 : 1];
+    return hphi::launch_sec(dd, prec, v, w, scratch, epi, fa, grid, st);
+  }
   if (use_batch(m, nvec) && hphi::batch_aligned(v, w)) {
     const hphi::BatchPlan* plan = epi == hphi::Epi::kLanczos1 ? nullptr : batch_plan(m, prec, nvec);
     if (scratch != nullptr || hphi::batch_scratch_bytes(m->sdev, plan, prec, m->cplx_model, nvec) == 0)
@@ -806,6 +810,7 @@ hphi::Status sec_autotune(hphi_model* m, int prec, hphi_tune_result* res, cudaSt
   HPHI_CUDA_TRY(cudaEventCreate(&tm.a));
   HPHI_CUDA_TRY(cudaEventCreate(&tm.b));
   const std::pair<int, int> dflt = sec_shape(m, prec);
+  m->sec_hi_cols[pi] = 0;  // the shapes are compared at the built-in pass-H columns
   float best = 1e30f, worst = 0.f, dms = 0.f;
   std::pair<int, int> best_sh = dflt;
   hphi::FusedArgs fa;
@@ -853,6 +858,41 @@ hphi::Status sec_autotune(hphi_model* m, int prec, hphi_tune_result* res, cudaSt
   }
   m->sec_L[pi] = best_sh.first;
   m->sec_K[pi] = best_sh.second;
+  // pass H at half the columns per lane on the chosen shape (narrower stripes keep a large
+  // class's stripe nearer L2's size, at more instructions per output)
+  {
+    const int full = prec == HPHI_FP64 ? 4 : 8;
+    const int saved_cols = m->sec_hi_cols[pi];
+    float ms_half = 1e30f;
+    if ((s = sec_ensure(m, prec, st)).code == 0 &&
+        (s = m->ws.work.ensure(hv_scratch_bytes(m, prec, 1, hphi::Epi::kStore))).code == 0) {
+      const int grid = hv_grid_for(m, 1, prec, hphi::Epi::kStore);
+      m->sec_hi_cols[pi] = full / 2;
+      s = hv_launch(m, prec, m->ws.vecA.p, m->ws.vecB.p, 1, hphi::Epi::kStore, fa, grid, m->ws.work.p, st);
+      if (!s.code) HPHI_CUDA_TRY(cudaEventRecord(tm.a, st));
+      for (int rep = 0; rep < 2 && !s.code; ++rep)
+        s = hv_launch(m, prec, m->ws.vecA.p, m->ws.vecB.p, 1, hphi::Epi::kStore, fa, grid, m->ws.work.p, st);
+      if (!s.code) {
+        HPHI_CUDA_TRY(cudaEventRecord(tm.b, st));
+        HPHI_CUDA_TRY(cudaEventSynchronize(tm.b));
+        HPHI_CUDA_TRY(cudaEventElapsedTime(&ms_half, tm.a, tm.b));
+        ms_half /= 2.f;
+        ++res->n_candidates;
+        worst = std::max(worst, ms_half);
+      }
+    }
+    if (s.code) {
+      m->sec_hi_cols[pi] = saved_cols;
+      return s;
+    }
+    if (ms_half < best) {
+      best = ms_half;
+      m->sec_hi_cols[pi] = full / 2;
+    } else {
+      m->sec_hi_cols[pi] = 0;
+    }
+    res->best_split_hi_cols = m->sec_hi_cols[pi] ? full / 2 : full;
+  }
   res->best_split_L = best_sh.first;
   res->best_split_K = best_sh.second;
   res->best_ms = best;
@@ -1074,6 +1114,7 @@ int hphi_set_sector_split(hphi_model* m, int prec, int L, int K, void* stream) {
   const int oldL = m->sec_L[pi], oldK = m->sec_K[pi];
   m->sec_L[pi] = L;
   m->sec_K[pi] = L < 0 ? 0 : K;
+  m->sec_hi_cols[pi] = 0;
   if (L >= 0) {
     const int esz = prec == HPHI_FP64 ? 8 : 4;
     const std::pair<int, int> sh = sec_shape(m, prec);

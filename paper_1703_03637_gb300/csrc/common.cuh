@@ -135,6 +135,7 @@ struct SecDev {
   int L, H, n_ones;
   int64_t dim;
   int K;                        // rows per tile of the row pass
+  int hi_cols;                  // pass H columns per lane (0: the built-in 4 for int64, 8 for fp32)
   int nq_max;                   // longest row present
   // coefficients: exchange class c has coef[c]; the fp64 path sums integer multiples
   // mult[c] of one unit (coef[c] = mult[c] * unit) and scales once

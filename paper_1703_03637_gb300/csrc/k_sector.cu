@@ -1104,9 +1104,16 @@ Status launch_hi(const SecDev& d, const T* X, T* W, const int* done, unsigned lo
   // neighbour's overhead over more columns: on the 6x6 sector 256-byte stripes measured 185 ms,
   // 512-byte 124 ms, and 1 KB about 2.5 % less again, although one stripe of the largest class
   // (360 MB) then far exceeds L2.
+  // The autotuner may halve them (d.hi_cols): on the 6x6 sector a 1 KB stripe of the largest
+  // class is 360 MB, so the partner reads partly come from DRAM.
   constexpr int EPT = sizeof(T) == 8 ? 4 : 8;
-  if (one) k_sec_hi<T, EPT, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
-  else k_sec_hi<T, EPT, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+  if (d.hi_cols == EPT / 2) {
+    if (one) k_sec_hi<T, EPT / 2, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+    else k_sec_hi<T, EPT / 2, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+  } else {
+    if (one) k_sec_hi<T, EPT, true><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+    else k_sec_hi<T, EPT, false><<<grid, kThreads, 0, st>>>(d, X, W, done, counter);
+  }
   HPHI_CUDA_TRY(cudaGetLastError());
   return {};
 }
