@@ -400,9 +400,13 @@ def assemble_lanczos_line(args, world, spec, D, steps, prec, esz, value, ms_step
     hv_avg_ms = t["hv_avg_ms"]
     achieved = D * bytes_row / (hv_avg_ms / 1e3) / 1e9
     traffic = MEASURED_TRAFFIC.get((args.workload, args.prec))
+    note = "no ncu capture of this kernel version"
+    cols = ((tune or {}).get(args.prec) or {}).get("split_hi_cols")
+    if traffic and args.workload == "heisenberg_6x6_sz0" and cols not in (None, 0, 4):
+        traffic, note = None, f"captured at 4 pass-H columns per lane; this run uses {cols}"
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic[0] if traffic else None,
-            "traffic_source": traffic[1] if traffic else "no ncu capture of this kernel version",
+            "traffic_source": traffic[1] if traffic else note,
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
             "kernel": hv_group_kernels(spec, hp_model_stub(spec), prec), "kernel_avg_ms": round(hv_avg_ms, 4),
             "algorithmic_bytes_per_launch": D * bytes_row}
