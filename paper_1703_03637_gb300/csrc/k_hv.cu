@@ -617,6 +617,19 @@ __device__ __forceinline__ T* cl_map(T* p, unsigned rank) {
   return reinterpret_cast<T*>(out);
 }
 
+// sum over the cluster's CTAs of one shared double: lane c of every warp loads CTA c's value
+// (one round trip of distributed shared memory for all of them) and the warp adds them in a
+// fixed tree order, so every thread of every CTA gets the same bits
+__device__ __forceinline__ double cl_gather_sum(double* p, int ncta) {
+  const int lane = threadIdx.x & 31;
+  double v = lane < ncta ? *cl_map(p, (unsigned)lane) : 0.0;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  // lanes may hold differently rounded sums; lane 0's is the same in every warp of every CTA,
+  // and the loop's exit test must see one value everywhere
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
 __device__ __forceinline__ unsigned cl_rank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -726,8 +739,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_lz_cl(const SpinDev md, LzDev
     double t = cl_block_sum(xh, s_w);
     if (tid == 0) s_part[0] = t;
     cl_sync();  // P written everywhere (so C is no longer read), partials of alpha ready
-    double xs = 0.0;
-    for (int c = 0; c < ncta; ++c) xs += *cl_map(&s_part[0], (unsigned)c);
+    const double xs = cl_gather_sum(&s_part[0], ncta);
     const double a = xs * sg * sg;  // alpha_k = (H v_k, v_k)
     const double gm = a * sg;
     double pp = 0.0;
@@ -739,8 +751,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_lz_cl(const SpinDev md, LzDev
     t = cl_block_sum(pp, s_w);
     if (tid == 0) s_part[1] = t;
     cl_sync();  // the new vector complete everywhere, partials of beta ready
-    double ps = 0.0;
-    for (int c = 0; c < ncta; ++c) ps += *cl_map(&s_part[1], (unsigned)c);
+    const double ps = cl_gather_sum(&s_part[1], ncta);
     const double b = sqrt(ps);
     if (rank == 0 && tid == 0) {
       lz.alpha[k] = a;
