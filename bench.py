@@ -40,11 +40,7 @@ METRIC = "H·v Gelem/s & %HBM peak; Lanczos/mTPQ steps/s, FP64 vs mixed+batched 
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per fused H v launch group from an ncu capture of the current
 # kernels, with where they come from; absent where no capture of the current kernels exists
-MEASURED_TRAFFIC = {("hubbard_4x4_8u8d", "fp64"): (10_560_000_000, "ncu capture of the 4x4 Hubbard sector, "
-                                                                   "quantise + pass D + pass U of one step"),
-                    ("heisenberg_6x5_sz15", "fp64"): (12_814_000_000, "ncu capture of this sector, k_quant + "
-                                                      "k_sec_hi + k_sec_lo at split (15, 2), one step"),
-                    ("heisenberg_6x6_sz0", "fp64"): (999_900_000_000, "ncu capture at full size (1-pass DRAM "
+MEASURED_TRAFFIC = {("heisenberg_6x6_sz0", "fp64"): (999_900_000_000, "ncu capture at full size (1-pass DRAM "
                                                      "counters): k_sec_hi + k_sec_lo of one step after the "
                                                      "first, split (15, 2), 1 KB pass-H stripes")}
 # fp64 FMA throughput of this machine's GB300 from a throughput probe (thread-level T op/s); the
@@ -388,8 +384,13 @@ def hv_group_kernels(spec, m, prec):
     """The kernels of one fused Lanczos pass-1 launch group, as the library picks them."""
     import paper_1703_03637_gb300 as hp
     if spec.kind == wl.SPIN and spec.basis == wl.BASIS_SZ and not m.is_complex:
-        ks = "k_quant + k_sec_hi + k_sec_lo" if prec == hp.FP64 else "k_sec_hi + k_sec_lo"
-        return ks + " (split-row H v fused with Lanczos pass 1; k_maxexp in the first step only)"
+        if prec == hp.FP64:
+            return ("k_sec_hi + k_sec_lo (split-row H v fused with Lanczos pass 1, on the int64 copy that the "
+                    "previous pass 2 wrote; k_maxexp + k_quant in the first step only)")
+        return "k_sec_hi + k_sec_lo (split-row H v fused with Lanczos pass 1)"
+    if spec.kind == wl.HUBBARD and not m.is_complex and prec == hp.FP64:
+        return ("k_hub_dn + k_hub_up_q (two-pass H v fused with Lanczos pass 1, on the int64 copy that the "
+                "previous pass 2 wrote; k_maxexp + k_quant in the first step only)")
     return hv_group_name(spec, m, prec, 1, "Lanczos pass 1")
 
 
@@ -471,7 +472,7 @@ def run_hubbard_sub(args, world, local, rank):
             "lanczos_steps_per_s": round(W["steps"] / (ms_step / 1e3), 2), "e0": t["res"]["eig"][0],
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "traffic": traffic[0] if traffic else None,
-                         "kernel": "k_quant + k_hub_dn + k_hub_up_q (Lanczos pass 1)",
+                         "kernel": "k_hub_dn + k_hub_up_q (Lanczos pass 1; k_maxexp + k_quant in the first step only)",
                          "kernel_avg_ms": round(t["hv_avg_ms"], 4), "algorithmic_bytes_per_launch": D * 24},
             "autotune": tune, "gpu_launches": t["launches"], "clocks": t["clocks"]}
 
