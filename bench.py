@@ -427,7 +427,7 @@ def assemble_lanczos_line(args, world, spec, D, steps, prec, esz, value, ms_step
         "config": {"workload": args.workload, "dim": D, "lanczos_steps_per_bench_step": steps,
                    "workload_lanczos_steps": wl.workload(args.workload)["steps"], "model": spec.name,
                    "sector": {0: "full", 1: f"S^z: n_up={spec.n_a}", 2: f"N_up={spec.n_a}, N_dn={spec.n_b}"}[spec.basis],
-                   "start": "philox uniform [-1, 1), seed 123432+rank, generated inside each bench step",
+                   "start": "philox gaussian, seed 123432+rank, generated inside each bench step",
                    "l2": l2_note(D * esz), "parallelism": f"replicas{world}"},
         "lanczos_steps_per_s": round(steps / (ms_step / 1e3), 3),
         "e0": t["res"]["eig"][0], "roofline": roof, "e2e": e2e, "gpu_launches": t["launches"], "clocks": t["clocks"],
@@ -547,7 +547,7 @@ def run_tpq(args, world, rank, local):
         "vs_baseline": None, "dtype": ("c128" if prec == hp.FP64 else "c64+f64acc") if m.is_complex else
         ("f64" if prec == hp.FP64 else "f32+f64acc"), "data": "synthetic",
         "config": {"workload": args.workload, "dim": D, "n_starts": nv, "tpq_steps_per_run": K, "l": W["l"],
-                   "model": spec.name, "start": "philox uniform [-1, 1), seed 123432+1000*rank",
+                   "model": spec.name, "start": "philox gaussian, seed 123432+1000*rank",
                    "l2": l2_note(D * nv * esz), "parallelism": f"replicas{world}"},
         "tpq_steps_per_s": round(K * args.steps / (ms / 1e3), 3),
         "u_last_mean": float(np.mean(res["u"][-1])), "roofline": roof, "e2e": e2e, "gpu_launches": launches,
@@ -622,7 +622,7 @@ def run_sectors(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == hp.FP64 else "f32+f64acc+f64 refine", "data": "synthetic",
         "config": {"workload": args.workload, "dim_total": sum(dims), "sectors": len(sectors), "lanczos_steps": steps,
-                   "model": spec.name, "start": "philox uniform [-1, 1), seed 123432+rank",
+                   "model": spec.name, "start": "philox gaussian, seed 123432+rank",
                    "l2": l2_note(max(dims) * (8 if prec == hp.FP64 else 4)), "parallelism": f"replicas{world}"},
         "e0_min": min(e), "roofline": roof, "gpu_launches": launches, "clocks": clocks, "autotune": tune,
     }

@@ -218,15 +218,18 @@ int hphi_set_window_bits(hphi_model* m, int bits);
 
 /* ---------------------------------------------------------------- start vectors */
 
-/* Fills v (device, [dim][nvec], precision prec) with uniform random numbers in [-1, 1) from
- * the counter-based generator Philox4x32-10 (Salmon et al., SC'11): element e = r * nvec + c
- * uses counter (e mod 2^32, e >> 32, 0, 0) and key (seed mod 2^32, seed >> 32); output words
- * w0, w1 give the 53-bit integer m_a = ((w0 << 32) | w1) >> 11 and the real part
- * (m_a - 2^52) 2^-52, words w2, w3 the imaginary part (complex models) likewise.  prec =
- * HPHI_FP64 holds these values exactly; HPHI_FP32 holds their round-to-nearest fp32 values.
- * Appendix A.2 / A.4 draw every coefficient of the initial vector from a random number
- * generator (dSFMT, whose stream depends on the process count); this generator depends on
- * the seed and the element index only. */
+/* Fills v (device, [dim][nvec], precision prec) with standard-normal numbers (a seeded
+ * Gaussian start vector) from the counter-based generator Philox4x32-10 (Salmon et al.,
+ * SC'11) and the Box-Muller transform: Philox block p uses counter (p mod 2^32, p >> 32, 0, 0)
+ * and key (seed mod 2^32, seed >> 32); its words w0, w1 give the 53-bit uniform
+ * u_a = ((((w0 << 32) | w1) >> 11) + 0.5) / 2^53 and w2, w3 likewise u_b, and the block's pair
+ * is g0 = sqrt(-2 ln u_a) cos(2 pi u_b), g1 = sqrt(-2 ln u_a) sin(2 pi u_b).  The elements
+ * e = r * nvec + c of a complex vector are g0 + i g1 of block e; those of a real vector are g0
+ * (e even) and g1 (e odd) of block e / 2.  prec = HPHI_FP64 evaluates the transform in fp64;
+ * HPHI_FP32 rounds the same uniforms to fp32 and evaluates it in fp32 arithmetic (values
+ * within a few fp32 ulps of the fp64 numbers).  Appendix A.2 / A.4 draw every coefficient of
+ * the initial vector from dSFMT, whose stream depends on the process count; this generator
+ * depends on the seed and the element index only. */
 int hphi_random_vector(hphi_model* m, void* v, int nvec, int prec, uint64_t seed, void* stream);
 
 /* Raw Philox4x32-10 on the device: for k < n, out[4k..4k+3] = Philox(ctr[4k..4k+3],

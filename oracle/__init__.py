@@ -65,7 +65,7 @@ def lib():
             L.or_apply_H.argtypes = [P, P, P, i32]
             L.or_apply_H_slice.argtypes = [P, P, P, i32, u64, u64]
             L.or_philox4x32_10.argtypes = [P, P, P]
-            L.or_uniform_pair.argtypes = [u64, u64, P]
+            L.or_gauss_pair.argtypes = [u64, u64, P]
             L.or_random_at.argtypes = [u64, P, i64, i32, P]
             L.or_apply_H_rows_philox.argtypes = [P, P, i64, u64, i32, i32, i32, P]
             L.or_lanczos.argtypes = [P, P, i32, f64, P, P]
@@ -204,7 +204,9 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def random_at(seed: int, idx, complex_: bool) -> np.ndarray:
-    """Elements idx of the Philox start vector of `seed` (uniform in [-1, 1), appendix A.2 / A.4)."""
+    """Elements idx of the Philox Gaussian start vector of `seed` (appendix A.2 / A.4's random
+    coefficients): complex element e is the Box-Muller pair of Philox block e, real elements
+    2p and 2p + 1 are the two numbers of block p."""
     idx = np.ascontiguousarray(idx, dtype=np.uint64)
     out = np.zeros(len(idx), dtype=np.complex128)
     lib().or_random_at(seed, _ptr(idx), len(idx), int(complex_), _ptr(out))

@@ -335,19 +335,36 @@ void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t 
   out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
 }
 
-// Start-vector numbers of element e of stream `seed` (appendix A.2 / A.4: random
-// coefficients): two uniform numbers in [-1, 1), each (m - 2^52) / 2^52 for a 53-bit integer
-// m taken from two Philox output words (real part: words 0, 1; imaginary part: words 2, 3).
-void uniform_pair(uint64_t seed, uint64_t e, double* u0, double* u1) {
-  const uint32_t ctr[4] = {(uint32_t)e, (uint32_t)(e >> 32), 0u, 0u};
+// Standard-normal pair of Philox block p of stream `seed` (Box & Muller 1958 on two 53-bit
+// uniforms in the open interval (0, 1)).
+void gauss_pair(uint64_t seed, uint64_t p, double* g0, double* g1) {
+  const uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), 0u, 0u};
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t x[4];
   philox4x32_10(ctr, key, x);
-  const int64_t ma = (int64_t)((((uint64_t)x[0] << 32) | x[1]) >> 11);
-  const int64_t mb = (int64_t)((((uint64_t)x[2] << 32) | x[3]) >> 11);
-  const double two52 = 4503599627370496.0;
-  *u0 = (double)(ma - (int64_t)4503599627370496) / two52;
-  *u1 = (double)(mb - (int64_t)4503599627370496) / two52;
+  const uint64_t a = (((uint64_t)x[0] << 32) | x[1]) >> 11;
+  const uint64_t b = (((uint64_t)x[2] << 32) | x[3]) >> 11;
+  const double ua = ((double)a + 0.5) * (1.0 / 9007199254740992.0);
+  const double ub = ((double)b + 0.5) * (1.0 / 9007199254740992.0);
+  const double rad = std::sqrt(-2.0 * std::log(ua));
+  const double ang = 2.0 * M_PI * ub;
+  *g0 = rad * std::cos(ang);
+  *g1 = rad * std::sin(ang);
+}
+
+// Element e of the start vector of `seed`: complex, g0 + i g1 of block e; real, g0 or g1
+// (e even / odd) of block e / 2.
+void start_element(uint64_t seed, uint64_t e, bool is_complex, double* re, double* im) {
+  double g0, g1;
+  if (is_complex) {
+    gauss_pair(seed, e, &g0, &g1);
+    *re = g0;
+    *im = g1;
+  } else {
+    gauss_pair(seed, e / 2, &g0, &g1);
+    *re = (e & 1) ? g1 : g0;
+    *im = 0.0;
+  }
 }
 
 }  // namespace
@@ -425,17 +442,11 @@ int or_apply_H_slice(const or_model* m, const double* v_ri, double* w_ri, int nv
 // ----------------------------------------------------------------- Philox start vectors
 void or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
 
-void or_uniform_pair(uint64_t seed, uint64_t e, double* g) { uniform_pair(seed, e, &g[0], &g[1]); }
+void or_gauss_pair(uint64_t seed, uint64_t p, double* g) { gauss_pair(seed, p, &g[0], &g[1]); }
 
-// Element values of a Philox start vector at arbitrary indices: real vectors take the first
-// number of each pair, complex ones both.  Output complex128 [n].
+// Element values of the Philox start vector at arbitrary indices.  Output complex128 [n].
 void or_random_at(uint64_t seed, const uint64_t* idx, int64_t n, int is_complex, double* out_ri) {
-  for (int64_t k = 0; k < n; ++k) {
-    double g0, g1;
-    uniform_pair(seed, idx[k], &g0, &g1);
-    out_ri[2 * k] = g0;
-    out_ri[2 * k + 1] = is_complex ? g1 : 0.0;
-  }
+  for (int64_t k = 0; k < n; ++k) start_element(seed, idx[k], is_complex != 0, &out_ri[2 * k], &out_ri[2 * k + 1]);
 }
 
 // Sampled rows of H v where v is the (unnormalised) Philox start vector of `seed`:
@@ -453,8 +464,8 @@ int or_apply_H_rows_philox(const or_model* m, const uint64_t* rows, int64_t nrow
     cplx acc = 0.0;
     auto f = [&](uint64_t col, cplx el) {
       double g0, g1;
-      uniform_pair(seed, col * (uint64_t)nvec + (uint64_t)c, &g0, &g1);
-      acc += el * cplx(g0, is_complex ? g1 : 0.0);
+      start_element(seed, col * (uint64_t)nvec + (uint64_t)c, is_complex != 0, &g0, &g1);
+      acc += el * cplx(g0, g1);
     };
     const bool ok = B.kind == 0 ? spin_row_elems(m, B, rows[k], f) : hub_row_elems(m, B, rows[k], f);
     out_ri[2 * k] = acc.real();

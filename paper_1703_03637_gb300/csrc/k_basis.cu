@@ -139,34 +139,54 @@ __global__ void k_philox_raw(const uint32_t* __restrict__ ctr, const uint32_t* _
   }
 }
 
-// Uniform numbers in [-1, 1) (appendix A.2 / A.4: every coefficient of the initial vector
-// is a random number).  Element e takes the Philox block of counter (e mod 2^32, e >> 32, 0, 0);
-// each pair of output words gives a 53-bit integer m, and t = m - 2^52 in [-2^52, 2^52) is the
-// value in units of 2^-52: the real part from words 0-1, the imaginary part from words 2-3.
-// fp64 holds t 2^-52 exactly; fp32 holds its round-to-nearest (the int64 -> fp32 conversion
-// rounds once, the power-of-two scale is exact), so an fp32 start vector is the fp32 rounding
-// of the fp64 one.  Two conversions and two multiplies per number: no transcendental work.
+// Standard-normal numbers (a seeded Gaussian start vector; appendix A.2 / A.4 draw every
+// coefficient from a random number generator).  Philox block p (counter (p mod 2^32, p >> 32,
+// 0, 0)) gives two 53-bit open-interval uniforms and, by Box-Muller, the pair
+// g0 = sqrt(-2 ln u_a) cos(2 pi u_b), g1 = sqrt(-2 ln u_a) sin(2 pi u_b).  A complex element e
+// is g0 + i g1 of block e; real elements 2p and 2p + 1 are g0 and g1 of block p, so no half
+// of a pair is wasted (GB300 runs the fp64 logarithm and sine / cosine at 1/64 of its fp32
+// rate).  One thread per block.
 template <bool CPLX, bool F64>
 __global__ void k_random(void* __restrict__ v, int64_t n_elem, uint64_t seed) {
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 o = philox(make_uint4((uint32_t)e, (uint32_t)((uint64_t)e >> 32), 0u, 0u), key);
-    const long long ta = (long long)(((((uint64_t)o.x) << 32) | o.y) >> 11) - (1ll << 52);
+  const int64_t n_blk = CPLX ? n_elem : (n_elem + 1) / 2;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_blk; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 o = philox(make_uint4((uint32_t)p, (uint32_t)((uint64_t)p >> 32), 0u, 0u), key);
+    const uint64_t a = ((((uint64_t)o.x) << 32) | o.y) >> 11;
+    const uint64_t b = ((((uint64_t)o.z) << 32) | o.w) >> 11;
     if (F64) {
-      const double xa = __ll2double_rn(ta) * 0x1p-52;
+      const double ua = ((double)a + 0.5) * (1.0 / 9007199254740992.0);
+      const double ub = ((double)b + 0.5) * (1.0 / 9007199254740992.0);
+      const double rad = sqrt(-2.0 * log(ua));
+      double sn, cs;
+      sincospi(2.0 * ub, &sn, &cs);
+      const double g0 = rad * cs, g1 = rad * sn;
       if (CPLX) {
-        const long long tb = (long long)(((((uint64_t)o.z) << 32) | o.w) >> 11) - (1ll << 52);
-        reinterpret_cast<double2*>(v)[e] = make_double2(xa, __ll2double_rn(tb) * 0x1p-52);
+        reinterpret_cast<double2*>(v)[p] = make_double2(g0, g1);
       } else {
-        reinterpret_cast<double*>(v)[e] = xa;
+        double* x = reinterpret_cast<double*>(v);
+        x[2 * p] = g0;
+        if (2 * p + 1 < n_elem) x[2 * p + 1] = g1;
       }
     } else {
-      const float xa = __ll2float_rn(ta) * 0x1p-52f;
+      // fp32 storage: the same two uniforms, rounded to fp32 (relative error 2^-24, also in
+      // the tail near 0), through the transform in fp32 arithmetic; the result is rounded to
+      // fp32 anyway.  ln u_a: logf of u_a below 1/2; above, log1pf(-(1 - u_a)) with 1 - u_a
+      // formed from the integer complement (2^53 - 1 - a + 0.5) / 2^53, so u_a near 1 keeps
+      // full relative accuracy
+      const float two53 = 1.0f / 9007199254740992.0f, half53 = 1.0f / 18014398509481984.0f;
+      const float ua = fmaf(__ull2float_rn(a), two53, half53);
+      const float la = (a < (1ull << 52)) ? logf(ua) : log1pf(-fmaf(__ull2float_rn((1ull << 53) - 1ull - a), two53, half53));
+      const float ub = fmaf(__ull2float_rn(b), two53, half53);
+      const float rad = sqrtf(-2.0f * la);
+      float sn, cs;
+      sincospif(2.0f * ub, &sn, &cs);
       if (CPLX) {
-        const long long tb = (long long)(((((uint64_t)o.z) << 32) | o.w) >> 11) - (1ll << 52);
-        reinterpret_cast<float2*>(v)[e] = make_float2(xa, __ll2float_rn(tb) * 0x1p-52f);
+        reinterpret_cast<float2*>(v)[p] = make_float2(rad * cs, rad * sn);
       } else {
-        reinterpret_cast<float*>(v)[e] = xa;
+        float* x = reinterpret_cast<float*>(v);
+        x[2 * p] = rad * cs;
+        if (2 * p + 1 < n_elem) x[2 * p + 1] = rad * sn;
       }
     }
   }
