@@ -145,6 +145,7 @@ struct SecDev {
   int mult[kSecMaxCls];
   double unit;
   int qextra;                   // extra headroom bits of the quantised copy
+  int dint;                     // the diagonal is an integer multiple of `unit` everywhere
   // low side
   // low-part tables cover the classes present: entry j - jbase for list position j, nJ of them
   uint32_t lo_off[kSecMaxL + 2];     // start of popcount class q in the list of all 2^L low parts

@@ -54,6 +54,10 @@ struct Analysis {
   std::vector<int> mult;
   bool int_ok = false;            // integer multiples found
   int qextra = 0;
+  // the diagonal in units of `unit` is an integer everywhere (fp64 pass R then forms the whole
+  // element as one exact int64 sum); maxdgi bounds its magnitude
+  bool dint = false;
+  double maxdgi = 0.0;
   // diagonal = c0 + sum_g gcoef[g] * count_g, count_g over pair bonds (both up) and sites (up)
   double c0 = 0.0;
   int n_dg = 0;
@@ -207,6 +211,25 @@ Analysis analyse(const SecTerms& t) {
     a.why = "split-row path: diagonal table too large";
     return a;
   }
+  if (a.int_ok && a.unit != 0.0) {
+    bool all_int = true;
+    double mx = 0.0;
+    for (int x = 0; x <= a.gmax[0] && all_int; ++x)
+      for (int y = 0; y <= a.gmax[1]; ++y) {
+        const double v = (a.c0 + a.gcoef[0] * x + a.gcoef[1] * y) / a.unit;
+        if (v != floor(v) || fabs(v) > 1048576.0) {
+          all_int = false;
+          break;
+        }
+        mx = std::max(mx, fabs(v));
+      }
+    if (all_int) {
+      a.dint = true;
+      a.maxdgi = mx;
+      // the element d q + S sums msum + maxdgi terms of magnitude < 2^(56 - qextra)
+      while (a.qextra < 40 && ((double)msum + mx) * ldexp(1.0, 56 - a.qextra) >= ldexp(1.0, 63)) ++a.qextra;
+    }
+  }
   a.ok = true;
   return a;
 }
@@ -336,6 +359,7 @@ Status sec_build(const SecTerms& t, int L, int K, SecTables** out, cudaStream_t 
   }
   d.unit = a.unit;
   d.qextra = a.qextra;
+  d.dint = a.dint ? 1 : 0;
 
   // low side: popcount-grouped list and ranks
   std::vector<uint32_t> lo_rank(nL), lo_list(nL);
@@ -701,6 +725,13 @@ __global__ void __launch_bounds__(kThreads) k_sec_hi(const SecDev d, const T* __
   }
 }
 
+// a 128-bit integer as the nearest-ish fp64 (two roundings: relative error below 2^-52)
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  const long long hi = (long long)(v >> 64);
+  const unsigned long long lo = (unsigned long long)v;
+  return fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo));
+}
+
 // K consecutive values of an interleaved shared-memory tile with the widest aligned loads
 template <class T, int K>
 __device__ __forceinline__ void tile_load(const T* p, T* out) {
@@ -737,6 +768,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   R* s_dtab = reinterpret_cast<R*>(smem_raw + (((size_t)(d.nq_max + 1) * K * sizeof(T) + 15) / 16) * 16);
+  int* s_dti = reinterpret_cast<int*>(s_dtab + d.dtab_n);  // fp64 with d.dint: the table in units
   __shared__ uint64_t s_roff[K];
   __shared__ uint32_t s_hrow[K];
   __shared__ uint32_t s_hdiag[K];
@@ -769,6 +801,14 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
   const double s_e2 = fold ? __longlong_as_double((long long)(e2 + 1023) << 52) : 1.0;
   const double r_k = fold ? __longlong_as_double((long long)(1023 - u_l2) << 52) : 1.0;
   for (int k = tid; k < d.dtab_n; k += NT) s_dtab[k] = (R)(d.dtab[k] * r_k);
+  // integral diagonal (in units of `unit`): in the folded fp64 Lanczos step the element is one
+  // exact int64 sum d q + (+-S), so its conversion is the only rounding, and <x, H x> adds the
+  // exact products q (d q +- S) in 128 bits, moved to fp64 every 64 elements
+  const bool dint = FIX && fold && d.dint && E == Epi::kLanczos1;
+  if (dint)
+    for (int k = tid; k < d.dtab_n; k += NT) s_dti[k] = (int)__double2ll_rn(d.dtab[k] * r_k);
+  __int128 ia = 0;
+  int ic = 0;
   if (tid < kSecMaxCls) s_w[tid] = tid < d.n_cls ? sec_w<T>(d, tid) : (T)0;
   if (tid < d.n_str)
     s_sb[tid] = make_uint2((uint32_t)d.str_b[tid] | ((uint32_t)d.str_cls[tid] << 16), (uint32_t)d.str_t[tid] * nJ);
@@ -953,15 +993,34 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
           if (m >= nk) break;
           uint32_t c = ld + s_hdiag[m];
           for (int l = 0; l < d.n_sl; ++l) c += (uint32_t)__popc(lo[e] & s_spm[m][l]) << (8 * d.sp_lg[l]);
-          const R dg = s_dtab[(c & 0xffu) + d.dstride * (c >> 8)];
+          const int ci = (int)(c & 0xffu) + d.dstride * (int)(c >> 8);
           const int64_t idx = (int64_t)s_roff[m] + u;
           const T xq = tile[u * K + m];
           const T wv = Wh[idx];
+          const R dg = s_dtab[ci];
           if constexpr (!FIX) {
             const R hv = ONE ? dg * xq + coef0 * (acc[e][m] + wv) : dg * xq + (acc[e][m] + wv);
             epilogue<float, E, NQ>(idx, 0, xq, 0.f, hv, 0.f, reinterpret_cast<float*>(w), fa, es, s_inv, red);
           } else {
             const long long S = acc[e][m] + wv;
+            if constexpr (E == Epi::kLanczos1) {
+              if (dint) {
+                const long long hq = (long long)s_dti[ci] * xq + (u_neg ? -S : S);  // hv = hq 2^e2
+                const double hvu = __ll2double_rn(hq);
+                double* P = reinterpret_cast<double*>(fa.out);
+                const double* Pin = fa.in ? reinterpret_cast<const double*>(fa.in) : P;
+                const double pv = fma(es.c1 * s_e2, hvu, -(es.c2 * Pin[idx]));
+                P[idx] = pv;
+                pmx = max(pmx, (int)((__double_as_longlong(pv) >> 52) & 0x7ff));
+                ia += (__int128)xq * (__int128)hq;
+                if (++ic == 64) {
+                  red.add(0, i128_to_double(ia), 1.0);
+                  ia = 0;
+                  ic = 0;
+                }
+                continue;
+              }
+            }
             const double xr = __ll2double_rn(xq);
             if (fold) {
               const double hvu = fma(dg, xr, __ll2double_rn(u_neg ? -S : S));  // hv = hvu 2^e2
@@ -997,6 +1056,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
     }
   }
   if constexpr (FIX && E == Epi::kLanczos1) {
+    if (ic) red.add(0, i128_to_double(ia), 1.0);
     if (fa.pexp != nullptr) {
       pmx = (int)__reduce_max_sync(0xffffffffu, (unsigned)pmx);
       if ((tid & 31) == 0 && pmx > 0) atomicMax(fa.pexp, pmx);
@@ -1023,8 +1083,9 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : 2) k_sec_lo(const SecDe
 }
 
 // ---------------------------------------------------------------- launch helpers
-size_t lo_smem(const SecDev& d, int esz) {  // the rows, their zero entry, the diagonal table
-  return (((size_t)(d.nq_max + 1) * d.K * esz + 15) / 16) * 16 + (size_t)d.dtab_n * esz;
+size_t lo_smem(const SecDev& d, int esz) {  // the rows, their zero entry, the diagonal table(s)
+  return (((size_t)(d.nq_max + 1) * d.K * esz + 15) / 16) * 16 + (size_t)d.dtab_n * esz +
+         (esz == 8 && d.dint ? (size_t)d.dtab_n * 4 : 0);
 }
 
 // row-pass threads: 1024 (one CTA per SM) for tiles above ~110 KB, else 512
