@@ -260,9 +260,10 @@ def run_e2e_lanczos(m, D, seed, steps, prec, args, world, v0_host=None):
 # benchmark (the 6x6 sector's 100-step fp64 run takes about a minute)
 BENCH_LANCZOS_STEPS = {"heisenberg_6x6_sz0": 20}
 # fp64-pipe operations per row of the fused Lanczos pass 1 of the split-row fp64 path, counted
-# from k_sec_lo's folded epilogue: two int64 -> fp64 conversions, the diagonal FMA, the update
-# c1 hv - c2 P (one multiply, one FMA) and the <C, H C> FMA
-SEC_FP64_OPS_PER_ROW = 6
+# from k_sec_lo's folded epilogue with an integral diagonal (the Heisenberg workloads): the
+# int64 -> fp64 conversion of the element and the update c1 hv - c2 P (one multiply, one FMA);
+# the element itself and <C, H C> are integer arithmetic
+SEC_FP64_OPS_PER_ROW = 3
 
 
 def host_ram_bytes():
