@@ -40,9 +40,9 @@ METRIC = "H·v Gelem/s & %HBM peak; Lanczos/mTPQ steps/s, FP64 vs mixed+batched 
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per fused H v launch group from an ncu capture of the current
 # kernels, with where they come from; absent where no capture of the current kernels exists
-MEASURED_TRAFFIC = {("heisenberg_6x6_sz0", "fp64"): (999_900_000_000, "ncu capture at full size (1-pass DRAM "
-                                                     "counters): k_sec_hi + k_sec_lo of one step after the "
-                                                     "first, split (15, 2), 1 KB pass-H stripes")}
+MEASURED_TRAFFIC = {("heisenberg_6x6_sz0", "fp64"): (1_001_300_000_000, "ncu capture at full size (1-pass DRAM "
+                                                       "counters): k_sec_hi + k_sec_lo of one step after the "
+                                                       "first, split (15, 2), 1 KB pass-H stripes")}
 # fp64 FMA throughput of this machine's GB300 from a throughput probe (thread-level T op/s); the
 # chip issues fp64 at 1/64 of its fp32 rate
 FP64_PEAK_TOPS = 0.50
