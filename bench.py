@@ -341,9 +341,9 @@ def run_ours(args, world, rank, local):
     m.release_workspace()
     # a real spin model of at most 32,768 rows runs the whole recurrence in one thread-block
     # cluster (k_lz_cl), which only graph-launched (unprofiled) runs take
-    one_cta = prec == hp.FP64 and spec.kind == wl.SPIN and not m.is_complex and D <= 32768
-    t = timed_lanczos(m, steps, prec, seed, args, world, local, rank, profile=not one_cta)
-    t["one_cta"] = one_cta
+    one_cluster = prec == hp.FP64 and spec.kind == wl.SPIN and not m.is_complex and D <= 32768
+    t = timed_lanczos(m, steps, prec, seed, args, world, local, rank, profile=not one_cluster)
+    t["one_cluster"] = one_cluster
     ms_step = t["ms"] / t["n"]
     res = t["res"]
     value = whole_job_rate(D * steps * t["n"], world, t["ms"] / 1e3)
@@ -412,7 +412,7 @@ def assemble_lanczos_line(args, world, spec, D, steps, prec, esz, value, ms_step
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
             "kernel": hv_group_kernels(spec, hp_model_stub(spec), prec), "kernel_avg_ms": round(hv_avg_ms, 4),
             "algorithmic_bytes_per_launch": D * bytes_row}
-    if t.get("one_cta"):
+    if t.get("one_cluster"):
         roof["kernel"] = ("k_lz_cl: the whole recurrence in one 16-CTA cluster, both vectors in distributed "
                           "shared memory (on chip); kernel_avg_ms is the run's device time per step")
     if prec == hp.FP64 and spec.kind == wl.SPIN and spec.basis == wl.BASIS_SZ:

@@ -1001,7 +1001,7 @@ def test_tpq_c64_carried_norm_drift_1000_steps():
         assert _rel(r64["h2"][:, c], h2) < 1e-5
 
 
-def test_lanczos_one_cta_heisenberg_ring12_full():
+def test_lanczos_one_cluster_heisenberg_ring12_full():
     """The 12-site ring in its full basis (4096 rows, 64 KB for both vectors) runs the whole
     100-step recurrence in one thread-block cluster (vectors in distributed shared memory): a
     handful of launches, the oracle's alpha / beta and the ring's ground-state energy."""
