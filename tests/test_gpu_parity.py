@@ -484,10 +484,25 @@ def _mg_closed_forms(n, res):
     k = 2 * np.pi * np.arange(n) / n
     e1 = n * 1.5 / 4 + np.min((np.cos(k) - 1) + 0.5 * (np.cos(2 * k) - 1))
     assert abs(by[n - 1] - e1) < 1e-10 and abs(by[1] - e1) < 1e-10
-    # S^z <-> -S^z partners share their spectrum; after a fixed step count the slowest
-    # mid-size sectors are converged to ~1e-9, so this checks the pairing at 1e-7
+    # S^z <-> -S^z partners share their spectrum, but their runs start from different seeded
+    # vectors, so after a fixed step count the slow mid-size sectors are converged to different
+    # depths (n_up = 7 and 21 of 28 sites differ by 5e-6 after 150 steps, each matching the
+    # oracle run from its own start vector).  A lowest Ritz value lies within its residual
+    # estimate |beta_m y_m| of an eigenvalue (section 3.4), which bounds the pairing; where both
+    # runs are converged the bound is tight.
+    def resid(r):
+        a, b = r["alpha"], r["beta"]
+        if len(a) < 2:
+            return abs(b[0]) if len(b) else 0.0
+        y = oracle.ritz_vector(a, b, 0)
+        return abs(b[len(a) - 1] * y[-1])
+    rs = {r["n_up"]: resid(r) for r in res}
     for up in range(n + 1):
-        assert abs(by[up] - by[n - up]) <= 1e-7 * max(1.0, abs(by[up]))
+        tol = 1e-9 * max(1.0, abs(by[up])) + rs[up] + rs[n - up]
+        assert abs(by[up] - by[n - up]) <= tol
+    # the partners of the most polarised sectors converge fully and pair tightly
+    for up in (2, 3, 4):
+        assert abs(by[up] - by[n - up]) <= 1e-9 * max(1.0, abs(by[up]))
 
 
 def test_j1j2_ring28_all_sectors_fp64_closed_forms():
