@@ -49,7 +49,7 @@ enum {
   HPHI_ERR_OUT_OF_MEMORY = -3,  /* device allocation failed                               */
   HPHI_ERR_NOT_BUILT = -4,      /* hphi_build_sector has not run since the last change    */
   HPHI_ERR_CUDA = -5,           /* a CUDA runtime call failed (message has the details)   */
-  HPHI_ERR_UNSUPPORTED = -7     /* valid request outside what this build implements       */
+  HPHI_ERR_UNSUPPORTED = -7     /* valid request outside what this library implements     */
 };
 
 /* ---------------------------------------------------------------- model definition */
