@@ -49,29 +49,33 @@ class _Model(ctypes.Structure):
     ]
 
 
+def _bind(L):
+    """Argument and result types of the oracle library's exported functions."""
+    P = ctypes.c_void_p
+    u64, i64, i32, f64 = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.or_dim.argtypes = [P, P]
+    L.or_binom.argtypes = [i32, i32]; L.or_binom.restype = u64
+    L.or_sector_list.argtypes = [i32, i32, P, i64]; L.or_sector_list.restype = i64
+    L.or_rank.argtypes = [u64, i32]; L.or_rank.restype = u64
+    L.or_unrank.argtypes = [u64, i32, i32]; L.or_unrank.restype = u64
+    L.or_hop_sign.argtypes = [u64, u64, i32, i32, i32]
+    L.or_apply_H.argtypes = [P, P, P, i32]
+    L.or_apply_H_slice.argtypes = [P, P, P, i32, u64, u64]
+    L.or_philox4x32_10.argtypes = [P, P, P]
+    L.or_gauss_pair.argtypes = [u64, u64, P]
+    L.or_random_at.argtypes = [u64, P, i64, i32, P]
+    L.or_apply_H_rows_philox.argtypes = [P, P, i64, u64, i32, i32, i32, P]
+    L.or_lanczos.argtypes = [P, P, i32, f64, P, P]
+    L.or_lanczos_vector.argtypes = [P, P, i32, P, P, P, P]
+    L.or_tpq.argtypes = [P, P, i32, f64, f64, P, P, P, P]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            u64, i64, i32, f64 = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_double
-            L.or_dim.argtypes = [P, P]
-            L.or_binom.argtypes = [i32, i32]; L.or_binom.restype = u64
-            L.or_sector_list.argtypes = [i32, i32, P, i64]; L.or_sector_list.restype = i64
-            L.or_rank.argtypes = [u64, i32]; L.or_rank.restype = u64
-            L.or_unrank.argtypes = [u64, i32, i32]; L.or_unrank.restype = u64
-            L.or_hop_sign.argtypes = [u64, u64, i32, i32, i32]
-            L.or_apply_H.argtypes = [P, P, P, i32]
-            L.or_apply_H_slice.argtypes = [P, P, P, i32, u64, u64]
-            L.or_philox4x32_10.argtypes = [P, P, P]
-            L.or_gauss_pair.argtypes = [u64, u64, P]
-            L.or_random_at.argtypes = [u64, P, i64, i32, P]
-            L.or_apply_H_rows_philox.argtypes = [P, P, i64, u64, i32, i32, i32, P]
-            L.or_lanczos.argtypes = [P, P, i32, f64, P, P]
-            L.or_lanczos_vector.argtypes = [P, P, i32, P, P, P, P]
-            L.or_tpq.argtypes = [P, P, i32, f64, f64, P, P, P, P]
-            _lib = L
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
 
 

@@ -432,7 +432,9 @@ def _num_ops(n):
 @pytest.mark.parametrize("basis", ["full", "sector"])
 def test_diag_observables_hubbard_match_fermion_operators(basis):
     """Doubly occupied sites and S^z_total of a Hubbard state against the Jordan-Wigner
-    number operators (mode i + n s, full-basis index up + 2^n dn)."""
+    number operators (mode i + n s, full-basis index up + 2^n dn).  The sector (3, 2) has
+    different up and down dimensions (4 and 6), so a transposed (up, down) index layout
+    changes the result."""
     n = 4
     spec = wl.hubbard(n, [], U=1.0)
     num = _num_ops(n)
@@ -441,8 +443,8 @@ def test_diag_observables_hubbard_match_fermion_operators(basis):
     if basis == "full":
         idx = np.arange(4 ** n)
     else:
-        spec = spec.with_basis(wl.BASIS_NUMBER, 3, 1)
-        idx = _indep.hubbard_sector_indices(n, 3, 1)
+        spec = spec.with_basis(wl.BASIS_NUMBER, 3, 2)
+        idx = _indep.hubbard_sector_indices(n, 3, 2)
     psi = wl.gaussian_vector(5, len(idx), nvec=3, complex_=True)
     d, sz, sz2 = oracle.diag_observables(spec, psi)
     full = np.zeros((4 ** n, 3), dtype=complex)
@@ -454,7 +456,7 @@ def test_diag_observables_hubbard_match_fermion_operators(basis):
         assert abs(sz[c] - np.vdot(x, Sz @ x).real / nn / n) < 1e-13
         assert abs(sz2[c] - np.vdot(x, Sz @ Sz @ x).real / nn / n) < 1e-13
     if basis == "sector":
-        assert np.allclose(sz, (3 - 1) / 2 / n, atol=1e-15) and np.allclose(sz2, 1.0 / n, atol=1e-15)
+        assert np.allclose(sz, (3 - 2) / 2 / n, atol=1e-15) and np.allclose(sz2, 0.25 / n, atol=1e-15)
     # the oracle's own U term is the doublon operator
     HU = oracle.dense_H(spec)
     x = psi[:, 0]
@@ -533,29 +535,44 @@ def test_inverse_iteration_converges_to_the_eigenvector():
     assert err1 < err0 * ((1e-2 - 1e-3) / (ev[1] - ev[0] - 1e-3 + 1e-2)) ** 2 * 10
 
 
-def test_lanczos_convergence_step_rule():
-    """Appendix C's rule on a recurrence with a known answer: T from a diagonal matrix with
-    well separated low levels converges; the rule returns an odd n >= 7 at which the first
-    excited Ritz value has settled, and None when eps is unreachable."""
-    d = np.concatenate([[-3.0, -2.0], np.linspace(0, 1, 200)])
+def _lanczos_diag(d, m):
+    """Lanczos with full reorthogonalisation on diag(d) from the uniform vector, in plain numpy
+    (the oracle's recurrence is pinned elsewhere)."""
     v0 = np.ones(len(d)) / math.sqrt(len(d))
-    # Lanczos on diag(d) in plain numpy (the oracle's recurrence is pinned elsewhere)
-    a, b = [], []
+    a, b, Q = [], [], [v0]
     q_prev, q, bk = np.zeros_like(v0), v0, 0.0
-    for _ in range(40):
+    for _ in range(m):
         w = d * q - bk * q_prev
         ak = q @ w
         w -= ak * q
-        w -= (w @ q) * q
+        Qm = np.array(Q)
+        w -= Qm.T @ (Qm @ w)
         bk = np.linalg.norm(w)
         a.append(ak)
         b.append(bk)
         q_prev, q = q, w / bk
+        Q.append(q)
+    return a, b
+
+
+def test_lanczos_convergence_step_rule():
+    """Appendix C's rule on recurrences with a known answer: T from a diagonal matrix converges;
+    the rule returns an odd n >= 7 at which the first excited Ritz value has settled, and None
+    when eps is unreachable.  In the second spectrum the ground level is isolated (settled
+    after 9 steps) while the first excited level sits next to the bulk, so a rule that watched
+    the ground level would stop with the first excited value still 0.06 off."""
+    d = np.concatenate([[-3.0, -2.0], np.linspace(0, 1, 200)])
+    a, b = _lanczos_diag(d, 40)
     n = oracle.lanczos_convergence_step(a, b, 1e-10)
     assert n is not None and n >= 7 and (n - 5) % 2 == 0
     e1n = oracle.ritz_values(a[:n], b[:n])[1]
     assert abs(e1n - (-2.0)) < 1e-8
     assert oracle.lanczos_convergence_step(a[:9], b[:9], 1e-300) is None
+    d = np.concatenate([[-10.0, -1.05], np.linspace(-1, 1, 300)])
+    a, b = _lanczos_diag(d, 80)
+    n = oracle.lanczos_convergence_step(a, b, 1e-10)
+    assert n is not None and n > 20 and (n - 5) % 2 == 0
+    assert abs(oracle.ritz_values(a[:n], b[:n])[1] - (-1.05)) < 1e-8
 
 
 def test_lanczos_reorth_keeps_the_basis_orthonormal():
