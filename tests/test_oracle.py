@@ -146,6 +146,31 @@ def test_spin_sector_vs_kronecker(n, k):
     assert np.max(np.abs(H - Href)) < 1e-13
 
 
+@pytest.mark.parametrize("nvec", [3, 4])
+def test_apply_H_vector_block_vs_independent_matrices(nvec):
+    """A [dim][nvec] block (row-major: the nvec values of a row are adjacent) is multiplied
+    column by column: against the Kronecker and Jordan-Wigner matrices, with different
+    columns, so a column index dropped or mixed up fails."""
+    for spec, dense in ((wl.random_spin_model(5, 7, 11, complex_=True, fields=True), _indep.dense_spin),
+                        (wl.random_hubbard_model(3, 6, 12, complex_=True), _indep.dense_hubbard)):
+        D = oracle.dim(spec)
+        V = wl.gaussian_vector(20 + nvec, D, nvec, complex_=True)
+        W = oracle.apply_H(spec, V)
+        assert W.shape == (D, nvec)
+        assert np.max(np.abs(W - dense(spec) @ V)) < 1e-12
+
+
+def test_apply_H_slice_rows():
+    """Rows [r0, r0 + n) of the product, for the CPU timing legs, equal those rows of the
+    Kronecker matrix times v."""
+    spec = wl.random_spin_model(6, 9, 13, complex_=True, fields=True)
+    D = oracle.dim(spec)
+    v = wl.gaussian_vector(31, D, 2, complex_=True)
+    full = _indep.dense_spin(spec) @ v
+    for r0, n in ((0, 5), (17, 23), (D - 9, 9)):
+        assert np.max(np.abs(oracle.apply_H_slice(spec, v, r0, n) - full[r0:r0 + n])) < 1e-12
+
+
 def test_sector_mismatch_is_reported():
     spec = wl.random_spin_model(4, 3, seed=3).with_basis(wl.BASIS_SZ, 2)
     with pytest.raises(oracle.OracleError):

@@ -83,6 +83,16 @@ CPP_MUTANTS = [
      [T.test_lanczos_ground_state_vs_dense]),
     ("lanczos_no_breakdown_stop", "    if (b_next <= brk * std::fmax(1.0, std::fabs(a_k))) break;\n", "",
      [T.test_lanczos_breakdown_on_one_state_sector]),
+    ("hubbard_index_transposed", "return rank_same_popcount(dn, n) * dim_up + rank_same_popcount(up, n);",
+     "return rank_same_popcount(up, n) * dim_dn + rank_same_popcount(dn, n);",
+     [lambda: T.test_hubbard_sector_vs_jordan_wigner(2, 1)]),
+    ("vector_block_column_dropped", "out[c] += el * v[col * nvec + c];", "out[c] += el * v[col * nvec];",
+     [lambda: T.test_apply_H_vector_block_vs_independent_matrices(3)]),
+    ("slice_offset_dropped", "const uint64_t r = r0 + (uint64_t)k;", "const uint64_t r = (uint64_t)k;",
+     [T.test_apply_H_slice_rows]),
+    ("tpq_norm_squared", "nrm_out[k - 1] = pn;", "nrm_out[k - 1] = pn * pn;", [T.test_tpq_matches_matrix_power]),
+    ("popcount_counts_every_bit", "while (x) { c += (int)(x & 1u); x >>= 1; }", "while (x) { c += 1; x >>= 1; }",
+     [T.test_paper_sz0_basis_and_ranks]),
 ]
 
 # (name, function, text of oracle/__init__.py, planted text, pins that must fail)
@@ -106,6 +116,8 @@ PY_MUTANTS = [
      [lambda: T.test_diag_observables_hubbard_match_fermion_operators("sector")]),
     ("ritz_beta_offset", "ritz_values", "e = np.asarray(beta[: n - 1], dtype=np.float64)",
      "e = np.asarray(beta[1:n], dtype=np.float64)", [T.test_lanczos_ground_state_vs_dense]),
+    ("ritz_vector_wrong_column", "ritz_vector", "    return v[:, which]\n", "    return v[:, -1]\n",
+     [T.test_lanczos_eigenvector_second_pass]),
 ]
 
 
